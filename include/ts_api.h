@@ -1,0 +1,218 @@
+/*
+ * ts_api.h -- C ABI of libts, the GB300 (sm_103a) differentiable triangle-splatting rasterizer.
+ *
+ * The library renders a triangle soup (or indexed mesh) with per-vertex colour and opacity into
+ * colour, depth and opacity images, and back-propagates image-space loss gradients to vertex
+ * positions, colours, opacities and the SE(3) camera pose.  It implements Triangle Splatting SLAM:
+ *   Eq. 1  projection v_I = pi(T_CW v_W);
+ *   Eq. 2  SDF phi(p) = max_i L_i(p) of the projected triangle, L_i the outward edge functions;
+ *   Eq. 3  window I(p) = ReLU(phi(p) / phi(s))^sigma, s the incentre;
+ *   Sec. 3.1 barycentric vertex-colour interpolation, face opacity o_F = (o_i + o_j + o_k) / 3;
+ *   Eq. 4  front-to-back alpha compositing over faces sorted in depth order;
+ *   Eq. 5-7 the analytic pose Jacobian, D v_C / D T_CW = [I_3, -[v_C]x], tau = (rho, theta).
+ *
+ * Conventions (all calls):
+ *   - Every pointer named "device" is CUDA device memory owned by the caller; libts never
+ *     allocates device memory.  Host pointers are read during the call only.
+ *   - All calls except ts_plan_init, ts_workspace_size, ts_status_string and ts_sync_status
+ *     are asynchronous on the given stream, perform no host synchronisation and no allocation,
+ *     and may be captured into a CUDA graph.
+ *   - Argument errors are returned synchronously (TS_ERR_INVALID_ARG, nothing launched).
+ *     Errors detected on the device (pair-capacity overflow, a bounded wait that timed out) are
+ *     latched in the workspace and reported by ts_sync_status; outputs are then unspecified.
+ *   - Calls on one workspace must run in the order ts_project -> ts_bin -> ts_render_fwd ->
+ *     ts_render_bwd -> ts_pose_grad on one stream (a later call may be repeated or omitted).
+ *     The workspace keeps the per-face records, the sorted tile lists and, per pixel, the final
+ *     transmittance and the list position of the last contribution, so that the backward pass
+ *     recomputes blending state instead of storing it.
+ *   - Images of the views are packed back to back: view v's colour starts at 3 * pix_off[v]
+ *     and is planar [3][H][W]; depth, alpha and the other per-pixel arrays start at pix_off[v]
+ *     and are [H][W]; pix_off[v] = sum over u < v of W_u * H_u.
+ *   - Pixel (x, y) samples the image point (x + 0.5, y + 0.5).
+ */
+#ifndef TS_API_H
+#define TS_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ts_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  TS_OK = 0,
+  TS_ERR_INVALID_ARG = 1, /* bad pointer, size, or parameter; nothing was launched */
+  TS_ERR_CUDA = 2,        /* a CUDA launch or runtime call failed */
+  TS_ERR_CAPACITY = 3,    /* more (tile, face) pairs than the plan's pair capacity */
+  TS_ERR_TIMEOUT = 4,     /* a bounded device wait expired; outputs unspecified */
+  TS_ERR_UNSUPPORTED = 5  /* a parameter combination this build does not implement */
+} ts_status;
+
+#define TS_MAX_VIEWS 256
+
+/* Pinhole camera of one view (Eq. 1): u = fx * x_c / z_c + cx, v = fy * y_c / z_c + cy. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} ts_camera;
+
+/* World-to-camera pose T_CW (Eq. 1): v_C = R v_W + t, R row-major. */
+typedef struct {
+  float R[9];
+  float t[3];
+} ts_pose;
+
+/* Rasterization parameters.  The paper fixes sigma (Table S5: 0.5); the rest are readings where
+ * the paper is silent: alpha = min(alpha_max, o_F * I); a contribution with alpha < alpha_min is
+ * skipped; a pixel stops before the face that would take its transmittance below T_min; faces
+ * with a vertex at z <= z_near, an inradius below r_min pixels, o_F < alpha_min or an empty
+ * pixel box are culled; bg is the background colour (weight T_final). */
+typedef struct {
+  float sigma, alpha_min, alpha_max, T_min, z_near, r_min;
+  float bg[3];
+  int32_t tile_w, tile_h;   /* tile shape: tile_w in {8, 16, 32}, tile_h in {4, 8, 16, 32}, <= 512 px */
+  int32_t tris_per_stage;   /* faces staged in shared memory per step: 32, 64 or 128 */
+  int32_t flags;            /* reserved, must be 0 */
+} ts_raster_params;
+
+/* The map (Sec. 3.1): N vertices with position, colour, opacity as structure-of-arrays float32
+ * device buffers, and M faces.  faces = NULL selects triangle-soup mode (face m uses vertices
+ * 3m, 3m+1, 3m+2; N = 3M); otherwise faces is device int32 [M][3].  The buffers must stay valid
+ * and unchanged from ts_project until the ts_render_bwd of the same workspace has completed. */
+typedef struct {
+  const float *px, *py, *pz;
+  const float *cr, *cg, *cb;
+  const float *op;
+  const int32_t* faces;
+  int64_t n_vertices, n_faces;
+} ts_map;
+
+/* Gradient buffers (device float32, same layout as ts_map).  ts_render_bwd ADDS into them, so
+ * the caller zeroes them once and multi-view sums need no extra pass.  Any pointer may be NULL
+ * to skip that gradient. */
+typedef struct {
+  float *gpx, *gpy, *gpz;
+  float *gcr, *gcg, *gcb;
+  float *gop;
+} ts_map_grad;
+
+/* Host-side plan: the views, the map size, the parameters and the workspace layout.  Filled by
+ * ts_plan_init; treat as opaque.  The caller owns it (stack or heap); it holds no pointers. */
+#define TS_PLAN_BYTES 24576
+typedef struct {
+  uint64_t opaque[TS_PLAN_BYTES / 8];
+} ts_plan;
+
+/* Device-side counters, copied to the host by ts_sync_status. */
+typedef struct {
+  uint64_t n_pairs;          /* (tile, face) pairs emitted by ts_bin (may exceed capacity) */
+  uint64_t pair_capacity;    /* the plan's capacity */
+  uint64_t n_visible;        /* (view, face) records that survived culling */
+  uint64_t fwd_contrib;      /* (pixel, face) contributions blended by ts_render_fwd */
+  uint64_t bwd_contrib;      /* (pixel, face) contributions differentiated by ts_render_bwd */
+  uint32_t error_bits;       /* bit 0 capacity overflow, bit 1 wait timeout */
+  uint32_t reserved;
+} ts_counters;
+
+/* Default parameters: sigma 0.5 (Table S5), alpha_min 1/255, alpha_max 0.99, T_min 1e-4,
+ * z_near 0.01, r_min 0.01 px, bg 0, tile 16 x 16, 64 faces per stage. */
+void ts_default_params(ts_raster_params* out);
+
+/* Validate the views and parameters and lay out the workspace.
+ *   cams: host array [n_views]; 1 <= n_views <= TS_MAX_VIEWS; 1 <= width, height <= 16384.
+ *   n_faces >= 0 (0 renders background only).
+ *   pair_capacity: (tile, face) pairs the workspace can hold; 0 picks 4 * n_views * n_faces
+ *   (at least 1024).  Returns TS_ERR_INVALID_ARG on any bad value. */
+ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, int64_t n_faces,
+                       const ts_raster_params* params, int64_t pair_capacity);
+
+/* Bytes of device workspace the plan needs (256-byte aligned base required). */
+size_t ts_workspace_size(const ts_plan* plan);
+
+/* Zero the workspace's persistent state (counters and gradient accumulators).  Call once after
+ * allocating the workspace and again after any device-side error.  Asynchronous. */
+ts_status ts_workspace_init(const ts_plan* plan, void* ws, size_t ws_bytes, ts_stream stream);
+
+/* Eq. 1-3 per (view, face): rigid transform, projection, culling, the face's screen-space
+ * record (edge functions, barycentric interpolants, opacity) and its tile box and depth key.
+ *   map:   device buffers (see ts_map); map->n_faces must equal the plan's n_faces.
+ *   poses: device array [n_views] of ts_pose.
+ *   ws:    device workspace of at least ts_workspace_size(plan) bytes, 256-byte aligned. */
+ts_status ts_project(const ts_plan* plan, const ts_map* map, const ts_pose* poses, void* ws,
+                     size_t ws_bytes, ts_stream stream);
+
+/* Depth ordering per tile (Eq. 4, "sorted in depth order"): exclusive scan of tiles touched,
+ * emission of 64-bit keys (global tile id << 32 | depth bits) with face-id values, a stable
+ * on-device LSD radix sort, and per-tile [start, end) ranges.  Ties keep ascending face id. */
+ts_status ts_bin(const ts_plan* plan, void* ws, ts_stream stream);
+
+/* Eq. 3-4 forward: per pixel, front-to-back compositing of its tile's list with early
+ * termination.  Writes (device, packed per view) color [3][H][W], depth [H][W] (sum of
+ * z(p) alpha T, unnormalised) and alpha [H][W] (= 1 - T_final).  color must not alias the
+ * others.  Any output may be NULL except that the workspace always records T_final and the
+ * last-contribution position needed by ts_render_bwd. */
+ts_status ts_render_fwd(const ts_plan* plan, void* ws, float* color, float* depth, float* alpha,
+                        ts_stream stream);
+
+/* Adjoint of Eq. 1-4: back-to-front re-traversal from each pixel's last contribution, recovering
+ * transmittance by division, warp-level reduction of per-face gradients before global atomics,
+ * then the chain rule through the projection into the map gradients (added, see ts_map_grad)
+ * and the per-view pose gradient partials consumed by ts_pose_grad.
+ *   dC [3][H][W], dD, dA [H][W] packed per view (device); dD or dA may be NULL (zero).
+ *   grad may be NULL or have NULL members to skip map gradients. */
+ts_status ts_render_bwd(const ts_plan* plan, void* ws, const float* dC, const float* dD,
+                        const float* dA, const ts_map_grad* grad, ts_stream stream);
+
+/* Eq. 5-7: dL/dtau per view for the left perturbation Exp(tau) o T_CW, tau = (rho, theta), as
+ * sum over the view's visible face vertices of [g_C ; v_C x g_C], reduced deterministically.
+ *   dtau: device float [n_views][6], overwritten. */
+ts_status ts_pose_grad(const ts_plan* plan, void* ws, float* dtau, ts_stream stream);
+
+/* Mean-L1 colour + depth loss used by tracking and mapping (Eq. 8 L1 part, Eq. 9): per view,
+ *   loss_v = sum |C - Cbar| / (3HW) + lambda_dep * sum_{Dbar > 0} |D - Dbar| / (HW),
+ * with dC = dloss/dC and dD = dloss/dD (overwritten; sign(0) = 0).  All pointers device, packed
+ * per view; loss: float [n_views], overwritten.  Deterministic. */
+ts_status ts_l1_loss(const ts_plan* plan, void* ws, const float* color, const float* depth,
+                     const float* tgt_color, const float* tgt_depth, float lambda_dep, float* loss,
+                     float* dC, float* dD, ts_stream stream);
+
+/* Pose update for tracking: poses[v] <- Exp(-step[v]) o poses[v] (left perturbation, closed-form
+ * SE(3) exponential), step = (rho, theta) device float [n_views][6]; poses device [n_views]. */
+ts_status ts_pose_apply(const ts_plan* plan, ts_pose* poses, const float* step, ts_stream stream);
+
+/* Synchronise the stream, copy the device counters into *out (may be NULL) and return
+ * TS_ERR_CAPACITY / TS_ERR_TIMEOUT if the device latched an error since ts_workspace_init,
+ * else TS_OK. */
+ts_status ts_sync_status(const ts_plan* plan, void* ws, ts_stream stream, ts_counters* out);
+
+/* Views, tiles and pixel offsets of the plan (host, for packing images).
+ *   pix_off, tile_off: host int64 [n_views + 1] (may be NULL). */
+ts_status ts_plan_layout(const ts_plan* plan, int64_t* pix_off, int64_t* tile_off,
+                         int32_t* tiles_x, int32_t* tiles_y);
+
+/* Debug access to intermediate arrays (asynchronous device-to-device copy of up to bytes).
+ *   what: 0 sorted keys (uint64 [capacity]), 1 sorted face ids (uint32 [capacity]),
+ *         2 tile ranges (uint32 [n_tiles][2]), 3 tile boxes (int16 [V*M][4]),
+ *         4 depth keys (uint32 [V*M]), 5 tiles touched (uint32 [V*M]),
+ *         6 T_final (float [total px]), 7 last-contribution positions (int32 [total px]),
+ *         8 face records (float [V*M][32]). */
+ts_status ts_debug_copy(const ts_plan* plan, void* ws, int32_t what, void* dst, size_t bytes,
+                        ts_stream stream);
+
+/* Per-stage CUDA-event timing: when events != NULL, later calls record events[2k] before and
+ * events[2k+1] after stage k (see TS_STAGE_*) on the launching stream.  events: host array of
+ * 2 * TS_N_STAGES cudaEvent_t created by the caller; NULL disables timing. */
+enum { TS_STAGE_PROJECT = 0, TS_STAGE_BIN = 1, TS_STAGE_FWD = 2, TS_STAGE_BWD_RASTER = 3,
+       TS_STAGE_BWD_PROJECT = 4, TS_STAGE_POSE = 5, TS_STAGE_LOSS = 6, TS_N_STAGES = 7 };
+ts_status ts_set_stage_events(ts_plan* plan, void* const* events);
+
+const char* ts_status_string(ts_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TS_API_H */

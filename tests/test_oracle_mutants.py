@@ -1,0 +1,30 @@
+"""Each planted mistake in the oracle (built with -DORACLE_MUTANT=k) must fail at least one pin.
+
+The mistakes are the plausible ones: a min instead of the mean face opacity (Sec. 3.1), inward
+edge normals (Eq. 2), a transposed rotation (Eq. 1), compositing with the transmittance after the
+face instead of before it (Eq. 4), a dropped background term, integer instead of half-integer
+pixel centres, a rotated barycentric index for depth, a flipped cross product in the pose
+Jacobian (Eq. 7), a missing 1/(1 - alpha) in the adjoint, a descending depth sort, an
+off-by-one tile box, and a wrong loss normalisation.
+"""
+import pytest
+
+import oracle_pins as P
+from oracle.oracle import Oracle
+
+MUTANTS = list(range(1, 13))
+
+
+@pytest.mark.parametrize("k", MUTANTS)
+def test_mutant_is_caught(k):
+    o = Oracle(mutant=k)
+    failed = []
+    for pin in P.ALL_PINS:
+        try:
+            if pin is P.pin_fd_gradients:
+                pin(o, seeds=(21,), sigmas=(1.0,))
+            else:
+                pin(o)
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"mutant {k} passed every pin"
