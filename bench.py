@@ -1,0 +1,344 @@
+"""Benchmark: Mpix/s of forward + backward rasterization on the room workload.
+
+Default workload: 1200x680 pinhole (fx = fy = 600), 300k-face room map, 20 seeded poses, one step =
+project + bin + forward + L1 colour/depth loss + backward (map gradients) + pose gradients for all
+20 views in one batched call sequence.  ``value`` = pixels of all views (all ranks) per second of
+device time, inputs resident in HBM, L2 flushed (256 MB write) between timed steps.
+
+Also reported: the same step done view by view (``plain_per_view``), the end-to-end metric with
+inputs copied from pinned host memory and results read back (``e2e``), per-stage event times and
+the roofline of the dominant kernel, sampled clocks, and the CPU oracle on a bounded sample.
+
+``--impl reference`` times the CPU oracle instead (the reference arm of this metric).
+Under torchrun (N > 1) every rank renders its own replica of the workload (replicas only: the
+views are independent, there is no exchange step), timed with a barrier and the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_FWD = 35.0   # algorithmic flops per blended (pixel, face) contribution, forward
+FLOPS_BWD = 90.0   # per differentiated contribution, backward raster
+W, H, F, N_FACES, N_VIEWS = 1200, 680, 600.0, 300_000, 20
+WORKLOAD = "room 1200x680 f=600, 300k faces, 20 poses, fwd+bwd (L1 colour+depth), batched"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--faces", type=int, default=N_FACES)
+    ap.add_argument("--views", type=int, default=N_VIEWS)
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--stage", type=int, default=64)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def scene(args):
+    from ts_synth import room_scene
+    return room_scene(3, args.faces, args.views, W, H, F, target_seed=4)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(sc, time_budget_s=20.0):
+    """The oracle (as it stands) on one view of the workload, all host cores: fwd + L1 + bwd."""
+    from oracle.oracle import Oracle, Params, SceneArrays, pack_targets
+    o = Oracle()
+    sub = sc.subset_views([0])
+    sa = SceneArrays.of(sub)
+    prm = Params()
+    nthreads = os.cpu_count() or 1
+    prm.n_threads = nthreads
+    tc, td = pack_targets(sub)
+    times = []
+    t_end = time.perf_counter() + time_budget_s
+    while True:
+        t0 = time.perf_counter()
+        f = o.forward(sa, prm)
+        lo = o.l1_loss(sa, f["color"], f["depth"], tc, td, 0.05)
+        o.backward(sa, prm, lo["dC"], lo["dD"])
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end or len(times) >= 3 or times[-1] > 0.5 * time_budget_s:
+            break
+    t = float(np.median(times))
+    return {"value": W * H / t / 1e6, "unit": "Mpix/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"1 of {sc.n_views} views (1200x680, {sc.n_faces} faces): fwd + L1 loss + bwd, "
+                      f"median of {len(times)} runs, {t:.2f} s each"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sc = scene(args)
+    steps = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(sc, time_budget_s=0.0)
+        if i >= args.warmup:
+            steps.append(W * H / r["value"] / 1e6)
+        base = r
+    t = float(np.mean(steps))
+    val = W * H / t / 1e6
+    line = {"impl": "reference", "metric": "Mpix/s fwd+bwd raster", "value": val, "unit": "Mpix/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle: one view per step)", "views_per_step": 1},
+            "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"], "value": val,
+                             "unit": "Mpix/s"},
+            "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2605_31419_gb300 as ts
+
+    sc = scene(args)
+    tw, th = (int(x) for x in args.tile.split("x"))
+    params = ts.ts_default_params(tile_w=tw, tile_h=th, tris_per_stage=args.stage)
+    rast = ts.Rasterizer(sc.cams, sc.n_faces, params)
+    m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa, device=dev)
+    poses = ts.poses_tensor(sc.poses, device=dev)
+    tgt_c = torch.as_tensor(np.concatenate([t.reshape(-1) for t in sc.tgt_color]), device=dev)
+    tgt_d = torch.as_tensor(np.concatenate([t.reshape(-1) for t in sc.tgt_depth]), device=dev)
+    grad = m.zeros_like()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # per-stage events (forced into existence by one record each)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(ts.binding.STAGES))]
+    for e in ev:
+        e.record(stream)
+
+    def step(r=rast, mp=m, ps=poses, tc=tgt_c, td=tgt_d, g=grad):
+        g.pos.zero_(); g.col.zero_(); g.opa.zero_()
+        r.forward(mp, ps)
+        r.l1_loss(tc, td, 0.05)
+        r.backward(r.dC, r.dD, None, g)
+        r.pose_grad()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    cnt = rast.counters()
+    ts.ts_set_stage_events(rast.plan, ev)
+    stage_ms = np.zeros(len(ts.binding.STAGES))
+    sampler = ClockSampler(dev.index or 0)
+    step_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        step()
+        s1.record(stream)
+        s1.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        for k in range(len(ts.binding.STAGES)):
+            stage_ms[k] += ev[2 * k].elapsed_time(ev[2 * k + 1])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ts.ts_set_stage_events(rast.plan, None)
+    t_step = float(np.sum(step_ms)) / args.steps / 1e3
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    stage_ms /= args.steps
+    pixels = sc.pixels()
+    value = pixels * world / t_step / 1e6
+
+    # -- plain per-view: the same work, one view per call sequence (its own plan) ------------------
+    plain_ms = None
+    if rank == 0:
+        single = ts.Rasterizer(sc.cams[:1], sc.n_faces, params)
+        P1 = W * H
+        for _ in range(2):
+            for v in range(sc.n_views):
+                step(single, m, poses[v:v + 1], tgt_c[3 * P1 * v:3 * P1 * (v + 1)], tgt_d[P1 * v:P1 * (v + 1)])
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        a0.record(stream)
+        for v in range(sc.n_views):
+            step(single, m, poses[v:v + 1], tgt_c[3 * P1 * v:3 * P1 * (v + 1)], tgt_d[P1 * v:P1 * (v + 1)])
+        a1.record(stream)
+        a1.synchronize()
+        plain_ms = a0.elapsed_time(a1)
+        del single
+
+    # -- end to end: pinned host inputs in, results out, through the same API ---------------------
+    e2e = None
+    if rank == 0:
+        h_pos, h_col, h_opa = m.pos.cpu().pin_memory(), m.col.cpu().pin_memory(), m.opa.cpu().pin_memory()
+        h_poses = poses.cpu().pin_memory()
+        h_tc, h_td = tgt_c.cpu().pin_memory(), tgt_d.cpu().pin_memory()
+        out_pos, out_col, out_opa = (torch.empty_like(h_pos).pin_memory(), torch.empty_like(h_col).pin_memory(),
+                                     torch.empty_like(h_opa).pin_memory())
+        out_tau, out_loss = torch.empty(sc.n_views, 6).pin_memory(), torch.empty(sc.n_views).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in (h_pos, h_col, h_opa, h_poses, h_tc, h_td))
+        d2h = sum(t.numel() * t.element_size() for t in (out_pos, out_col, out_opa, out_tau, out_loss))
+        d_pos, d_col, d_opa = torch.empty_like(m.pos), torch.empty_like(m.col), torch.empty_like(m.opa)
+        d_poses, d_tc, d_td = torch.empty_like(poses), torch.empty_like(tgt_c), torch.empty_like(tgt_d)
+        dm = ts.Map(d_pos, d_col, d_opa)
+
+        def e2e_step():
+            for d, hsrc in ((d_pos, h_pos), (d_col, h_col), (d_opa, h_opa), (d_poses, h_poses), (d_tc, h_tc),
+                            (d_td, h_td)):
+                d.copy_(hsrc, non_blocking=True)
+            step(rast, dm, d_poses, d_tc, d_td)
+            out_pos.copy_(grad.pos, non_blocking=True)
+            out_col.copy_(grad.col, non_blocking=True)
+            out_opa.copy_(grad.opa, non_blocking=True)
+            out_tau.copy_(rast.dtau, non_blocking=True)
+            out_loss.copy_(rast.loss_v, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e_ms = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1.0)
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            e2e_step()
+            b1.record(stream)
+            b1.synchronize()
+            e_ms.append(b0.elapsed_time(b1))
+        e2e = {"value": pixels / (float(np.mean(e_ms)) / 1e3) / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank == 0:
+        peaks, peak_src = measured_peaks()
+        names = ts.binding.STAGES
+        dom = int(np.argmax(stage_ms))
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
+        if names[dom] in ("bwd_raster", "fwd"):
+            contrib = cnt["bwd_contrib"] if names[dom] == "bwd_raster" else cnt["fwd_contrib"]
+            flops = (FLOPS_BWD if names[dom] == "bwd_raster" else FLOPS_FWD) * contrib
+            ach = flops / (stage_ms[dom] / 1e3) / 1e12
+            roof = {"kernel": f"k_render_{'bwd' if names[dom] == 'bwd_raster' else 'fwd'}", "bound": "alu",
+                    "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                    "work": f"{contrib} (pixel, face) contributions x {FLOPS_BWD if names[dom] == 'bwd_raster' else FLOPS_FWD:.0f} flops"}
+        else:
+            roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": None, "traffic": None}
+        launches = 2 + 3 + 5 * int(rast.plan_passes()) + 1 + 1 + 2 + 2 + 1
+        line = {
+            "metric": "Mpix/s fwd+bwd raster", "value": value, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "views": sc.n_views, "W": W, "H": H, "faces": sc.n_faces,
+                       "tile": args.tile, "tris_per_stage": args.stage, "l2": "flushed (256 MB write) between steps",
+                       "parallelism": f"replicas x{world}"},
+            "plain_per_view": {"value": pixels / (plain_ms / 1e3) / 1e6 if plain_ms else None, "unit": "Mpix/s",
+                               "ms_per_step": plain_ms},
+            "stages_ms": {n: float(t) for n, t in zip(names, stage_ms)},
+            "counters": {k: int(v) for k, v in cnt.items() if isinstance(v, (int, np.integer))},
+            "roofline": roof, "peaks": peak_src, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(sc)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -113,7 +113,8 @@ typedef struct {
   uint64_t n_visible;        /* (view, face) records that survived culling */
   uint64_t fwd_contrib;      /* (pixel, face) contributions blended by ts_render_fwd */
   uint64_t bwd_contrib;      /* (pixel, face) contributions differentiated by ts_render_bwd */
-  uint32_t error_bits;       /* bit 0 capacity overflow, bit 1 wait timeout */
+  uint32_t error_bits;       /* bit 0 capacity overflow, bit 1 wait timeout, bit 2 an internal index
+                                failed its bounds check and the access was skipped (TS_ERR_CUDA) */
   uint32_t reserved;
 } ts_counters;
 

@@ -139,6 +139,7 @@ class Oracle:
         L.oracle_pixel_trace.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, i32, vp]
         L.oracle_pixel_trace.restype = i32
         L.oracle_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_backward_ex.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_l1_loss.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, vp]
         L.oracle_l1_loss.restype = d
         L.oracle_window.argtypes = [vp, d, d, d, vp]
@@ -197,12 +198,13 @@ class Oracle:
         dpos, dcol = np.zeros((N, 3)), np.zeros((N, 3))
         dopa = np.zeros(N)
         dtau = np.zeros((len(sa.cams), 6))
+        dtau_abs = np.zeros((len(sa.cams), 6))
         f = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
         dC, dD, dA = f(dC), f(dD), f(dA)
         sc, p = sa.c(), prm.c()
-        self.lib.oracle_backward(C.byref(sc), C.byref(p), _ptr(dC), _ptr(dD), _ptr(dA), _ptr(dpos), _ptr(dcol),
-                                 _ptr(dopa), _ptr(dtau))
-        return dict(dpos=dpos, dcol=dcol, dopa=dopa, dtau=dtau)
+        self.lib.oracle_backward_ex(C.byref(sc), C.byref(p), _ptr(dC), _ptr(dD), _ptr(dA), _ptr(dpos), _ptr(dcol),
+                                    _ptr(dopa), _ptr(dtau), _ptr(dtau_abs))
+        return dict(dpos=dpos, dcol=dcol, dopa=dopa, dtau=dtau, dtau_abs=dtau_abs)
 
     def l1_loss(self, sa: SceneArrays, color, depth, tgt_color, tgt_depth, lambda_dep: float = 0.05):
         f = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731

@@ -648,17 +648,19 @@ int oracle_pixel_trace(const or_scene* sc, const or_params* p, int view, int x, 
 
 // Adjoint of Eq. 4 and Eq. 1-3 for the loss gradients dC, dD, dA (same packing
 // as the images).  Gradients are ADDED to dpos [N][3], dcol [N][3], dopa [N],
-// dtau [V][6] (rho then theta).
-int oracle_backward(const or_scene* sc, const or_params* p, const double* dC, const double* dD, const double* dA,
-                    double* dpos, double* dcol, double* dopa, double* dtau) {
+// dtau [V][6] (rho then theta).  dtau_abs (optional, [V][6]) receives the sum of the absolute
+// values of the per-(pixel, face) pose terms: the scale against which the cancelling sum dtau is
+// compared.
+int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC, const double* dD, const double* dA,
+                       double* dpos, double* dcol, double* dopa, double* dtau, double* dtau_abs) {
   Ctx c = make_ctx(sc, p);
   Bins b = make_bins(c);
   const int nt = threads_of(p);
   for (int v = 0; v < sc->n_views; ++v) {
     const View& w = c.views[v];
     const int64_t HW = (int64_t)w.W * w.H;
-    double tau_acc[6] = {0, 0, 0, 0, 0, 0};
-#pragma omp parallel for num_threads(nt) schedule(dynamic, 1) reduction(+ : tau_acc[:6])
+    double tau_acc[6] = {0, 0, 0, 0, 0, 0}, tau_abs[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1) reduction(+ : tau_acc[:6], tau_abs[:6])
     for (int y = 0; y < w.H; ++y) {
       std::vector<Contrib> list;
       for (int x = 0; x < w.W; ++x) {
@@ -716,13 +718,22 @@ int oracle_backward(const or_scene* sc, const or_params* p, const double* dC, co
               dopa[vi] += g[7 * kk + 6];
             }
           }
-          for (int i = 0; i < 6; ++i) tau_acc[i] += g[21 + i];
+          for (int i = 0; i < 6; ++i) {
+            tau_acc[i] += g[21 + i];
+            tau_abs[i] += std::fabs(g[21 + i]);
+          }
         }
       }
     }
     if (dtau) for (int i = 0; i < 6; ++i) dtau[6 * v + i] += tau_acc[i];
+    if (dtau_abs) for (int i = 0; i < 6; ++i) dtau_abs[6 * v + i] += tau_abs[i];
   }
   return 0;
+}
+
+int oracle_backward(const or_scene* sc, const or_params* p, const double* dC, const double* dD, const double* dA,
+                    double* dpos, double* dcol, double* dopa, double* dtau) {
+  return oracle_backward_ex(sc, p, dC, dD, dA, dpos, dcol, dopa, dtau, nullptr);
 }
 
 // L1 colour + depth loss (R11).  Returns the total over views; loss_v [V];

@@ -1,0 +1,154 @@
+// k_loss.cu -- the tracking/mapping loss of the raster path and the pose update.
+//
+// Loss (Eq. 8 L1 part and Eq. 9, per view): sum |C - Cbar| / (3HW) + lambda_dep *
+// sum_{Dbar > 0} |D - Dbar| / (HW), with its gradient written in the same pass; partial sums
+// per block are reduced in a fixed order so the loss is deterministic.
+// Pose update: T <- Exp(-step) o T with the closed-form SE(3) exponential (left perturbation,
+// step = (rho, theta)), used by gradient-descent tracking (Sec. 3.3).
+#include <algorithm>
+
+#include "ts_internal.cuh"
+
+namespace {
+
+constexpr int LOSS_T = 256;
+constexpr int LOSS_PER = 8;  // pixels per thread; 2048 per block
+
+__global__ void __launch_bounds__(LOSS_T) k_loss_partial(const TsView* __restrict__ views, const float* __restrict__ C,
+                                                         const float* __restrict__ D, const float* __restrict__ tC,
+                                                         const float* __restrict__ tD, float lambda_dep,
+                                                         float* __restrict__ dC, float* __restrict__ dD,
+                                                         float* __restrict__ part, int nblk) {
+  __shared__ float red[LOSS_T / 32][2];
+  const int v = blockIdx.y;
+  const TsView vw = views[v];
+  const long long HW = (long long)vw.W * vw.H;
+  const long long base = (long long)blockIdx.x * LOSS_T * LOSS_PER;
+  float lc = 0.f, ld = 0.f;
+  if (base < HW) {
+    const float ic = 1.0f / (3.0f * (float)HW), id = lambda_dep / (float)HW;
+#pragma unroll
+    for (int k = 0; k < LOSS_PER; ++k) {
+      const long long i = base + (long long)k * LOSS_T + threadIdx.x;
+      if (i >= HW) break;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const long long o = 3 * vw.pix_off + ch * HW + i;
+        const float r = C[o] - tC[o];
+        lc += fabsf(r);
+        dC[o] = r > 0.f ? ic : (r < 0.f ? -ic : 0.f);
+      }
+      const long long o = vw.pix_off + i;
+      const float t = tD[o];
+      const float r = D[o] - t;
+      const bool valid = t > 0.f;
+      if (valid) ld += fabsf(r);
+      dD[o] = valid ? (r > 0.f ? id : (r < 0.f ? -id : 0.f)) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lc += __shfl_xor_sync(0xffffffffu, lc, o);
+    ld += __shfl_xor_sync(0xffffffffu, ld, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = lc;
+    red[threadIdx.x >> 5][1] = ld;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < LOSS_T / 32; ++w) s += red[w][threadIdx.x];
+    part[((long long)v * nblk + blockIdx.x) * 2 + threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(LOSS_T) k_loss_final(const TsView* __restrict__ views, const float* __restrict__ part,
+                                                       int nblk, float lambda_dep, float* __restrict__ loss) {
+  __shared__ float red[LOSS_T][2];
+  const int v = blockIdx.x;
+  float a = 0.f, b = 0.f;
+  for (int k = threadIdx.x; k < nblk; k += LOSS_T) {
+    a += part[((long long)v * nblk + k) * 2];
+    b += part[((long long)v * nblk + k) * 2 + 1];
+  }
+  red[threadIdx.x][0] = a;
+  red[threadIdx.x][1] = b;
+  __syncthreads();
+  for (int o = LOSS_T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[threadIdx.x][0] += red[threadIdx.x + o][0];
+      red[threadIdx.x][1] += red[threadIdx.x + o][1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const TsView vw = views[v];
+    const double HW = (double)vw.W * vw.H;
+    loss[v] = (float)((double)red[0][0] / (3.0 * HW) + (double)lambda_dep * (double)red[0][1] / HW);
+  }
+}
+
+__global__ void k_pose_apply(ts_pose* poses, const float* __restrict__ step, int V) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const float* st = step + 6 * v;
+  const float rho[3] = {-st[0], -st[1], -st[2]};
+  const float w0 = -st[3], w1 = -st[4], w2 = -st[5];
+  const float a2 = w0 * w0 + w1 * w1 + w2 * w2;
+  const float a = sqrtf(a2);
+  float A, B, Cc;  // sin a / a, (1 - cos a) / a^2, (a - sin a) / a^3
+  if (a < 1e-3f) {
+    A = 1.f - a2 / 6.f;
+    B = 0.5f - a2 / 24.f;
+    Cc = 1.f / 6.f - a2 / 120.f;
+  } else {
+    const float sa = sinf(a), ca = cosf(a);
+    A = sa / a;
+    B = (1.f - ca) / a2;
+    Cc = (a - sa) / (a2 * a);
+  }
+  const float K[9] = {0.f, -w2, w1, w2, 0.f, -w0, -w1, w0, 0.f};
+  float K2[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+  float R[9], Vm[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float I3 = (i % 4 == 0) ? 1.f : 0.f;
+    R[i] = I3 + A * K[i] + B * K2[i];
+    Vm[i] = I3 + B * K[i] + Cc * K2[i];
+  }
+  float te[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) te[i] = Vm[3 * i] * rho[0] + Vm[3 * i + 1] * rho[1] + Vm[3 * i + 2] * rho[2];
+  ts_pose P = poses[v];
+  ts_pose Q;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Q.R[3 * i + j] = R[3 * i] * P.R[j] + R[3 * i + 1] * P.R[3 + j] + R[3 * i + 2] * P.R[6 + j];
+    Q.t[i] = R[3 * i] * P.t[0] + R[3 * i + 1] * P.t[1] + R[3 * i + 2] * P.t[2] + te[i];
+  }
+  poses[v] = Q;
+}
+
+}  // namespace
+
+cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* color, const float* depth,
+                              const float* tc, const float* td, float lambda_dep, float* loss, float* dC, float* dD,
+                              cudaStream_t s) {
+  const int nblk = (int)p->n_loss_blocks;
+  dim3 grid((unsigned)nblk, (unsigned)p->V);
+  k_loss_partial<<<grid, LOSS_T, 0, s>>>(w.views, color, depth, tc, td, lambda_dep, dC, dD, w.loss, nblk);
+  k_loss_final<<<p->V, LOSS_T, 0, s>>>(w.views, w.loss, nblk, lambda_dep, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t ts_launch_pose_apply(const TsPlanImpl* p, ts_pose* poses, const float* step, cudaStream_t s) {
+  k_pose_apply<<<(p->V + 63) / 64, 64, 0, s>>>(poses, step, p->V);
+  return cudaGetLastError();
+}

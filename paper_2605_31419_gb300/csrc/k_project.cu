@@ -1,0 +1,177 @@
+// k_project.cu -- Eq. 1-3 per (view, face): projection, culling and the screen-space record.
+//
+// One thread per (view, face), view-major so that a warp reads 32 consecutive faces' vertex
+// data (coalesced structure-of-arrays loads).  The projection, area, perimeter, inradius, face
+// opacity, pixel box and depth key follow one fixed FP32 operation order (no FMA contraction,
+// IEEE division and square root), so culling, tiles and depth keys are reproducible bit for bit.
+#include "ts_internal.cuh"
+
+namespace {
+
+struct MapArgs {
+  const float *px, *py, *pz, *cr, *cg, *cb, *op;
+  const int32_t* faces;
+  long long n_vertices;
+};
+
+__global__ void k_setup(TsViewTable tab, int V, MapArgs map, const ts_pose* __restrict__ poses, TsDevHeader* hdr,
+                        TsView* views, ts_pose* ws_poses) {
+  const int t = threadIdx.x;
+  for (int v = t; v < V; v += blockDim.x) {
+    views[v] = tab.v[v];
+    ws_poses[v] = poses[v];
+  }
+  if (t == 0) {
+    hdr->n_pairs = 0;
+    hdr->n_visible = 0;
+    hdr->fwd_contrib = 0;
+    hdr->bwd_contrib = 0;
+    hdr->indexed = map.faces ? 1u : 0u;
+    hdr->px = map.px; hdr->py = map.py; hdr->pz = map.pz;
+    hdr->cr = map.cr; hdr->cg = map.cg; hdr->cb = map.cb;
+    hdr->op = map.op;
+    hdr->faces = map.faces;
+    hdr->n_vertices = map.n_vertices;
+  }
+}
+
+struct ProjArgs {
+  MapArgs map;
+  const TsView* views;
+  const ts_pose* poses;
+  long long M;
+  long long VM;
+  float z_near, r_min, alpha_min;
+  int tile_w, tile_h;
+  float4* frec;
+  short4* rect;
+  uint32_t* zbits;
+  uint32_t* count;
+  TsDevHeader* hdr;
+};
+
+__global__ void __launch_bounds__(256) k_project(ProjArgs a) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool vis = false;
+  if (idx < a.VM) {
+    const int view = (int)(idx / a.M);
+    const long long m = idx - (long long)view * a.M;
+    const TsView vw = a.views[view];
+    const ts_pose P = a.poses[view];
+    long long vi[3];
+    if (a.map.faces) {
+      vi[0] = a.map.faces[3 * m]; vi[1] = a.map.faces[3 * m + 1]; vi[2] = a.map.faces[3 * m + 2];
+    } else {
+      vi[0] = 3 * m; vi[1] = 3 * m + 1; vi[2] = 3 * m + 2;
+    }
+    float u[3], v[3], z[3], o[3];
+    vis = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const long long j = vi[k];
+      if (j < 0 || j >= a.map.n_vertices) { vis = false; break; }
+      float xc, yc, zc;
+      ts_rigid_f32(P, __ldg(a.map.px + j), __ldg(a.map.py + j), __ldg(a.map.pz + j), xc, yc, zc);
+      if (!(zc > a.z_near)) { vis = false; break; }
+      ts_pinhole_f32(vw, xc, yc, zc, u[k], v[k]);
+      z[k] = zc;
+      o[k] = __ldg(a.map.op + j);
+    }
+    float area2 = 0.f, len[3] = {0.f, 0.f, 0.f}, per = 0.f, oF = 0.f;
+    if (vis) {
+      const float du1 = __fsub_rn(u[1], u[0]), dv1 = __fsub_rn(v[1], v[0]);
+      const float du2 = __fsub_rn(u[2], u[0]), dv2 = __fsub_rn(v[2], v[0]);
+      area2 = __fsub_rn(__fmul_rn(du1, dv2), __fmul_rn(du2, dv1));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3;
+        const float ex = __fsub_rn(u[j], u[i]), ey = __fsub_rn(v[j], v[i]);
+        len[i] = __fsqrt_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)));
+      }
+      per = __fadd_rn(__fadd_rn(len[0], len[1]), len[2]);
+      const float r = __fdiv_rn(fabsf(area2), per);
+      if (!(r >= a.r_min)) vis = false;
+      oF = __fdiv_rn(__fadd_rn(__fadd_rn(o[0], o[1]), o[2]), 3.0f);
+      if (oF < a.alpha_min) vis = false;
+    }
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    if (vis) {
+      const float umin = fminf(u[0], fminf(u[1], u[2])), umax = fmaxf(u[0], fmaxf(u[1], u[2]));
+      const float vmin = fminf(v[0], fminf(v[1], v[2])), vmax = fmaxf(v[0], fmaxf(v[1], v[2]));
+      const float fx0 = ceilf(__fsub_rn(umin, 0.5f)), fx1 = floorf(__fsub_rn(umax, 0.5f));
+      const float fy0 = ceilf(__fsub_rn(vmin, 0.5f)), fy1 = floorf(__fsub_rn(vmax, 0.5f));
+      const float Wm = (float)(vw.W - 1), Hm = (float)(vw.H - 1);
+      if (!(fx0 <= fx1) || fx1 < 0.0f || fx0 > Wm) vis = false;
+      if (!(fy0 <= fy1) || fy1 < 0.0f || fy0 > Hm) vis = false;
+      if (vis) {
+        x0 = fx0 < 0.0f ? 0 : (int)fx0;
+        x1 = fx1 > Wm ? vw.W - 1 : (int)fx1;
+        y0 = fy0 < 0.0f ? 0 : (int)fy0;
+        y1 = fy1 > Hm ? vw.H - 1 : (int)fy1;
+      }
+    }
+    if (vis) {
+      const float zk = __fdiv_rn(__fadd_rn(__fadd_rn(z[0], z[1]), z[2]), 3.0f);
+      a.zbits[idx] = __float_as_uint(zk);
+      // record: edge vectors, normalised edge-function scales s_i / D2, barycentric scale 1 / D2
+      const float e0x = u[1] - u[0], e0y = v[1] - v[0];
+      const float e1x = u[2] - u[1], e1y = v[2] - v[1];
+      const float e2x = u[0] - u[2], e2y = v[0] - v[2];
+      const float invD = 1.0f / area2;
+      const float k0 = (per / len[0]) * invD, k1 = (per / len[1]) * invD, k2 = (per / len[2]) * invD;
+      float4* rec = a.frec + idx * (TS_REC_WORDS / 4);
+      const long long j0 = vi[0], j1 = vi[1], j2 = vi[2];
+      rec[0] = make_float4(u[0], u[1], u[2], v[0]);
+      rec[1] = make_float4(v[1], v[2], e0x, e0y);
+      rec[2] = make_float4(e1x, e1y, e2x, e2y);
+      rec[3] = make_float4(k0, k1, k2, invD);
+      rec[4] = make_float4(oF, __ldg(a.map.cr + j0), __ldg(a.map.cg + j0), __ldg(a.map.cb + j0));
+      rec[5] = make_float4(__ldg(a.map.cr + j1), __ldg(a.map.cg + j1), __ldg(a.map.cb + j1), __ldg(a.map.cr + j2));
+      rec[6] = make_float4(__ldg(a.map.cg + j2), __ldg(a.map.cb + j2), z[0], z[1]);
+      rec[7] = make_float4(z[2], __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
+                           __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)idx));
+      const int tx0 = x0 / a.tile_w, tx1 = x1 / a.tile_w, ty0 = y0 / a.tile_h, ty1 = y1 / a.tile_h;
+      a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
+      a.count[idx] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    } else {
+      a.rect[idx] = make_short4(-1, -1, -1, -1);
+      a.count[idx] = 0u;
+    }
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, vis);
+  if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&a.hdr->n_visible, (unsigned long long)__popc(ball));
+}
+
+}  // namespace
+
+cudaError_t ts_launch_setup(const TsPlanImpl* p, const TsWs& w, const ts_map* map, const ts_pose* poses,
+                            cudaStream_t s) {
+  TsViewTable local;  // passed by value: capture-safe, no host-to-device copy
+  for (int v = 0; v < p->V; ++v) local.v[v] = p->views[v];
+  MapArgs m{map->px, map->py, map->pz, map->cr, map->cg, map->cb, map->op, map->faces, map->n_vertices};
+  k_setup<<<1, 256, 0, s>>>(local, p->V, m, poses, w.hdr, w.views, w.poses);
+  return cudaGetLastError();
+}
+
+cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* map, cudaStream_t s) {
+  const long long VM = (long long)p->V * p->M;
+  if (VM == 0) return cudaSuccess;
+  ProjArgs a;
+  a.map = MapArgs{map->px, map->py, map->pz, map->cr, map->cg, map->cb, map->op, map->faces, map->n_vertices};
+  a.views = w.views;
+  a.poses = w.poses;
+  a.M = p->M;
+  a.VM = VM;
+  a.z_near = p->prm.z_near;
+  a.r_min = p->prm.r_min;
+  a.alpha_min = p->prm.alpha_min;
+  a.tile_w = p->prm.tile_w;
+  a.tile_h = p->prm.tile_h;
+  a.frec = w.frec;
+  a.rect = w.rect;
+  a.zbits = w.zbits;
+  a.count = w.count;
+  a.hdr = w.hdr;
+  k_project<<<(unsigned)((VM + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}

@@ -1,0 +1,438 @@
+// k_render.cu -- Eq. 3-4 forward blend and its adjoint, one CTA per (view, tile).
+//
+// Staging: the tile's depth-sorted face ids select 128-byte records that one warp copies into
+// shared memory with TMA bulk copies (cp.async.bulk, one per record) completing on an mbarrier;
+// two buffers alternate so the next stage streams in while the current one is blended.  Each
+// warp owns an 8 x 4 pixel sub-block of the tile; a per-record bit mask (computed once per
+// stage from the face's pixel box) lets a warp skip faces that cannot reach its sub-block with a
+// single uniform branch.
+//
+// Forward: per pixel, front to back: window (Eq. 3) from cancellation-free edge functions,
+// alpha = min(alpha_max, o_F I), skip below alpha_min, stop before the face that would take T
+// below T_min, accumulate colour, depth and opacity (Eq. 4).  Writes C + T bg, D, A = 1 - T, and
+// per pixel T_final and the list position after the last contribution.
+//
+// Backward: per pixel, back to front from that position: recover T_n = T_{n+1} / (1 - alpha_n),
+// keep the suffix sum S of later contributions (including the background term), form
+// dL/dalpha_n = T_n v_n - S / (1 - alpha_n) with v_n = gC . c_n + gD z_n + gA, and chain into 22
+// per-face sums (barycentric-weighted gradients of the edge, colour and depth interpolants, and
+// of o_F).  A warp reduces the 24-word vector with a 27-shuffle reduce-scatter, leaving one sum
+// per lane, and issues a single 24-lane atomic add into the face's accumulator.
+#include <algorithm>
+
+#include "ts_internal.cuh"
+
+namespace {
+
+struct RenderArgs {
+  const TsView* views;
+  int V;
+  long long M, VM;
+  const float4* frec;
+  const uint32_t* ids;
+  const uint2* ranges;
+  float* color;
+  float* depth;
+  float* alpha;
+  float* tfin;
+  int32_t* nlast;
+  const float* dC;
+  const float* dD;
+  const float* dA;
+  float* grad;
+  float sigma, alpha_min, alpha_max, T_min;
+  float bg0, bg1, bg2;
+  int S;
+  TsDevHeader* hdr;
+};
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <int TW, int TH>
+struct TileGeom {
+  static constexpr int NT = TW * TH;
+  static constexpr int NSBX = TW / 8;
+  int view, X0, Y0, x, y;
+  bool inimg;
+  float px, py;
+  TsView vw;
+};
+
+template <int TW, int TH>
+__device__ __forceinline__ TileGeom<TW, TH> tile_geom(const RenderArgs& a, int* s_view) {
+  TileGeom<TW, TH> g;
+  const long long tile = blockIdx.x;
+  if (threadIdx.x == 0) *s_view = ts_find_view(a.views, a.V, tile);
+  __syncthreads();
+  g.view = *s_view;
+  g.vw = a.views[g.view];
+  const long long lt = tile - g.vw.tile_off;
+  const int ty = (int)(lt / g.vw.TX), tx = (int)(lt - (long long)ty * g.vw.TX);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  g.X0 = tx * TW;
+  g.Y0 = ty * TH;
+  g.x = g.X0 + (warp % TileGeom<TW, TH>::NSBX) * 8 + (lane & 7);
+  g.y = g.Y0 + (warp / TileGeom<TW, TH>::NSBX) * 4 + (lane >> 3);
+  g.inimg = g.x < g.vw.W && g.y < g.vw.H;
+  g.px = (float)g.x + 0.5f;
+  g.py = (float)g.y + 0.5f;
+  return g;
+}
+
+// Warp 0 issues the bulk copies of stage `st` (records [st*S, st*S + cnt) of the tile's list)
+// into buffer `b`.
+__device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, uint64_t* bar, int b, int st,
+                                            uint32_t start, int n, const float4* vbase) {
+  const int lane = threadIdx.x & 31;
+  const int S = a.S;
+  const int cnt = min(S, n - st * S);
+  if (lane == 0) ts_mbar_arrive_expect_tx(&bar[b], (uint32_t)cnt * 128u);
+  __syncwarp();
+  for (int j = lane; j < cnt; j += 32) {
+    uint32_t id = __ldg(a.ids + start + (uint32_t)(st * S + j));
+    if ((long long)id >= a.M) {  // never expected: record the fault and stage an in-bounds record
+      atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
+      id = 0;
+    }
+    ts_bulk_g2s(smrec + ((size_t)b * S + j) * 8, vbase + (size_t)id * 8, 128u, &bar[b]);
+  }
+}
+
+// Replace each staged record's pixel-box word by the mask of warp sub-blocks it overlaps.
+template <int TW, int TH>
+__device__ __forceinline__ void stage_masks(float* rb, int cnt, int X0, int Y0) {
+  constexpr int NSBX = TW / 8;
+  for (int j = threadIdx.x; j < cnt; j += TW * TH) {
+    float* r = rb + j * TS_REC_WORDS;
+    const uint32_t bx = __float_as_uint(r[R_BOXX]), by = __float_as_uint(r[R_BOXY]);
+    const int x0 = (int)(bx & 0xffffu) - X0, x1 = (int)(bx >> 16) - X0;
+    const int y0 = (int)(by & 0xffffu) - Y0, y1 = (int)(by >> 16) - Y0;
+    uint32_t mask = 0;
+    if (x1 >= 0 && x0 < TW && y1 >= 0 && y0 < TH) {
+      const int c0 = max(x0, 0) >> 3, c1 = min(x1, TW - 1) >> 3;
+      const int r0 = max(y0, 0) >> 2, r1 = min(y1, TH - 1) >> 2;
+      const uint32_t cols = ((2u << c1) - 1u) & ~((1u << c0) - 1u);
+      for (int rr = r0; rr <= r1; ++rr) mask |= cols << (rr * NSBX);
+    }
+    r[R_MASK] = __uint_as_float(mask);
+  }
+}
+
+__device__ __forceinline__ void count_add(unsigned long long* ctr, unsigned v) {
+  const unsigned s = __reduce_add_sync(FULL, v);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
+  constexpr int NT = TW * TH;
+  extern __shared__ __align__(128) float4 smrec[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_view;
+  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, &s_view);
+  const int warp = threadIdx.x >> 5;
+  const uint2 rg = a.ranges[blockIdx.x];
+  const int n = (int)(rg.y - rg.x);
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+  int nl = 0;
+  bool done = !g.inimg;
+  unsigned contrib = 0;
+  if (n > 0) {
+    const int S = a.S;
+    const int nst = (n + S - 1) / S;
+    const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
+    if (threadIdx.x == 0) {
+      ts_mbar_init(&bar[0], 1);
+      ts_mbar_init(&bar[1], 1);
+      ts_fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) issue_stage(a, smrec, bar, 0, 0, rg.x, n, vbase);
+    for (int st = 0; st < nst; ++st) {
+      const int b = st & 1;
+      const int cnt = min(S, n - st * S);
+      const bool ok = ts_mbar_wait(&bar[b], (uint32_t)(st >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          atomicOr(&a.hdr->error_bits, TS_ERRBIT_TIMEOUT);
+          ts_mbar_wait(&bar[b], (uint32_t)(st >> 1) & 1u);  // let the late copies land before leaving
+        }
+        return;
+      }
+      float* rb = reinterpret_cast<float*>(smrec + (size_t)b * S * 8);
+      stage_masks<TW, TH>(rb, cnt, g.X0, g.Y0);
+      __syncthreads();
+      if (warp == 0 && st + 1 < nst) issue_stage(a, smrec, bar, b ^ 1, st + 1, rg.x, n, vbase);
+      for (int j = 0; j < cnt; ++j) {
+        const float* r = rb + j * TS_REC_WORDS;
+        if (!((__float_as_uint(r[R_MASK]) >> warp) & 1u)) continue;  // warp-uniform
+        if (done) continue;
+        const TsPix e = ts_eval_edges(r, g.px, g.py);
+        if (!(e.m > 0.f)) continue;
+        const float I = ts_window(e.m, a.sigma);
+        const float al = fminf(r[R_OF] * I, a.alpha_max);
+        if (al < a.alpha_min) continue;
+        const float Tn = T * (1.f - al);
+        if (Tn < a.T_min) { done = true; continue; }
+        const float invD = r[R_INVD];
+        const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
+        const float w = al * T;
+        C0 += w * (l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2]);
+        C1 += w * (l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1]);
+        C2 += w * (l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2]);
+        D += w * (l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2]);
+        T = Tn;
+        nl = st * S + j + 1;
+        ++contrib;
+      }
+      if (__syncthreads_count(!done) == 0) {
+        if (threadIdx.x == 0 && st + 1 < nst) {
+          if (!ts_mbar_wait(&bar[b ^ 1], (uint32_t)((st + 1) >> 1) & 1u)) atomicOr(&a.hdr->error_bits, TS_ERRBIT_TIMEOUT);
+        }
+        break;
+      }
+    }
+  }
+  count_add(&a.hdr->fwd_contrib, contrib);
+  if (g.inimg) {
+    const long long HW = (long long)g.vw.W * g.vw.H;
+    const long long pi = (long long)g.y * g.vw.W + g.x;
+    const long long o = g.vw.pix_off + pi;
+    if (a.color) {
+      float* c = a.color + 3 * g.vw.pix_off + pi;
+      c[0] = C0 + T * a.bg0;
+      c[HW] = C1 + T * a.bg1;
+      c[2 * HW] = C2 + T * a.bg2;
+    }
+    if (a.depth) a.depth[o] = D;
+    if (a.alpha) a.alpha[o] = 1.f - T;
+    a.tfin[o] = T;
+    a.nlast[o] = nl;
+  }
+  (void)NT;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
+  extern __shared__ __align__(128) float4 smrec[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_view;
+  __shared__ int s_nmax;
+  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, &s_view);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint2 rg = a.ranges[blockIdx.x];
+  float T = 0.f, Sacc = 0.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
+  int nl = 0;
+  if (g.inimg) {
+    const long long HW = (long long)g.vw.W * g.vw.H;
+    const long long pi = (long long)g.y * g.vw.W + g.x;
+    const long long o = g.vw.pix_off + pi;
+    T = a.tfin[o];
+    nl = a.nlast[o];
+    const float* dc = a.dC + 3 * g.vw.pix_off + pi;
+    gC0 = dc[0];
+    gC1 = dc[HW];
+    gC2 = dc[2 * HW];
+    gD = a.dD ? a.dD[o] : 0.f;
+    gA = a.dA ? a.dA[o] : 0.f;
+    Sacc = T * (gC0 * a.bg0 + gC1 * a.bg1 + gC2 * a.bg2);
+  }
+  if (threadIdx.x == 0) s_nmax = 0;
+  __syncthreads();
+  {
+    const int m = __reduce_max_sync(FULL, (unsigned)nl);
+    if (lane == 0 && m) atomicMax(&s_nmax, m);
+  }
+  __syncthreads();
+  // positions come from the forward pass over the same lists; clamp in case the caller did not
+  // run it after the last ts_bin
+  const int n = min(s_nmax, (int)(rg.y - rg.x));
+  unsigned contrib = 0;
+  if (n > 0) {
+    const int S = a.S;
+    const int nst = (n + S - 1) / S;
+    const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
+    if (threadIdx.x == 0) {
+      ts_mbar_init(&bar[0], 1);
+      ts_mbar_init(&bar[1], 1);
+      ts_fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) issue_stage(a, smrec, bar, 0, nst - 1, rg.x, n, vbase);
+    const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
+    const int q = lane & 3;
+    const int widx = (hi16 ? 12 : 0) + (hi8 ? 6 : 0) + (hi4 ? 3 : 0) + q;
+    for (int k = 0; k < nst; ++k) {
+      const int st = nst - 1 - k;
+      const int b = k & 1;
+      const int cnt = min(S, n - st * S);
+      const bool ok = ts_mbar_wait(&bar[b], (uint32_t)(k >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          atomicOr(&a.hdr->error_bits, TS_ERRBIT_TIMEOUT);
+          ts_mbar_wait(&bar[b], (uint32_t)(k >> 1) & 1u);  // let the late copies land before leaving
+        }
+        return;
+      }
+      float* rb = reinterpret_cast<float*>(smrec + (size_t)b * S * 8);
+      stage_masks<TW, TH>(rb, cnt, g.X0, g.Y0);
+      __syncthreads();
+      if (warp == 0 && k + 1 < nst) issue_stage(a, smrec, bar, b ^ 1, st - 1, rg.x, n, vbase);
+      for (int j = cnt - 1; j >= 0; --j) {
+        const float* r = rb + j * TS_REC_WORDS;
+        if (!((__float_as_uint(r[R_MASK]) >> warp) & 1u)) continue;  // warp-uniform
+        const int pos = st * S + j;
+        bool cb = false;
+        TsPix e;
+        float I = 0.f, al = 0.f;
+        if (pos < nl) {
+          e = ts_eval_edges(r, g.px, g.py);
+          if (e.m > 0.f) {
+            I = ts_window(e.m, a.sigma);
+            al = fminf(r[R_OF] * I, a.alpha_max);
+            cb = al >= a.alpha_min;
+          }
+        }
+        if (!__any_sync(FULL, cb)) continue;
+        float v[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) v[i] = 0.f;
+        if (cb) {
+          const float oma = 1.f - al;
+          const float Tn = T / oma;
+          const float invD = r[R_INVD];
+          const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
+          const float c0 = l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2];
+          const float c1 = l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1];
+          const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
+          const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
+          const float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
+          const float dal = val * Tn - Sacc / oma;
+          Sacc += val * al * Tn;
+          T = Tn;
+          const float w = al * Tn;
+          const float w0 = gC0 * w, w1 = gC1 * w, w2 = gC2 * w, wz = gD * w;
+          v[G_C + 0] = w0 * l0; v[G_C + 1] = w0 * l1; v[G_C + 2] = w0 * l2;
+          v[G_C + 3] = w1 * l0; v[G_C + 4] = w1 * l1; v[G_C + 5] = w1 * l2;
+          v[G_C + 6] = w2 * l0; v[G_C + 7] = w2 * l1; v[G_C + 8] = w2 * l2;
+          v[G_Z + 0] = wz * l0; v[G_Z + 1] = wz * l1; v[G_Z + 2] = wz * l2;
+          v[G_CNT] = 1.f;
+          const float oF = r[R_OF];
+          if (!(oF * I > a.alpha_max)) {
+            v[G_O] = dal * I;
+            const float dI = dal * oF;
+            const float dm = (a.sigma == 0.5f) ? dI * 0.5f / I : dI * a.sigma * I / e.m;
+            const float d0 = dm * l0, d1 = dm * l1, d2 = dm * l2;
+            v[G_E + 0] = e.arg == 0 ? d0 : 0.f; v[G_E + 1] = e.arg == 0 ? d1 : 0.f; v[G_E + 2] = e.arg == 0 ? d2 : 0.f;
+            v[G_E + 3] = e.arg == 1 ? d0 : 0.f; v[G_E + 4] = e.arg == 1 ? d1 : 0.f; v[G_E + 5] = e.arg == 1 ? d2 : 0.f;
+            v[G_E + 6] = e.arg == 2 ? d0 : 0.f; v[G_E + 7] = e.arg == 2 ? d1 : 0.f; v[G_E + 8] = e.arg == 2 ? d2 : 0.f;
+          }
+          ++contrib;
+        }
+        // reduce-scatter: 24 -> 12 -> 6 -> 3 values per lane, then a butterfly over 4 lanes
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+          const float send = hi16 ? v[i] : v[i + 12];
+          const float keep = hi16 ? v[i + 12] : v[i];
+          v[i] = keep + __shfl_xor_sync(FULL, send, 16);
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const float send = hi8 ? v[i] : v[i + 6];
+          const float keep = hi8 ? v[i + 6] : v[i];
+          v[i] = keep + __shfl_xor_sync(FULL, send, 8);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float send = hi4 ? v[i] : v[i + 3];
+          const float keep = hi4 ? v[i + 3] : v[i];
+          v[i] = keep + __shfl_xor_sync(FULL, send, 4);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          v[i] += __shfl_xor_sync(FULL, v[i], 2);
+          v[i] += __shfl_xor_sync(FULL, v[i], 1);
+        }
+        const float mine = q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
+        if (q < 3 && mine != 0.f) {
+          const uint32_t slot = __float_as_uint(r[R_SLOT]);
+          if ((long long)slot < a.VM) {
+            atomicAdd(a.grad + (size_t)slot * TS_GRAD_WORDS + widx, mine);
+          } else {
+            atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
+          }
+        }
+      }
+    }
+  }
+  count_add(&a.hdr->bwd_contrib, contrib);
+}
+
+template <int TW, int TH>
+cudaError_t launch_pair(bool fwd, const RenderArgs& a, long long n_tiles, cudaStream_t s) {
+  const size_t smem = (size_t)2 * a.S * 128;
+  if (n_tiles == 0) return cudaSuccess;
+  if (fwd) {
+    k_render_fwd<TW, TH><<<(unsigned)n_tiles, TW * TH, smem, s>>>(a);
+  } else {
+    k_render_bwd<TW, TH><<<(unsigned)n_tiles, TW * TH, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch(bool fwd, const TsPlanImpl* p, const RenderArgs& a, cudaStream_t s) {
+  const int tw = p->prm.tile_w, th = p->prm.tile_h;
+  if (tw == 16 && th == 16) return launch_pair<16, 16>(fwd, a, p->n_tiles, s);
+  if (tw == 8 && th == 8) return launch_pair<8, 8>(fwd, a, p->n_tiles, s);
+  if (tw == 16 && th == 8) return launch_pair<16, 8>(fwd, a, p->n_tiles, s);
+  if (tw == 32 && th == 8) return launch_pair<32, 8>(fwd, a, p->n_tiles, s);
+  if (tw == 16 && th == 32) return launch_pair<16, 32>(fwd, a, p->n_tiles, s);
+  if (tw == 32 && th == 16) return launch_pair<32, 16>(fwd, a, p->n_tiles, s);
+  return cudaErrorInvalidValue;
+}
+
+RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
+  RenderArgs a;
+  a.views = w.views;
+  a.V = p->V;
+  a.M = p->M;
+  a.VM = (long long)p->V * p->M;
+  a.frec = w.frec;
+  a.ids = w.vals[ts_sort_final_buffer(p)];
+  a.ranges = w.ranges;
+  a.color = a.depth = a.alpha = nullptr;
+  a.tfin = w.tfin;
+  a.nlast = w.nlast;
+  a.dC = a.dD = a.dA = nullptr;
+  a.grad = w.grad;
+  a.sigma = p->prm.sigma;
+  a.alpha_min = p->prm.alpha_min;
+  a.alpha_max = p->prm.alpha_max;
+  a.T_min = p->prm.T_min;
+  a.bg0 = p->prm.bg[0];
+  a.bg1 = p->prm.bg[1];
+  a.bg2 = p->prm.bg[2];
+  a.S = p->prm.tris_per_stage;
+  a.hdr = w.hdr;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t ts_launch_render_fwd(const TsPlanImpl* p, const TsWs& w, float* color, float* depth, float* alpha,
+                                 cudaStream_t s) {
+  RenderArgs a = base_args(p, w);
+  a.color = color;
+  a.depth = depth;
+  a.alpha = alpha;
+  return dispatch(true, p, a, s);
+}
+
+cudaError_t ts_launch_render_bwd(const TsPlanImpl* p, const TsWs& w, const float* dC, const float* dD,
+                                 const float* dA, cudaStream_t s) {
+  RenderArgs a = base_args(p, w);
+  a.dC = dC;
+  a.dD = dD;
+  a.dA = dA;
+  return dispatch(false, p, a, s);
+}

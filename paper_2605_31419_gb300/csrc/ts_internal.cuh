@@ -1,0 +1,272 @@
+// ts_internal.cuh -- internal declarations shared by libts translation units (sm_103a).
+//
+// Layout of the device workspace, the per-(view, face) screen-space record, the host plan, and
+// the device helpers every kernel uses: the fixed-order FP32 projection (Eq. 1), the
+// cancellation-free edge functions (Eq. 2-3), the TMA bulk copy with an mbarrier, and bounded
+// waits that report a timeout instead of hanging.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ts_api.h"
+
+#define TS_PLAN_MAGIC 0x54535031u  // "TSP1"
+#define TS_REC_WORDS 32            // 128-byte record, a multiple of 16 B for cp.async.bulk
+#define TS_GRAD_WORDS 24           // per-(view, face) gradient accumulator
+#define TS_SCAN_ITEMS 4096         // items per scan block (1024 threads x 4)
+#define TS_SORT_ITEMS 4096         // keys per radix-sort block (256 threads x 16)
+#define TS_SORT_THREADS 256
+#define TS_ERRBIT_CAPACITY 1u
+#define TS_ERRBIT_TIMEOUT 2u
+#define TS_ERRBIT_BOUNDS 4u  // an index failed its bounds check (the access was skipped)
+
+// Record word indices.  u, v: projected vertices (pixels, FP32 as produced by Eq. 1 in the fixed
+// op order); e_i = q_{i+1} - q_i; k_i = s_i / D2 with s_i = perimeter / |e_i| and D2 twice the
+// signed area, so that E_i(p) = k_i * cross(e_i, p - q_i) = s_i * lambda_{i+2}(p) is the edge
+// function normalised to 1 at the incentre (E_i = phi-ratio of Eq. 3 where edge i is nearest);
+// invD = 1 / D2 gives the barycentrics lambda_{i+2} = cross_i * invD; oF the face opacity;
+// c the vertex colours; z the camera-space vertex depths; box the pixel box (x0 | x1 << 16,
+// y0 | y1 << 16); slot = view * M + face.
+enum {
+  R_U0 = 0, R_U1, R_U2, R_V0, R_V1, R_V2,
+  R_E0X, R_E0Y, R_E1X, R_E1Y, R_E2X, R_E2Y,
+  R_K0, R_K1, R_K2, R_INVD,
+  R_OF, R_C0 = 17, R_C1 = 20, R_C2 = 23, R_Z0 = 26, R_Z1, R_Z2,
+  R_BOXX = 29, R_BOXY = 30, R_SLOT = 31
+};
+// In shared memory the render kernels overwrite R_BOXY with the per-warp sub-block mask.
+#define R_MASK R_BOXY
+
+// Gradient word indices: G_E[i][k] = sum_p dL/dE_i * lambda_k (edge i nearest), G_c[ch][k] =
+// sum_p dL/dc_ch * lambda_k, G_z[k] = sum_p dL/dz * lambda_k, G_o = dL/do_F, count = pixels.
+enum { G_E = 0, G_C = 9, G_Z = 18, G_O = 21, G_CNT = 22 };
+
+struct TsView {
+  float fx, fy, cx, cy;
+  int32_t W, H, TX, TY;
+  int64_t tile_off, pix_off;
+};  // 48 bytes
+
+struct TsViewTable {
+  TsView v[TS_MAX_VIEWS];
+};
+
+// Device-side header at the start of the workspace.
+struct TsDevHeader {
+  unsigned long long n_pairs;
+  unsigned long long n_visible;
+  unsigned long long fwd_contrib;
+  unsigned long long bwd_contrib;
+  unsigned int error_bits;
+  unsigned int indexed;
+  const float *px, *py, *pz, *cr, *cg, *cb, *op;
+  const int32_t* faces;
+  long long n_vertices;
+  unsigned int pad[14];
+};
+
+struct TsPlanImpl {
+  uint32_t magic;
+  int32_t V;
+  int64_t M;
+  int64_t cap;
+  ts_raster_params prm;
+  int64_t n_tiles, n_pix;
+  int32_t tile_bits, sort_passes;
+  int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks;
+  // workspace layout (byte offsets)
+  size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
+      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, total;
+  void* events[2 * TS_N_STAGES];
+  int32_t timing;
+  TsView views[TS_MAX_VIEWS];
+};
+static_assert(sizeof(TsPlanImpl) <= TS_PLAN_BYTES, "plan too large");
+
+// Pointers into one workspace.
+struct TsWs {
+  TsDevHeader* hdr;
+  TsView* views;
+  ts_pose* poses;
+  float4* frec;
+  short4* rect;
+  uint32_t* zbits;
+  uint32_t* count;
+  uint32_t* offs;
+  uint32_t* bsums;
+  unsigned long long* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;
+  uint32_t* hsums;
+  uint2* ranges;
+  float* tfin;
+  int32_t* nlast;
+  float* grad;
+  float* pose;
+  float* loss;
+};
+
+inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
+  char* b = (char*)ws;
+  TsWs w;
+  w.hdr = (TsDevHeader*)(b + p->o_hdr);
+  w.views = (TsView*)(b + p->o_views);
+  w.poses = (ts_pose*)(b + p->o_poses);
+  w.frec = (float4*)(b + p->o_frec);
+  w.rect = (short4*)(b + p->o_rect);
+  w.zbits = (uint32_t*)(b + p->o_zbits);
+  w.count = (uint32_t*)(b + p->o_count);
+  w.offs = (uint32_t*)(b + p->o_offs);
+  w.bsums = (uint32_t*)(b + p->o_bsums);
+  w.keys[0] = (unsigned long long*)(b + p->o_keys0);
+  w.keys[1] = (unsigned long long*)(b + p->o_keys1);
+  w.vals[0] = (uint32_t*)(b + p->o_vals0);
+  w.vals[1] = (uint32_t*)(b + p->o_vals1);
+  w.hist = (uint32_t*)(b + p->o_hist);
+  w.hsums = (uint32_t*)(b + p->o_hsums);
+  w.ranges = (uint2*)(b + p->o_ranges);
+  w.tfin = (float*)(b + p->o_tfin);
+  w.nlast = (int32_t*)(b + p->o_nlast);
+  w.grad = (float*)(b + p->o_grad);
+  w.pose = (float*)(b + p->o_pose);
+  w.loss = (float*)(b + p->o_loss);
+  return w;
+}
+
+// ------------------------------------------------------------------------------------------
+// Launchers (one per translation unit); each returns cudaGetLastError() of its launches.
+// ------------------------------------------------------------------------------------------
+cudaError_t ts_launch_setup(const TsPlanImpl* p, const TsWs& w, const ts_map* map, const ts_pose* poses,
+                            cudaStream_t s);
+cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* map, cudaStream_t s);
+cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s);
+cudaError_t ts_launch_render_fwd(const TsPlanImpl* p, const TsWs& w, float* color, float* depth, float* alpha,
+                                 cudaStream_t s);
+cudaError_t ts_launch_render_bwd(const TsPlanImpl* p, const TsWs& w, const float* dC, const float* dD,
+                                 const float* dA, cudaStream_t s);
+cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_map_grad* g, cudaStream_t s);
+cudaError_t ts_launch_pose_reduce(const TsPlanImpl* p, const TsWs& w, float* dtau, cudaStream_t s);
+cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* color, const float* depth,
+                              const float* tc, const float* td, float lambda_dep, float* loss, float* dC,
+                              float* dD, cudaStream_t s);
+cudaError_t ts_launch_pose_apply(const TsPlanImpl* p, ts_pose* poses, const float* step, cudaStream_t s);
+int ts_sort_final_buffer(const TsPlanImpl* p);  // 0 or 1: which key/val buffer holds the sorted pairs
+
+// ------------------------------------------------------------------------------------------
+// Device helpers
+// ------------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ int ts_find_view(const TsView* views, int V, long long tile) {
+  int lo = 0, hi = V - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (views[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Camera-space vertex in the fixed FP32 operation order (Eq. 1, one rounding per operation,
+// no FMA): x_c = ((R0 x + R1 y) + R2 z) + t0, likewise y_c, z_c.
+__device__ __forceinline__ void ts_rigid_f32(const ts_pose& P, float x, float y, float z, float& xc, float& yc,
+                                             float& zc) {
+  xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P.R[0], x), __fmul_rn(P.R[1], y)), __fmul_rn(P.R[2], z)), P.t[0]);
+  yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P.R[3], x), __fmul_rn(P.R[4], y)), __fmul_rn(P.R[5], z)), P.t[1]);
+  zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P.R[6], x), __fmul_rn(P.R[7], y)), __fmul_rn(P.R[8], z)), P.t[2]);
+}
+
+// Pinhole projection in the fixed order: u = (fx * (x_c / z_c)) + cx.
+__device__ __forceinline__ void ts_pinhole_f32(const TsView& v, float xc, float yc, float zc, float& u, float& w) {
+  u = __fadd_rn(__fmul_rn(v.fx, __fdiv_rn(xc, zc)), v.cx);
+  w = __fadd_rn(__fmul_rn(v.fy, __fdiv_rn(yc, zc)), v.cy);
+}
+
+// a*d - b*c with a single rounding error (Kahan's FMA algorithm).  With exact inputs the
+// edge cross products keep full relative accuracy near the edge, where the window's slope
+// is largest (sigma = 0.5 gives an infinite derivative at the boundary).
+__device__ __forceinline__ float ts_det2(float a, float b, float c, float d) {
+  const float w = b * c;
+  const float e = fmaf(-b, c, w);
+  const float f = fmaf(a, d, -w);
+  return f + e;
+}
+
+// Per-pixel evaluation of one staged record: barycentric cross products, normalised edge
+// functions and their minimum (the ratio phi(p) / phi(s) of Eq. 3).
+struct TsPix {
+  float cr0, cr1, cr2;  // cross(e_i, p - q_i)
+  float m;              // min_i E_i
+  int arg;              // argmin
+};
+
+__device__ __forceinline__ TsPix ts_eval_edges(const float* r, float px, float py) {
+  TsPix o;
+  o.cr0 = ts_det2(r[R_E0X], r[R_E0Y], px - r[R_U0], py - r[R_V0]);
+  o.cr1 = ts_det2(r[R_E1X], r[R_E1Y], px - r[R_U1], py - r[R_V1]);
+  o.cr2 = ts_det2(r[R_E2X], r[R_E2Y], px - r[R_U2], py - r[R_V2]);
+  const float e0 = o.cr0 * r[R_K0], e1 = o.cr1 * r[R_K1], e2 = o.cr2 * r[R_K2];
+  o.m = e0;
+  o.arg = 0;
+  if (e1 < o.m) { o.m = e1; o.arg = 1; }
+  if (e2 < o.m) { o.m = e2; o.arg = 2; }
+  return o;
+}
+
+// Eq. 3 window: I = ratio^sigma for ratio > 0.
+__device__ __forceinline__ float ts_window(float m, float sigma) {
+  if (sigma == 0.5f) return sqrtf(m);
+  return exp2f(sigma * __log2f(m));
+}
+
+__device__ __forceinline__ uint32_t ts_smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ts_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ts_smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void ts_fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void ts_mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ts_smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One TMA bulk copy global -> shared, completing on an mbarrier (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void ts_bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          ts_smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(ts_smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t ts_globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after ~limit_ns nanoseconds.  Returns
+// false on timeout (the caller latches TS_ERRBIT_TIMEOUT and leaves).
+__device__ __forceinline__ bool ts_mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = 2000000000ull) {
+  const uint32_t a = ts_smem_u32(bar);
+  uint32_t done = 0;
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it == 0) t0 = ts_globaltimer();
+    else if ((it & 63) == 0 && ts_globaltimer() - t0 > limit_ns) return false;
+  }
+}
+
+#endif  // __CUDACC__

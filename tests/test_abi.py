@@ -1,0 +1,94 @@
+"""libts builds, loads without a GPU and exports every entry point include/ts_api.h declares;
+host-side plan logic and argument validation (no device work)."""
+import json
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ts_api.h")
+
+
+@pytest.fixture(scope="module")
+def ts():
+    from paper_2605_31419_gb300 import _build
+    _build.build()
+    import paper_2605_31419_gb300 as ts
+    return ts
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+(ts_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(ts):
+    names = declared_functions()
+    assert len(names) >= 16, names
+    out = subprocess.run(["nm", "-D", "--defined-only", ts.binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (ts_[a-z0-9_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    # and the Python binding declares the same set with the same names
+    assert set(names) == set(ts.binding.SIGNATURES), set(names) ^ set(ts.binding.SIGNATURES)
+    for n in names:
+        getattr(ts.binding.lib(), n)
+
+
+def test_default_params_match_paper(ts):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    p = ts.ts_default_params()
+    assert p.sigma == g["sigma"]["value"]
+    assert (p.tile_w, p.tile_h, p.tris_per_stage) == (16, 16, 64)
+
+
+def test_plan_layout_and_workspace(ts):
+    cams = np.array([[150, 150, 80, 60, 160, 120], [40, 40, 28.5, 16.5, 57, 33]])
+    plan = ts.ts_plan_init(cams, 2000, ts.ts_default_params())
+    lay = ts.ts_plan_layout(plan, 2)
+    assert list(lay["pix_off"]) == [0, 19200, 19200 + 57 * 33]
+    assert list(lay["tiles_x"]) == [10, 4] and list(lay["tiles_y"]) == [8, 3]
+    assert list(lay["tile_off"]) == [0, 80, 92]
+    ws = ts.ts_workspace_size(plan)
+    # records (128 B), gradients (96 B) and pair buffers dominate
+    assert ws > 2 * 2000 * (128 + 96) + 4 * 2 * 2000 * 24
+    assert ws % 256 == 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(tile_w=12), dict(tile_h=5), dict(tris_per_stage=48), dict(sigma=0.0), dict(alpha_max=1.0),
+    dict(T_min=1.0), dict(z_near=0.0), dict(flags=1)])
+def test_plan_rejects_bad_params(ts, bad):
+    with pytest.raises(ts.TsError) as e:
+        ts.ts_plan_init(np.array([[150, 150, 80, 60, 160, 120]]), 10, ts.ts_default_params(**bad))
+    assert e.value.status == 1
+
+
+def test_plan_rejects_bad_views(ts):
+    p = ts.ts_default_params()
+    for cams in (np.zeros((0, 6)), np.array([[150, 150, 80, 60, 0, 120]]), np.array([[-1, 150, 80, 60, 16, 16]]),
+                 np.tile([[10, 10, 5, 5, 16, 16]], (257, 1))):
+        with pytest.raises(ts.TsError):
+            ts.ts_plan_init(cams, 10, p)
+    with pytest.raises(ts.TsError):
+        ts.ts_plan_init(np.array([[10, 10, 5, 5, 16, 16]]), -1, p)
+
+
+def test_device_calls_reject_null_arguments(ts):
+    """Argument checks run before any CUDA call, so they are testable without a GPU."""
+    import ctypes as C
+    L = ts.binding.lib()
+    plan = ts.ts_plan_init(np.array([[10, 10, 5, 5, 16, 16]]), 4, ts.ts_default_params())
+    assert L.ts_project(C.byref(plan), None, None, None, 0, None) == 1
+    assert L.ts_bin(None, None, None) == 1
+    assert L.ts_render_fwd(C.byref(plan), None, None, None, None, None) == 1
+    assert L.ts_render_bwd(C.byref(plan), C.c_void_p(256), None, None, None, None, None) == 1
+    assert L.ts_pose_grad(C.byref(plan), None, None, None) == 1
+    # misaligned workspace
+    assert L.ts_bin(C.byref(plan), C.c_void_p(8), None) == 1
+    assert ts.ts_status_string(3) == "pair capacity exceeded"
