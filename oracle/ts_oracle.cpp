@@ -486,7 +486,12 @@ struct DualTerm {
 // perturbation tau = (rho, theta) (slots 21..26), evaluated at tau = 0.
 // Left perturbation Exp(tau) o T_CW moves a camera-space point v_C to
 // v_C + rho + theta x v_C to first order (Eq. 6-7).
-DualTerm dual_term(const Ctx& c, int view, int64_t m, double px, double py) {
+// The projected vertices carry the VALUES of the walk's projection pr (the
+// FP32 fixed-order values in FP32 mode, R14) and the derivatives of the
+// projection evaluated in double: the term is differentiated at the same
+// point the forward walk evaluated it, which matters near edges where the
+// window's slope grows like 1/sqrt(ratio).
+DualTerm dual_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px, double py) {
   const or_scene* sc = c.sc;
   const View& w = c.views[view];
   const double* P = sc->poses + 12 * view;
@@ -519,6 +524,9 @@ DualTerm dual_term(const Ctx& c, int view, int64_t m, double px, double py) {
     qx[k] = Dual(w.fx) * (vc[0] / vc[2]) + Dual(w.cx);
     qy[k] = Dual(w.fy) * (vc[1] / vc[2]) + Dual(w.cy);
     zc[k] = vc[2];
+    qx[k].v = pr.u[k];
+    qy[k].v = pr.v[k];
+    zc[k].v = pr.z[k];
   }
   Dual lam[3];
   double ratio;
@@ -695,7 +703,7 @@ int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC,
           const double dalpha = valk * q.T - suffix[k + 1] / (1.0 - q.alpha);
 #endif
           const double wgt = q.alpha * q.T;
-          DualTerm dt = dual_term(c, v, q.face, px, py);
+          DualTerm dt = dual_term(c, v, q.face, b.proj[(size_t)v * sc->n_faces + q.face], px, py);
           double g[NT];
           for (int i = 0; i < NT; ++i) {
             g[i] = dalpha * dt.alpha.d[i] + gD * wgt * dt.z.d[i];

@@ -35,14 +35,16 @@ def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, lambda_dep=0.
     out["counters"] = rast.counters(raise_on_error=False)
     if backward:
         dev = lambda a: None if a is None else torch.as_tensor(np.asarray(a), dtype=torch.float32, device="cuda")  # noqa
-        if dC is None:
+        if scene.tgt_color:
             tc, td = pack_targets(scene)
             loss, gC, gD = rast.l1_loss(dev(tc), dev(td), lambda_dep)
             out["loss_v"] = loss.cpu().numpy().astype(np.float64)
             out["dC"] = gC.cpu().numpy().astype(np.float64)
             out["dD"] = gD.cpu().numpy().astype(np.float64)
             gA = None
-        else:
+        if dC is not None:
+            # image gradients supplied by the caller (the L1 gradient is a sign: where the two renders
+            # differ by ~1e-5 around C = Cbar it may flip, so parity of the backward uses one dC)
             gC, gD, gA = dev(dC), dev(dD), dev(dA)
         g = m.zeros_like()
         rast.backward(gC, gD, gA, g)

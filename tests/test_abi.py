@@ -14,8 +14,8 @@ HEADER = os.path.join(ROOT, "include", "ts_api.h")
 
 @pytest.fixture(scope="module")
 def ts():
-    from paper_2605_31419_gb300 import _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2605_31419_gb300 as ts
     return ts
 

@@ -40,7 +40,8 @@ def run(name, tile=(16, 16), S=64, **kw):
         from oracle.oracle import Oracle
         sc = SCENES[name]()
         p, po = params_pair(tile_w=tile[0], tile_h=tile[1], tris_per_stage=S, **kw)
-        _cache[key] = (sc, p, po, gpu_run(sc, p), oracle_run(Oracle(), sc, po))
+        r = oracle_run(Oracle(), sc, po)
+        _cache[key] = (sc, p, po, gpu_run(sc, p, dC=r["dC_used"], dD=r["dD_used"]), r)
     return _cache[key]
 
 
@@ -152,8 +153,8 @@ def test_edge_cases(oracle, case):
         sc = _single([[x * zz, y * zz, zz] for zz in z for (x, y) in tri])
         sc.opa[:] = 0.9
     p, po = params_pair(**kw)
-    g = gpu_run(sc, p)
     r = oracle_run(oracle, sc, po)
+    g = gpu_run(sc, p, dC=r["dC_used"], dD=r["dD_used"])
     for k in ("color", "depth", "alpha"):
         assert_images(g[k], r[k], k)
     assert np.array_equal(g["n_last"], r["n_last"])
