@@ -180,6 +180,22 @@ ts_status ts_l1_loss(const ts_plan* plan, void* ws, const float* color, const fl
                      const float* tgt_color, const float* tgt_depth, float lambda_dep, float* loss,
                      float* dC, float* dD, ts_stream stream);
 
+/* The same loss as ts_l1_loss for callers that cannot give the library any device memory of its
+ * own: an application that owns the whole device budget and lends out only the image buffers,
+ * or a loop in which a cudaMalloc would synchronise the device or exceed a fixed memory pool.
+ * The paper has no counterpart; this is a deployment variant of the loss above.
+ *   cams: host array [n_views] describing the packed images (only width and height are used);
+ *   color, depth, tgt_color, tgt_depth, loss, dC, dD: device, as in ts_l1_loss.
+ * Needs no plan and no workspace and allocates nothing: the per-block partial sums live in one
+ * static device array of 512 KiB (65536 (view, 2048-pixel block) slots), held by every GPU that
+ * loads the library until the process exits.  n_views * ceil(max W*H / 2048) above 65536 returns
+ * TS_ERR_INVALID_ARG, as do null pointers and bad sizes.  The first call on a device looks up the
+ * array's address (make it before any stream capture).  Each call rewrites every slot it reads,
+ * so nothing carries over between calls; calls that overlap on the GPU share the array and race. */
+ts_status ts_l1_loss_noalloc(const ts_camera* cams, int32_t n_views, const float* color, const float* depth,
+                             const float* tgt_color, const float* tgt_depth, float lambda_dep, float* loss,
+                             float* dC, float* dD, ts_stream stream);
+
 /* Pose update for tracking: poses[v] <- Exp(-step[v]) o poses[v] (left perturbation, closed-form
  * SE(3) exponential), step = (rho, theta) device float [n_views][6]; poses device [n_views]. */
 ts_status ts_pose_apply(const ts_plan* plan, ts_pose* poses, const float* step, ts_stream stream);
