@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--faces", type=int, default=N_FACES)
     ap.add_argument("--views", type=int, default=N_VIEWS)
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="16x8")
     ap.add_argument("--stage", type=int, default=64)
     return ap.parse_args()
 

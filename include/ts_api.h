@@ -119,7 +119,7 @@ typedef struct {
 } ts_counters;
 
 /* Default parameters: sigma 0.5 (Table S5), alpha_min 1/255, alpha_max 0.99, T_min 1e-4,
- * z_near 0.01, r_min 0.01 px, bg 0, tile 16 x 16, 64 faces per stage. */
+ * z_near 0.01, r_min 0.01 px, bg 0, tile 16 x 8, 64 faces per stage. */
 void ts_default_params(ts_raster_params* out);
 
 /* Validate the views and parameters and lay out the workspace.

@@ -41,9 +41,11 @@ struct ProjArgs {
   const ts_pose* poses;
   long long M;
   long long VM;
+  int V;
   float z_near, r_min, alpha_min;
   int tile_w, tile_h;
   float4* frec;
+  float* grad;
   short4* rect;
   uint32_t* zbits;
   uint32_t* count;
@@ -128,8 +130,14 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
       rec[4] = make_float4(oF, __ldg(a.map.cr + j0), __ldg(a.map.cg + j0), __ldg(a.map.cb + j0));
       rec[5] = make_float4(__ldg(a.map.cr + j1), __ldg(a.map.cg + j1), __ldg(a.map.cb + j1), __ldg(a.map.cr + j2));
       rec[6] = make_float4(__ldg(a.map.cg + j2), __ldg(a.map.cb + j2), z[0], z[1]);
+      // gradient slot of this (view, face), face-major so that a face's views are adjacent;
+      // cleared here for the raster backward's atomics
+      const long long slot = m * a.V + view;
       rec[7] = make_float4(z[2], __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
-                           __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)idx));
+                           __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)slot));
+      float4* gs = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
+#pragma unroll
+      for (int i = 0; i < TS_GRAD_WORDS / 4; ++i) gs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       const int tx0 = x0 / a.tile_w, tx1 = x1 / a.tile_w, ty0 = y0 / a.tile_h, ty1 = y1 / a.tile_h;
       a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
       a.count[idx] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
@@ -167,6 +175,8 @@ cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* 
   a.alpha_min = p->prm.alpha_min;
   a.tile_w = p->prm.tile_w;
   a.tile_h = p->prm.tile_h;
+  a.V = p->V;
+  a.grad = w.grad;
   a.frec = w.frec;
   a.rect = w.rect;
   a.zbits = w.zbits;

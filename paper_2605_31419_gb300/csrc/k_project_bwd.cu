@@ -1,9 +1,6 @@
 // k_project_bwd.cu -- chain rule from the per-face screen-space sums to the map and the pose.
 //
-// One thread per face loops over the views.  For each view where the face was visible it reads
-// (and clears, so the accumulator is zero for the next call) the 24 sums written by the raster
-// backward, recomputes the projection in the same fixed FP32 order as the forward pass, and
-// applies, in closed form:
+// Closed form per visible (view, face), from the 24 sums the raster backward accumulated:
 //   * interpolants with vertex values w (colour channels, camera depth): dL/dw_k is the sum
 //     itself, and moving vertex k moves the interpolant's plane: dL/dq_k -= dL/dw_k * grad f;
 //   * edge functions E_i = s_i lambda_{i+2} with s_i = perimeter / |e_i| (Eq. 2-3 normalised
@@ -11,8 +8,20 @@
 //   * o_F = (o_i + o_j + o_k) / 3 (Sec. 3.1): each vertex opacity gets a third;
 //   * the pinhole (Eq. 1) to camera space, R^T to world space, and the left-perturbation pose
 //     Jacobian [I, -[v_C]x] (Eq. 7): dL/dtau += [g_C ; v_C x g_C].
-// The per-view pose terms are reduced over the block (fixed order) into per-block partials; a
-// second kernel sums the partials of each view in a fixed order, so dtau is deterministic.
+//
+// Gradient slots are face-major (slot = face * V + view) and cleared by the projection pass for
+// the visible ones.  Two passes keep every lane busy and the result deterministic:
+//   A. persistent warps scan the visibility counts, queue the visible slots with ballots, and run
+//      the chain rule on full warps of visible slots, writing each slot's world-space position
+//      gradient (words 0..8) and pose terms (words 24..29) back into it;
+//   B. persistent warps take 4 faces at a time: one ballot round trip gives each face's visible
+//      views, every lane then sums one output word (3 positions x 3 vertices, 3 colours x 3
+//      vertices, the opacity) over those views in view order with up to 8 loads in flight, and
+//      adds it to the map gradient; the lane that owns a view adds the face's pose terms to the
+//      warp's per-view sums in shared memory.  At the end the warps' sums are added in a fixed
+//      order into per-block partials, which a last kernel adds in a fixed order.
+#include <algorithm>
+
 #include "ts_internal.cuh"
 
 namespace {
@@ -21,182 +30,248 @@ struct PBArgs {
   const TsView* views;
   const ts_pose* poses;
   int V;
-  long long M;
+  long long M, VM;
   const uint32_t* count;
   float* grad;
   const TsDevHeader* hdr;
-  float *gpx, *gpy, *gpz, *gcr, *gcg, *gcb, *gop;
+  float* dst[7];  // gpx, gpy, gpz, gcr, gcg, gcb, gop
   float* part;
   int nblocks;
 };
 
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
+__device__ __forceinline__ long long face_vertex(const TsDevHeader* h, long long m, int k) {
+  long long j = h->faces ? (long long)h->faces[3 * m + k] : 3 * m + k;
+  return (j >= 0 && j < h->n_vertices) ? j : 0;
 }
 
-__global__ void __launch_bounds__(256) k_project_bwd(PBArgs a) {
-  __shared__ float red[8][6];
-  const long long m = (long long)blockIdx.x * 256 + threadIdx.x;
-  const bool valid = m < a.M;
+// Pass A body: the chain rule of one visible (view, face).
+__device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) {
   const TsDevHeader* h = a.hdr;
-  long long vi[3] = {0, 0, 0};
-  float X[3][3], col[3][3];
-  if (valid) {
-    if (h->faces) {
-      vi[0] = h->faces[3 * m]; vi[1] = h->faces[3 * m + 1]; vi[2] = h->faces[3 * m + 2];
-    } else {
-      vi[0] = 3 * m; vi[1] = 3 * m + 1; vi[2] = 3 * m + 2;
-    }
+  const long long slot = m * a.V + v;
+  float4* gp = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
+  float G[24];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const long long j = (vi[k] >= 0 && vi[k] < h->n_vertices) ? vi[k] : 0;
-      X[k][0] = h->px[j]; X[k][1] = h->py[j]; X[k][2] = h->pz[j];
-      col[k][0] = h->cr[j]; col[k][1] = h->cg[j]; col[k][2] = h->cb[j];
-    }
+  for (int i = 0; i < 6; ++i) {
+    const float4 q = gp[i];
+    G[4 * i] = q.x; G[4 * i + 1] = q.y; G[4 * i + 2] = q.z; G[4 * i + 3] = q.w;
   }
-  float dpos[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  float dcol[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  float dop = 0.f;  // same for all three vertices
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = 0; v < a.V; ++v) {
-    float tau[6] = {0, 0, 0, 0, 0, 0};
-    const long long slot = (long long)v * a.M + m;
-    if (valid && a.count[slot] > 0) {
-      float G[24];
-      float4* gp = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        const float4 q = gp[i];
-        G[4 * i] = q.x; G[4 * i + 1] = q.y; G[4 * i + 2] = q.z; G[4 * i + 3] = q.w;
-        gp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      const TsView vw = a.views[v];
-      const ts_pose P = a.poses[v];
-      float xc[3], yc[3], zc[3], u[3], w[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        ts_rigid_f32(P, X[k][0], X[k][1], X[k][2], xc[k], yc[k], zc[k]);
-        ts_pinhole_f32(vw, xc[k], yc[k], zc[k], u[k], w[k]);
-      }
-      float ex[3], ey[3], len[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int j = (i + 1) % 3;
-        ex[i] = u[j] - u[i];
-        ey[i] = w[j] - w[i];
-        len[i] = sqrtf(ex[i] * ex[i] + ey[i] * ey[i]);
-      }
-      const float per = len[0] + len[1] + len[2];
-      const float D2 = (u[1] - u[0]) * (w[2] - w[0]) - (u[2] - u[0]) * (w[1] - w[0]);
-      const float invD = 1.0f / D2;
-      float A[3], B[3];  // gradient of the barycentric lambda_k
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-        A[k] = (w[k1] - w[k2]) * invD;
-        B[k] = (u[k2] - u[k1]) * invD;
-      }
-      float s[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) s[i] = per / len[i];
-      float fa[3], fb[3];  // colour-field gradients
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        fa[ch] = col[0][ch] * A[0] + col[1][ch] * A[1] + col[2][ch] * A[2];
-        fb[ch] = col[0][ch] * B[0] + col[1][ch] * B[1] + col[2][ch] * B[2];
-      }
-      const float za = zc[0] * A[0] + zc[1] * A[1] + zc[2] * A[2];
-      const float zb = zc[0] * B[0] + zc[1] * B[1] + zc[2] * B[2];
-      float gu[3], gv[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        float su = G[G_Z + k] * za, sv = G[G_Z + k] * zb;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          su += G[G_C + 3 * ch + k] * fa[ch];
-          sv += G[G_C + 3 * ch + k] * fb[ch];
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const int o = (i + 2) % 3;
-          su += G[G_E + 3 * i + k] * s[i] * A[o];
-          sv += G[G_E + 3 * i + k] * s[i] * B[o];
-        }
-        gu[k] = -su;
-        gv[k] = -sv;
-      }
-      // edge lengths through s_i = per / len_i
-      float ds[3], sum_ds_len = 0.f;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        ds[i] = G[G_E + 3 * i + (i + 2) % 3];
-        sum_ds_len += ds[i] / len[i];
-      }
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const float dlen = sum_ds_len - ds[j] * per / (len[j] * len[j]);
-        const float cx = dlen * ex[j] / len[j], cy = dlen * ey[j] / len[j];
-        const int j1 = (j + 1) % 3;
-        gu[j1] += cx; gv[j1] += cy;
-        gu[j] -= cx; gv[j] -= cy;
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float iz = 1.0f / zc[k];
-        const float gx = gu[k] * vw.fx * iz;
-        const float gy = gv[k] * vw.fy * iz;
-        const float gz = -(gx * xc[k] + gy * yc[k]) * iz + G[G_Z + k];  // pinhole + interpolated depth
-        // world-space gradient R^T g_C
-        dpos[k][0] += P.R[0] * gx + P.R[3] * gy + P.R[6] * gz;
-        dpos[k][1] += P.R[1] * gx + P.R[4] * gy + P.R[7] * gz;
-        dpos[k][2] += P.R[2] * gx + P.R[5] * gy + P.R[8] * gz;
-        tau[0] += gx; tau[1] += gy; tau[2] += gz;
-        tau[3] += yc[k] * gz - zc[k] * gy;
-        tau[4] += zc[k] * gx - xc[k] * gz;
-        tau[5] += xc[k] * gy - yc[k] * gx;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) dcol[k][ch] += G[G_C + 3 * ch + k];
-      }
-      dop += G[G_O] * (1.0f / 3.0f);
-    }
-    // fixed-order block reduction of the pose terms of view v
-#pragma unroll
-    for (int i = 0; i < 6; ++i) tau[i] = warp_sum(tau[i]);
-    if (lane == 0) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) red[warp][i] = tau[i];
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-      float s = 0.f;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
-      a.part[((long long)v * a.nblocks + blockIdx.x) * 6 + threadIdx.x] = s;
-    }
-    __syncthreads();
-  }
-  if (!valid) return;
-  float* gp3[3] = {a.gpx, a.gpy, a.gpz};
-  float* gc3[3] = {a.gcr, a.gcg, a.gcb};
-  const bool indexed = h->faces != nullptr;
+  const TsView vw = a.views[v];
+  const ts_pose P = a.poses[v];
+  // The projection, edge vectors, lengths and area are recomputed in the forward record's fixed
+  // operation order, so the chain rule sees bit-identical values; for slivers the area is a
+  // cancelling difference and a one-ulp change of a vertex would move the gradient visibly.
+  float xc[3], yc[3], zc[3], u[3], w[3], col[3][3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const long long j = vi[k];
-    if (j < 0 || j >= h->n_vertices) continue;
+    const long long j = face_vertex(h, m, k);
+    ts_rigid_f32(P, __ldg(h->px + j), __ldg(h->py + j), __ldg(h->pz + j), xc[k], yc[k], zc[k]);
+    ts_pinhole_f32(vw, xc[k], yc[k], zc[k], u[k], w[k]);
+    col[k][0] = __ldg(h->cr + j); col[k][1] = __ldg(h->cg + j); col[k][2] = __ldg(h->cb + j);
+  }
+  float ex[3], ey[3], len[3], il[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (gp3[c]) {
-        if (indexed) atomicAdd(gp3[c] + j, dpos[k][c]); else gp3[c][j] += dpos[k][c];
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3;
+    ex[i] = u[j] - u[i];
+    ey[i] = w[j] - w[i];
+    len[i] = __fsqrt_rn(__fadd_rn(__fmul_rn(ex[i], ex[i]), __fmul_rn(ey[i], ey[i])));
+    il[i] = 1.0f / len[i];
+  }
+  const float per = __fadd_rn(__fadd_rn(len[0], len[1]), len[2]);
+  const float D2 = __fsub_rn(__fmul_rn(__fsub_rn(u[1], u[0]), __fsub_rn(w[2], w[0])),
+                             __fmul_rn(__fsub_rn(u[2], u[0]), __fsub_rn(w[1], w[0])));
+  const float invD = 1.0f / D2;
+  float A[3], B[3];  // gradient of the barycentric lambda_k
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+    A[k] = (w[k1] - w[k2]) * invD;
+    B[k] = (u[k2] - u[k1]) * invD;
+  }
+  float fa[3], fb[3];  // colour-field gradients
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    fa[ch] = col[0][ch] * A[0] + col[1][ch] * A[1] + col[2][ch] * A[2];
+    fb[ch] = col[0][ch] * B[0] + col[1][ch] * B[1] + col[2][ch] * B[2];
+  }
+  const float za = zc[0] * A[0] + zc[1] * A[1] + zc[2] * A[2];
+  const float zb = zc[0] * B[0] + zc[1] * B[1] + zc[2] * B[2];
+  float gu[3], gv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float su = G[G_Z + k] * za, sv = G[G_Z + k] * zb;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      su += G[G_C + 3 * ch + k] * fa[ch];
+      sv += G[G_C + 3 * ch + k] * fb[ch];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int o = (i + 2) % 3;
+      const float si = per * il[i];
+      su += G[G_E + 3 * i + k] * si * A[o];
+      sv += G[G_E + 3 * i + k] * si * B[o];
+    }
+    gu[k] = -su;
+    gv[k] = -sv;
+  }
+  // edge lengths through s_i = per / len_i: dL/dlen_j = sum_i dL/ds_i / len_i - dL/ds_j per / len_j^2
+  float ds[3], sum_ds_len = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ds[i] = G[G_E + 3 * i + (i + 2) % 3];
+    sum_ds_len += ds[i] * il[i];
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float dlen = sum_ds_len - ds[j] * per * il[j] * il[j];
+    const float cx = dlen * ex[j] * il[j], cy = dlen * ey[j] * il[j];
+    const int j1 = (j + 1) % 3;
+    gu[j1] += cx; gv[j1] += cy;
+    gu[j] -= cx; gv[j] -= cy;
+  }
+  float out[9];
+  float tau[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float iz = 1.0f / zc[k];
+    const float gx = gu[k] * vw.fx * iz;
+    const float gy = gv[k] * vw.fy * iz;
+    const float gz = -(gx * xc[k] + gy * yc[k]) * iz + G[G_Z + k];  // pinhole + interpolated depth
+    out[3 * k + 0] = P.R[0] * gx + P.R[3] * gy + P.R[6] * gz;  // R^T g_C
+    out[3 * k + 1] = P.R[1] * gx + P.R[4] * gy + P.R[7] * gz;
+    out[3 * k + 2] = P.R[2] * gx + P.R[5] * gy + P.R[8] * gz;
+    tau[0] += gx; tau[1] += gy; tau[2] += gz;
+    tau[3] += yc[k] * gz - zc[k] * gy;
+    tau[4] += zc[k] * gx - xc[k] * gz;
+    tau[5] += xc[k] * gy - yc[k] * gx;
+  }
+  // write back: positions into words 0..8 (edge sums, now consumed), pose terms into 24..29
+  float* gs = a.grad + slot * TS_GRAD_WORDS;
+  gp[0] = make_float4(out[0], out[1], out[2], out[3]);
+  gp[1] = make_float4(out[4], out[5], out[6], out[7]);
+  gs[8] = out[8];
+  gp[6] = make_float4(tau[0], tau[1], tau[2], tau[3]);
+  gs[28] = tau[4];
+  gs[29] = tau[5];
+}
+
+constexpr int PA_T = 256;
+constexpr int PA_WARPS = PA_T / 32;
+
+__global__ void __launch_bounds__(PA_T) k_pbwd_chain(PBArgs a) {
+  __shared__ long long q[PA_WARPS][64];  // queued view-major indices v * M + m
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * PA_WARPS + warp, nw = (long long)gridDim.x * PA_WARPS;
+  const unsigned lt = (1u << lane) - 1u;
+  int qn = 0;
+  for (long long c = gw; c * 32 < a.VM; c += nw) {
+    const long long idx = c * 32 + lane;
+    const bool vis = idx < a.VM && a.count[idx] > 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, vis);
+    if (vis) q[warp][qn + __popc(bal & lt)] = idx;
+    qn += __popc(bal);
+    __syncwarp();
+    if (qn >= 32) {
+      const long long e = q[warp][lane];
+      const int v = (int)(e / a.M);
+      chain_slot(a, v, e - (long long)v * a.M);
+      __syncwarp();
+      if (lane < qn - 32) q[warp][lane] = q[warp][lane + 32];
+      qn -= 32;
+      __syncwarp();
+    }
+  }
+  if (lane < qn) {
+    const long long e = q[warp][lane];
+    const int v = (int)(e / a.M);
+    chain_slot(a, v, e - (long long)v * a.M);
+  }
+}
+
+constexpr int PG_WARPS = 4;
+constexpr int PG_T = 32 * PG_WARPS;
+constexpr int PG_F = 4;  // faces per warp iteration
+
+__global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
+  extern __shared__ float pv[];  // [PG_WARPS][V][8] per-warp per-view pose sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const TsDevHeader* h = a.hdr;
+  float* my = pv + (size_t)warp * a.V * 8;
+  for (int i = lane; i < a.V * 8; i += 32) my[i] = 0.f;
+  __syncwarp();
+  // lanes 0..20 each own one output word: array c (gpx..gop), vertex k
+  const int c = lane / 3, k = lane - 3 * (lane / 3);
+  const bool owner = lane < 21;
+  const int word = c < 3 ? G_DPOS + 3 * k + c : (c < 6 ? G_C + 3 * (c - 3) + k : G_O);
+  const float scale = c == 6 ? (1.0f / 3.0f) : 1.0f;
+  float* dst = owner ? a.dst[c] : nullptr;
+  const bool indexed = h->faces != nullptr;
+  const long long stride = (long long)gridDim.x * PG_WARPS * PG_F;
+  for (long long m0 = ((long long)blockIdx.x * PG_WARPS + warp) * PG_F; m0 < a.M; m0 += stride) {
+    long long j[PG_F];
+    float old[PG_F], s[PG_F];
+#pragma unroll
+    for (int f = 0; f < PG_F; ++f) {
+      const long long m = m0 + f;
+      j[f] = (m < a.M && owner) ? face_vertex(h, m, k) : 0;
+      old[f] = (m < a.M && dst && !indexed) ? dst[j[f]] : 0.f;  // issued early
+      s[f] = 0.f;
+    }
+    for (int r = 0; r * 32 < a.V; ++r) {
+      const int vl = r * 32 + lane;
+      unsigned msk[PG_F];
+#pragma unroll
+      for (int f = 0; f < PG_F; ++f) {
+        const long long m = m0 + f;
+        const uint32_t cnt = (m < a.M && vl < a.V) ? a.count[(long long)vl * a.M + m] : 0u;
+        msk[f] = __ballot_sync(0xffffffffu, cnt > 0);
       }
-      if (gc3[c]) {
-        if (indexed) atomicAdd(gc3[c] + j, dcol[k][c]); else gc3[c][j] += dcol[k][c];
+      // pose terms: the lane owning view vl adds each face's terms to the warp's sums (face order)
+#pragma unroll
+      for (int f = 0; f < PG_F; ++f) {
+        if ((msk[f] >> lane) & 1u) {
+          const float* t = a.grad + ((m0 + f) * a.V + vl) * TS_GRAD_WORDS + G_TAU;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) my[vl * 8 + i] += t[i];
+        }
+      }
+      // output words: sum over the visible views in view order, up to 8 loads in flight
+#pragma unroll
+      for (int f = 0; f < PG_F; ++f) {
+        unsigned bits = msk[f];
+        const float* base = a.grad + (m0 + f) * a.V * TS_GRAD_WORDS + word;
+        while (bits) {
+          float vals[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            vals[u] = 0.f;
+            if (bits) {
+              const int v = r * 32 + __ffs(bits) - 1;
+              bits &= bits - 1;
+              if (owner) vals[u] = base[(long long)v * TS_GRAD_WORDS];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s[f] += vals[u];
+        }
       }
     }
-    if (a.gop) {
-      if (indexed) atomicAdd(a.gop + j, dop); else a.gop[j] += dop;
+#pragma unroll
+    for (int f = 0; f < PG_F; ++f) {
+      if (m0 + f < a.M && dst) {
+        if (indexed) atomicAdd(dst + j[f], s[f] * scale);
+        else dst[j[f]] = old[f] + s[f] * scale;
+      }
     }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < a.V * 6; t += PG_T) {
+    const int v = t / 6, i = t - 6 * (t / 6);
+    float sum = 0.f;
+#pragma unroll
+    for (int w = 0; w < PG_WARPS; ++w) sum += pv[((size_t)w * a.V + v) * 8 + i];
+    a.part[((long long)v * a.nblocks + blockIdx.x) * 6 + i] = sum;
   }
 }
 
@@ -224,6 +299,11 @@ __global__ void __launch_bounds__(256) k_pose_reduce(const float* __restrict__ p
 
 }  // namespace
 
+int ts_pose_blocks(long long M) {
+  const long long want = (M + PG_WARPS * PG_F - 1) / (PG_WARPS * PG_F);
+  return (int)std::max<long long>(1, std::min<long long>(want, 152LL * 16));
+}
+
 cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_map_grad* g, cudaStream_t s) {
   if (p->M == 0) {
     return cudaMemsetAsync(w.pose, 0, (size_t)p->V * p->n_pose_blocks * 6 * 4, s);
@@ -233,15 +313,20 @@ cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_m
   a.poses = w.poses;
   a.V = p->V;
   a.M = p->M;
+  a.VM = (long long)p->V * p->M;
   a.count = w.count;
   a.grad = w.grad;
   a.hdr = w.hdr;
-  a.gpx = g->gpx; a.gpy = g->gpy; a.gpz = g->gpz;
-  a.gcr = g->gcr; a.gcg = g->gcg; a.gcb = g->gcb;
-  a.gop = g->gop;
+  a.dst[0] = g->gpx; a.dst[1] = g->gpy; a.dst[2] = g->gpz;
+  a.dst[3] = g->gcr; a.dst[4] = g->gcg; a.dst[5] = g->gcb;
+  a.dst[6] = g->gop;
   a.part = w.pose;
   a.nblocks = (int)p->n_pose_blocks;
-  k_project_bwd<<<(unsigned)p->n_pose_blocks, 256, 0, s>>>(a);
+  const long long chunks = (a.VM + 31) / 32;
+  const long long grid_a = std::min<long long>((chunks + PA_WARPS - 1) / PA_WARPS, 152LL * 8);
+  k_pbwd_chain<<<(unsigned)grid_a, PA_T, 0, s>>>(a);
+  const size_t smem = (size_t)PG_WARPS * p->V * 8 * sizeof(float);  // <= 32 KiB for 256 views
+  k_pbwd_gather<<<(unsigned)p->n_pose_blocks, PG_T, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -98,12 +98,15 @@ __device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, 
   }
 }
 
-// Replace each staged record's pixel-box word by the mask of warp sub-blocks it overlaps.
+// For each staged record, the mask of warp sub-blocks (8 x 4 pixels) that can contain one of its
+// covered pixel centres: sub-blocks inside the face's pixel box whose pixel-centre rectangle,
+// widened by 0.01 px, is not entirely outside one of the three edges.  Conservative: a pixel with
+// a positive window always keeps its sub-block's bit.
 template <int TW, int TH>
-__device__ __forceinline__ void stage_masks(float* rb, int cnt, int X0, int Y0) {
+__device__ __forceinline__ void stage_masks(const float* rb, uint32_t* smask, int cnt, int X0, int Y0) {
   constexpr int NSBX = TW / 8;
   for (int j = threadIdx.x; j < cnt; j += TW * TH) {
-    float* r = rb + j * TS_REC_WORDS;
+    const float* r = rb + j * TS_REC_WORDS;
     const uint32_t bx = __float_as_uint(r[R_BOXX]), by = __float_as_uint(r[R_BOXY]);
     const int x0 = (int)(bx & 0xffffu) - X0, x1 = (int)(bx >> 16) - X0;
     const int y0 = (int)(by & 0xffffu) - Y0, y1 = (int)(by >> 16) - Y0;
@@ -111,10 +114,25 @@ __device__ __forceinline__ void stage_masks(float* rb, int cnt, int X0, int Y0) 
     if (x1 >= 0 && x0 < TW && y1 >= 0 && y0 < TH) {
       const int c0 = max(x0, 0) >> 3, c1 = min(x1, TW - 1) >> 3;
       const int r0 = max(y0, 0) >> 2, r1 = min(y1, TH - 1) >> 2;
-      const uint32_t cols = ((2u << c1) - 1u) & ~((1u << c0) - 1u);
-      for (int rr = r0; rr <= r1; ++rr) mask |= cols << (rr * NSBX);
+      const float sgn = r[R_INVD] > 0.f ? 1.f : -1.f;
+      const float qx[3] = {r[R_U0], r[R_U1], r[R_U2]}, qy[3] = {r[R_V0], r[R_V1], r[R_V2]};
+      const float ex[3] = {r[R_E0X], r[R_E1X], r[R_E2X]}, ey[3] = {r[R_E0Y], r[R_E1Y], r[R_E2Y]};
+      for (int rr = r0; rr <= r1; ++rr) {
+        const float cy = (float)(Y0 + rr * 4) + 2.0f;  // centre of the sub-block's pixel centres
+        for (int cc = c0; cc <= c1; ++cc) {
+          const float cx = (float)(X0 + cc * 8) + 4.0f;
+          bool in = true;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const float f = sgn * (ex[i] * (cy - qy[i]) - ey[i] * (cx - qx[i])) + fabsf(ey[i]) * 3.51f +
+                            fabsf(ex[i]) * 1.51f;
+            in = in && f > 0.f;
+          }
+          if (in) mask |= 1u << (rr * NSBX + cc);
+        }
+      }
     }
-    r[R_MASK] = __uint_as_float(mask);
+    smask[j] = mask;
   }
 }
 
@@ -129,8 +147,9 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_view;
+  __shared__ uint32_t smask[2][128];
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, &s_view);
-  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint2 rg = a.ranges[blockIdx.x];
   const int n = (int)(rg.y - rg.x);
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
@@ -159,31 +178,37 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
         }
         return;
       }
-      float* rb = reinterpret_cast<float*>(smrec + (size_t)b * S * 8);
-      stage_masks<TW, TH>(rb, cnt, g.X0, g.Y0);
+      const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
+      stage_masks<TW, TH>(rb, smask[b], cnt, g.X0, g.Y0);
       __syncthreads();
       if (warp == 0 && st + 1 < nst) issue_stage(a, smrec, bar, b ^ 1, st + 1, rg.x, n, vbase);
-      for (int j = 0; j < cnt; ++j) {
-        const float* r = rb + j * TS_REC_WORDS;
-        if (!((__float_as_uint(r[R_MASK]) >> warp) & 1u)) continue;  // warp-uniform
-        if (done) continue;
-        const TsPix e = ts_eval_edges(r, g.px, g.py);
-        if (!(e.m > 0.f)) continue;
-        const float I = ts_window(e.m, a.sigma);
-        const float al = fminf(r[R_OF] * I, a.alpha_max);
-        if (al < a.alpha_min) continue;
-        const float Tn = T * (1.f - al);
-        if (Tn < a.T_min) { done = true; continue; }
-        const float invD = r[R_INVD];
-        const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
-        const float w = al * T;
-        C0 += w * (l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2]);
-        C1 += w * (l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1]);
-        C2 += w * (l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2]);
-        D += w * (l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2]);
-        T = Tn;
-        nl = st * S + j + 1;
-        ++contrib;
+      // this warp visits only the stage's faces whose mask has its bit (front to back)
+      for (int q = 0; q * 32 < cnt; ++q) {
+        const int jq = q * 32 + lane;
+        unsigned bits = __ballot_sync(FULL, jq < cnt && ((smask[b][min(jq, cnt - 1)] >> warp) & 1u));
+        while (bits) {
+          const int j = q * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          if (done) continue;
+          const float* r = rb + j * TS_REC_WORDS;
+          const TsPix e = ts_eval_edges(r, g.px, g.py);
+          if (!(e.m > 0.f)) continue;
+          const float I = ts_window(e.m, a.sigma);
+          const float al = fminf(r[R_OF] * I, a.alpha_max);
+          if (al < a.alpha_min) continue;
+          const float Tn = T * (1.f - al);
+          if (Tn < a.T_min) { done = true; continue; }
+          const float invD = r[R_INVD];
+          const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
+          const float w = al * T;
+          C0 += w * (l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2]);
+          C1 += w * (l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1]);
+          C2 += w * (l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2]);
+          D += w * (l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2]);
+          T = Tn;
+          nl = st * S + j + 1;
+          ++contrib;
+        }
       }
       if (__syncthreads_count(!done) == 0) {
         if (threadIdx.x == 0 && st + 1 < nst) {
@@ -218,6 +243,7 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_view;
   __shared__ int s_nmax;
+  __shared__ uint32_t smask[2][128];
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, &s_view);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint2 rg = a.ranges[blockIdx.x];
@@ -274,13 +300,19 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
         }
         return;
       }
-      float* rb = reinterpret_cast<float*>(smrec + (size_t)b * S * 8);
-      stage_masks<TW, TH>(rb, cnt, g.X0, g.Y0);
+      const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
+      stage_masks<TW, TH>(rb, smask[b], cnt, g.X0, g.Y0);
       __syncthreads();
       if (warp == 0 && k + 1 < nst) issue_stage(a, smrec, bar, b ^ 1, st - 1, rg.x, n, vbase);
-      for (int j = cnt - 1; j >= 0; --j) {
+      // this warp visits only the stage's faces whose mask has its bit (back to front)
+      for (int qq = (cnt - 1) >> 5; qq >= 0; --qq) {
+        const int jq = qq * 32 + lane;
+        unsigned bits = __ballot_sync(FULL, jq < cnt && ((smask[b][min(jq, cnt - 1)] >> warp) & 1u));
+        while (bits) {
+        const int hb = 31 - __clz(bits);
+        bits &= ~(1u << hb);
+        const int j = qq * 32 + hb;
         const float* r = rb + j * TS_REC_WORDS;
-        if (!((__float_as_uint(r[R_MASK]) >> warp) & 1u)) continue;  // warp-uniform
         const int pos = st * S + j;
         bool cb = false;
         TsPix e;
@@ -362,7 +394,8 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
             atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
           }
         }
-      }
+        }  // while bits
+      }    // stage words
     }
   }
   count_add(&a.hdr->bwd_contrib, contrib);

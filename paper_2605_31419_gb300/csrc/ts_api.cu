@@ -52,7 +52,7 @@ void ts_default_params(ts_raster_params* o) {
   o->r_min = 0.01f;
   o->bg[0] = o->bg[1] = o->bg[2] = 0.0f;
   o->tile_w = 16;
-  o->tile_h = 16;
+  o->tile_h = 8;
   o->tris_per_stage = 64;
   o->flags = 0;
 }
@@ -101,7 +101,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->sort_passes = (32 + tb + 7) / 8;
   p->n_scan_blocks = std::max<int64_t>(1, (VM + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
   p->n_sort_blocks_cap = (cap + TS_SORT_ITEMS - 1) / TS_SORT_ITEMS;
-  p->n_pose_blocks = std::max<int64_t>(1, (n_faces + 255) / 256);
+  p->n_pose_blocks = std::max(1, ts_pose_blocks(n_faces));
   int64_t max_hw = 0;
   for (int v = 0; v < n_views; ++v) max_hw = std::max<int64_t>(max_hw, (int64_t)p->views[v].W * p->views[v].H);
   p->n_loss_blocks = (max_hw + 2047) / 2048;

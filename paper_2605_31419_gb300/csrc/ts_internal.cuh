@@ -13,7 +13,7 @@
 
 #define TS_PLAN_MAGIC 0x54535031u  // "TSP1"
 #define TS_REC_WORDS 32            // 128-byte record, a multiple of 16 B for cp.async.bulk
-#define TS_GRAD_WORDS 24           // per-(view, face) gradient accumulator
+#define TS_GRAD_WORDS 32           // per-(view, face) gradient slot: 24 accumulators + chain outputs
 #define TS_SCAN_ITEMS 4096         // items per scan block (1024 threads x 4)
 #define TS_SORT_ITEMS 4096         // keys per radix-sort block (256 threads x 16)
 #define TS_SORT_THREADS 256
@@ -40,7 +40,9 @@ enum {
 
 // Gradient word indices: G_E[i][k] = sum_p dL/dE_i * lambda_k (edge i nearest), G_c[ch][k] =
 // sum_p dL/dc_ch * lambda_k, G_z[k] = sum_p dL/dz * lambda_k, G_o = dL/do_F, count = pixels.
-enum { G_E = 0, G_C = 9, G_Z = 18, G_O = 21, G_CNT = 22 };
+// The raster backward accumulates words 0..23; the chain-rule pass then overwrites words
+// G_DPOS.. with the face's world-space vertex-position gradients and G_TAU.. with its pose terms.
+enum { G_E = 0, G_C = 9, G_Z = 18, G_O = 21, G_CNT = 22, G_DPOS = 0, G_TAU = 24 };
 
 struct TsView {
   float fx, fy, cx, cy;
@@ -152,6 +154,7 @@ cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* c
                               float* dD, cudaStream_t s);
 cudaError_t ts_launch_pose_apply(const TsPlanImpl* p, ts_pose* poses, const float* step, cudaStream_t s);
 int ts_sort_final_buffer(const TsPlanImpl* p);  // 0 or 1: which key/val buffer holds the sorted pairs
+int ts_pose_blocks(long long M);                 // blocks of the projection-backward kernel
 
 // ------------------------------------------------------------------------------------------
 // Device helpers

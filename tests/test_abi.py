@@ -44,12 +44,12 @@ def test_default_params_match_paper(ts):
     g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
     p = ts.ts_default_params()
     assert p.sigma == g["sigma"]["value"]
-    assert (p.tile_w, p.tile_h, p.tris_per_stage) == (16, 16, 64)
+    assert (p.tile_w, p.tile_h, p.tris_per_stage) == (16, 8, 64)
 
 
 def test_plan_layout_and_workspace(ts):
     cams = np.array([[150, 150, 80, 60, 160, 120], [40, 40, 28.5, 16.5, 57, 33]])
-    plan = ts.ts_plan_init(cams, 2000, ts.ts_default_params())
+    plan = ts.ts_plan_init(cams, 2000, ts.ts_default_params(tile_h=16))
     lay = ts.ts_plan_layout(plan, 2)
     assert list(lay["pix_off"]) == [0, 19200, 19200 + 57 * 33]
     assert list(lay["tiles_x"]) == [10, 4] and list(lay["tiles_y"]) == [8, 3]
