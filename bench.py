@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mapping-window and tracking measurements")
     ap.add_argument("--faces", type=int, default=N_FACES)
     ap.add_argument("--views", type=int, default=N_VIEWS)
     ap.add_argument("--tile", default="16x8")
@@ -143,6 +144,81 @@ def cpu_baseline(sc, time_budget_s=20.0):
     return {"value": W * H / t / 1e6, "unit": "Mpix/s", "cores": nthreads, "kind": "oracle",
             "sample": f"1 of {sc.n_views} views (1200x680, {sc.n_faces} faces): fwd + L1 loss + bwd, "
                       f"median of {len(times)} runs, {t:.2f} s each"}
+
+
+def bench_mapping_window(ts, torch, dev, n_faces=1_000_000, steps=5):
+    """Mapping window: 12 keyframes (4 each of 320x240, 640x480, 1200x680) of a 1M-face map,
+    joint forward + backward with gradients accumulated into shared map buffers.  Plain per-view
+    calls vs one batched pass vs the autotuned, graph-captured batched pass."""
+    from ts_synth.scenes import Scene, mixed_keyframe_cameras, noise_targets, room_map, trajectory_poses
+    pos, col, opa = room_map(5, n_faces)
+    cams = mixed_keyframe_cameras(4)
+    poses_np = trajectory_poses(1005, len(cams))
+    tcs, tds = noise_targets(6, cams)
+    m = ts.Map.from_numpy(pos, col, opa, device=dev)
+    grad = m.zeros_like()
+    poses = ts.poses_tensor(poses_np, device=dev)
+    tc = torch.as_tensor(np.concatenate([t.reshape(-1) for t in tcs]), device=dev)
+    td = torch.as_tensor(np.concatenate([t.reshape(-1) for t in tds]), device=dev)
+    pixels = int(sum(c[4] * c[5] for c in cams))
+    off = np.concatenate([[0], np.cumsum(cams[:, 4] * cams[:, 5])]).astype(int)
+    out = {"workload": "room 1M faces, 12 keyframes: 4x 320x240, 4x 640x480, 4x 1200x680, fwd+bwd", "pixels": pixels}
+    # plain: one plan per keyframe, called one after another
+    singles = [ts.MultiViewStep(m, cams[v:v + 1], poses[v:v + 1], tc[3 * off[v]:3 * off[v + 1]], td[off[v]:off[v + 1]],
+                                None, grad) for v in range(len(cams))]
+    ms_plain = ts.batch.time_ms(lambda: [s.step() for s in singles], iters=steps)
+    del singles
+    torch.cuda.empty_cache()
+    batched = ts.MultiViewStep(m, cams, poses, tc, td, None, grad)
+    ms_batched = ts.batch.time_ms(batched.step, iters=steps)
+    del batched
+    torch.cuda.empty_cache()
+    best, _ = ts.autotune(m, cams, poses, tc, td, grad, tiles=((16, 8), (8, 8), (16, 16), (32, 8)), stages=(64, 128),
+                          iters=2, use_cache=False)
+    tuned = ts.MultiViewStep(m, cams, poses, tc, td, ts.params_of(best), grad)
+    tuned.capture()
+    ms_tuned = ts.batch.time_ms(lambda: tuned.run(1, use_graph=True), iters=steps)
+    del tuned
+    torch.cuda.empty_cache()
+    out.update({"plain_per_view_mpix_s": pixels / ms_plain / 1e3, "batched_mpix_s": pixels / ms_batched / 1e3,
+                "batched_graph_autotuned_mpix_s": pixels / ms_tuned / 1e3, "ms": {"plain": ms_plain,
+                "batched": ms_batched, "batched_graph_autotuned": ms_tuned}, "autotuned": best})
+    return out
+
+
+def bench_tracking(ts, torch, dev, n_hyp=64, iters=100):
+    """Tracking: 64 pose hypotheses of a 640x480 (f = 525) camera on a 150k-face room map,
+    100 gradient iterations each, replayed from one captured CUDA graph."""
+    from ts_synth.scenes import perturb_pose, room_map, trajectory_poses
+    pos, col, opa = room_map(7, 150_000)
+    W_, H_, f = 640, 480, 525.0
+    cam = np.array([f, f, W_ / 2, H_ / 2, W_, H_])
+    gt = trajectory_poses(1007, 8)[2]
+    m = ts.Map.from_numpy(pos, col, opa, device=dev)
+    # target: the GT render plus noise (sigma 0.02 on colour, 1 % on depth)
+    r0 = ts.Rasterizer(cam[None, :], m.n_faces)
+    C, D, _ = r0.forward(m, ts.poses_tensor(gt[None, :], device=dev))
+    g = torch.Generator(device=dev).manual_seed(8)
+    tc = (C + 0.02 * torch.randn(C.shape, generator=g, device=dev)).contiguous()
+    td = (D * (1 + 0.01 * torch.randn(D.shape, generator=g, device=dev))).contiguous()
+    del r0
+    rng = np.random.default_rng(9)
+    init = np.stack([perturb_pose(gt, rng) for _ in range(n_hyp)])
+    trk = ts.Tracker(m, cam, tc.view(3, H_, W_), td.view(H_, W_), init)
+    trk.capture()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    trk.run(iters, use_graph=True)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    e0 = ts.pose_error(init, np.tile(gt, (n_hyp, 1)))
+    e1 = ts.pose_error(trk.poses.cpu().numpy(), np.tile(gt, (n_hyp, 1)))
+    px = n_hyp * W_ * H_ * iters
+    return {"workload": f"640x480 f=525, 150k-face room, {n_hyp} hypotheses x {iters} iterations (graph replay)",
+            "mpix_s": px / ms / 1e3, "ms_per_iteration": ms / iters,
+            "median_error_before": {"cm": float(np.median(e0[:, 0]) * 100), "deg": float(np.median(e0[:, 1]))},
+            "median_error_after": {"cm": float(np.median(e1[:, 0]) * 100), "deg": float(np.median(e1[:, 1]))}}
 
 
 def run_reference(args):
@@ -318,7 +394,9 @@ def main():
         else:
             roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": None}
-        launches = 2 + 3 + 5 * int(rast.plan_passes()) + 1 + 1 + 2 + 2 + 1
+        # setup + project, scan (3), 5 per radix pass, ranges, forward, loss (2), raster backward,
+        # chain rule + gather, pose reduction
+        launches = 2 + 3 + 5 * int(rast.plan_passes()) + 1 + 1 + 2 + 1 + 2 + 1
         line = {
             "metric": "Mpix/s fwd+bwd raster", "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
@@ -333,6 +411,11 @@ def main():
             "roofline": roof, "peaks": peak_src, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clocks,
         }
+        if not args.no_extras:
+            del rast
+            torch.cuda.empty_cache()
+            line["mapping_window"] = bench_mapping_window(ts, torch, dev)
+            line["tracking"] = bench_tracking(ts, torch, dev)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(sc)
         print(json.dumps(line), flush=True)

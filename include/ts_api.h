@@ -75,8 +75,13 @@ typedef struct {
   float bg[3];
   int32_t tile_w, tile_h;   /* tile shape: tile_w in {8, 16, 32}, tile_h in {4, 8, 16, 32}, <= 512 px */
   int32_t tris_per_stage;   /* faces staged in shared memory per step: 32, 64 or 128 */
-  int32_t flags;            /* reserved, must be 0 */
+  int32_t flags;            /* TS_FLAG_* bits; other bits must be 0 */
 } ts_raster_params;
+
+/* ts_raster_params.flags: run the raster kernels as persistent CTAs (as many as are resident on
+ * the GPU) that take (view, tile) work items from a device counter, instead of one CTA per tile.
+ * Results are identical; it helps when tiles of very uneven cost (mixed resolutions) are batched. */
+#define TS_FLAG_PERSISTENT 1
 
 /* The map (Sec. 3.1): N vertices with position, colour, opacity as structure-of-arrays float32
  * device buffers, and M faces.  faces = NULL selects triangle-soup mode (face m uses vertices
@@ -199,6 +204,14 @@ ts_status ts_l1_loss_noalloc(const ts_camera* cams, int32_t n_views, const float
 /* Pose update for tracking: poses[v] <- Exp(-step[v]) o poses[v] (left perturbation, closed-form
  * SE(3) exponential), step = (rho, theta) device float [n_views][6]; poses device [n_views]. */
 ts_status ts_pose_apply(const ts_plan* plan, ts_pose* poses, const float* step, ts_stream stream);
+
+/* Gradient-descent tracking step (Sec. 3.3: the pose is optimised by gradient descent on
+ * dL/dtau; rotation and translation learning rates of Table S5): Adam on dtau per view, then
+ * poses[v] <- Exp(-step) o poses[v].  state: device float [n_views][13] (first moments, second
+ * moments, step count), zeroed by the caller before the first step and updated in place, so the
+ * step can be captured in a CUDA graph and replayed.  lr_rho scales the translation part. */
+ts_status ts_pose_adam(const ts_plan* plan, ts_pose* poses, const float* dtau, float* state, float lr_rho,
+                       float lr_theta, float beta1, float beta2, float eps, ts_stream stream);
 
 /* Synchronise the stream, copy the device counters into *out (may be NULL) and return
  * TS_ERR_CAPACITY / TS_ERR_TIMEOUT if the device latched an error since ts_workspace_init,

@@ -1,0 +1,141 @@
+"""Batched multi-view passes, CUDA-graph capture and the launch-shape autotuner.
+
+``MultiViewStep`` runs the joint forward + backward of many views of one map -- the mapping
+window of Sec. 3.4 (keyframes of uneven resolution replayed together) -- as one plan: one launch
+per stage for all views, gradients of every view accumulated into shared vertex, colour and
+opacity buffers, optionally persistent raster CTAs and a captured CUDA graph.  ``autotune`` times
+the candidate tile shapes, stage sizes and launch forms on the actual workload and caches the
+winner per workload signature.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from typing import Iterable, Optional
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .rasterizer import Map, Rasterizer
+
+TILE_SHAPES = ((16, 8), (8, 8), (16, 16), (32, 8), (16, 32), (32, 16))
+STAGE_SIZES = (32, 64, 128)
+
+
+class MultiViewStep:
+    """Forward, L1 loss and backward of all views of ``cams`` on ``m`` in one batched pass."""
+
+    def __init__(self, m: Map, cams, poses: torch.Tensor, tgt_color: torch.Tensor, tgt_depth: torch.Tensor,
+                 params: Optional[B.TsRasterParams] = None, grad: Optional[Map] = None, lambda_dep: float = 0.05,
+                 pair_capacity: int = 0, want_pose: bool = True):
+        self.map, self.poses = m, poses
+        self.tc, self.td = tgt_color, tgt_depth
+        self.rast = Rasterizer(cams, m.n_faces, params, pair_capacity=pair_capacity)
+        self.grad = grad
+        self.lambda_dep = float(lambda_dep)
+        self.want_pose = want_pose
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+
+    def step(self):
+        r = self.rast
+        r.project(self.map, self.poses)
+        r.bin()
+        r.render_fwd()
+        r.l1_loss(self.tc, self.td, self.lambda_dep)
+        r.backward(r.dC, r.dD, None, self.grad)
+        if self.want_pose:
+            r.pose_grad()
+
+    def capture(self):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+
+    def run(self, n: int = 1, use_graph: bool = False):
+        if use_graph and self.graph is None:
+            self.capture()
+        for _ in range(n):
+            if use_graph:
+                self.graph.replay()
+            else:
+                self.step()
+
+
+def time_ms(fn, iters: int = 5, warmup: int = 2) -> float:
+    """Mean device time of fn() with CUDA events on the current stream."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(iters):
+        fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / iters
+
+
+def signature(cams, n_faces: int) -> str:
+    cams = np.asarray(cams, np.float64).reshape(-1, 6)
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    key = json.dumps([name, int(n_faces), sorted(map(tuple, cams[:, 4:6].astype(int).tolist()))])
+    return hashlib.sha1(key.encode()).hexdigest()[:16]
+
+
+def _cache_path() -> str:
+    return os.environ.get("TS_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "ts_gb300_autotune.json"))
+
+
+def autotune(m: Map, cams, poses, tgt_color, tgt_depth, grad: Optional[Map] = None,
+             tiles: Iterable = TILE_SHAPES, stages: Iterable = STAGE_SIZES, persistent=(False, True),
+             iters: int = 3, use_cache: bool = True, **param_overrides):
+    """Pick (tile_w, tile_h, tris_per_stage, persistent) for this workload by timing the full
+    forward + backward step.  Returns (best dict, all timings)."""
+    sig = signature(cams, m.n_faces)
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+        if sig in cache:
+            return cache[sig], None
+    results = []
+    best = None
+    for (tw, th) in tiles:
+        for S in stages:
+            for per in persistent:
+                p = B.ts_default_params(tile_w=tw, tile_h=th, tris_per_stage=S,
+                                        flags=(B_FLAG_PERSISTENT if per else 0), **param_overrides)
+                step = MultiViewStep(m, cams, poses, tgt_color, tgt_depth, p, grad)
+                ms = time_ms(step.step, iters=iters, warmup=1)
+                results.append(dict(tile_w=tw, tile_h=th, tris_per_stage=S, persistent=per, ms=ms))
+                if best is None or ms < best["ms"]:
+                    best = results[-1]
+                del step
+                torch.cuda.empty_cache()
+    if use_cache:
+        cache[sig] = best
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return best, results
+
+
+B_FLAG_PERSISTENT = 1  # TS_FLAG_PERSISTENT of include/ts_api.h
+
+
+def params_of(choice: dict, **overrides) -> B.TsRasterParams:
+    return B.ts_default_params(tile_w=choice["tile_w"], tile_h=choice["tile_h"],
+                               tris_per_stage=choice["tris_per_stage"],
+                               flags=B_FLAG_PERSISTENT if choice.get("persistent") else 0, **overrides)

@@ -88,6 +88,8 @@ SIGNATURES = {
     "ts_l1_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
     "ts_pose_apply": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
     "ts_l1_loss_noalloc": (_st, [C.POINTER(TsCamera), _i32, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
+    "ts_pose_adam": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
+                           _vp]),
     "ts_sync_status": (_st, [C.POINTER(TsPlan), _vp, _vp, C.POINTER(TsCounters)]),
     "ts_plan_layout": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp]),
     "ts_debug_copy": (_st, [C.POINTER(TsPlan), _vp, _i32, _vp, _sz, _vp]),
@@ -246,6 +248,11 @@ def ts_l1_loss_noalloc(cams, color, depth, tgt_color, tgt_depth, lambda_dep, los
     _check(lib().ts_l1_loss_noalloc(arr, len(arr), _ptr(color), _ptr(depth), _ptr(tgt_color), _ptr(tgt_depth),
                                     float(lambda_dep), _ptr(loss), _ptr(dC), _ptr(dD), _stream(stream)),
            "ts_l1_loss_noalloc")
+
+
+def ts_pose_adam(plan, poses, dtau, state, lr_rho, lr_theta, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().ts_pose_adam(C.byref(plan), _ptr(poses), _ptr(dtau), _ptr(state), float(lr_rho), float(lr_theta),
+                              float(beta1), float(beta2), float(eps), _stream(stream)), "ts_pose_adam")
 
 
 def ts_pose_apply(plan, poses, step, stream=None):

@@ -90,10 +90,8 @@ __global__ void __launch_bounds__(LOSS_T) k_loss_final(const TsView* __restrict_
   }
 }
 
-__global__ void k_pose_apply(ts_pose* poses, const float* __restrict__ step, int V) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
-  const float* st = step + 6 * v;
+// T <- Exp(-st) o T for one view (closed-form SE(3) exponential, st = (rho, theta)).
+__device__ void pose_left_step(ts_pose* poses, int v, const float st[6]) {
   const float rho[3] = {-st[0], -st[1], -st[2]};
   const float w0 = -st[3], w1 = -st[4], w2 = -st[5];
   const float a2 = w0 * w0 + w1 * w1 + w2 * w2;
@@ -136,6 +134,40 @@ __global__ void k_pose_apply(ts_pose* poses, const float* __restrict__ step, int
   poses[v] = Q;
 }
 
+__global__ void k_pose_apply(ts_pose* poses, const float* __restrict__ step, int V) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float st[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) st[i] = step[6 * v + i];
+  pose_left_step(poses, v, st);
+}
+
+// Adam on the manifold gradient dL/dtau of each view (Sec. 3.3 tracking; learning rates per
+// block: rho (translation) and theta (rotation), Table S5), then T <- Exp(-step) o T.
+// state[v] = first moments (6), second moments (6), step count (1); updated in place so the
+// iteration can be replayed from a CUDA graph.
+__global__ void k_pose_adam(ts_pose* poses, const float* __restrict__ dtau, float* __restrict__ state, int V,
+                            float lr_rho, float lr_theta, float b1, float b2, float eps) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float* s = state + 13 * v;
+  const float t = s[12] + 1.0f;
+  s[12] = t;
+  const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
+  float st[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float g = dtau[6 * v + i];
+    const float m = b1 * s[i] + (1.0f - b1) * g;
+    const float q = b2 * s[6 + i] + (1.0f - b2) * g * g;
+    s[i] = m;
+    s[6 + i] = q;
+    st[i] = (i < 3 ? lr_rho : lr_theta) * (m / c1) / (sqrtf(q / c2) + eps);
+  }
+  pose_left_step(poses, v, st);
+}
+
 }  // namespace
 
 cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* color, const float* depth,
@@ -150,5 +182,11 @@ cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* c
 
 cudaError_t ts_launch_pose_apply(const TsPlanImpl* p, ts_pose* poses, const float* step, cudaStream_t s) {
   k_pose_apply<<<(p->V + 63) / 64, 64, 0, s>>>(poses, step, p->V);
+  return cudaGetLastError();
+}
+
+cudaError_t ts_launch_pose_adam(const TsPlanImpl* p, ts_pose* poses, const float* dtau, float* state, float lr_rho,
+                                float lr_theta, float b1, float b2, float eps, cudaStream_t s) {
+  k_pose_adam<<<(p->V + 63) / 64, 64, 0, s>>>(poses, dtau, state, p->V, lr_rho, lr_theta, b1, b2, eps);
   return cudaGetLastError();
 }

@@ -1,11 +1,11 @@
-// k_render.cu -- Eq. 3-4 forward blend and its adjoint, one CTA per (view, tile).
+// k_render.cu -- Eq. 3-4 forward blend and its adjoint, one CTA per (view, tile) at a time.
 //
 // Staging: the tile's depth-sorted face ids select 128-byte records that one warp copies into
 // shared memory with TMA bulk copies (cp.async.bulk, one per record) completing on an mbarrier;
 // two buffers alternate so the next stage streams in while the current one is blended.  Each
-// warp owns an 8 x 4 pixel sub-block of the tile; a per-record bit mask (computed once per
-// stage from the face's pixel box) lets a warp skip faces that cannot reach its sub-block with a
-// single uniform branch.
+// warp owns an 8 x 4 pixel sub-block of the tile; per stage, a mask per record says which
+// sub-blocks can contain one of the face's covered pixel centres, and each warp walks only the
+// set bits of its own ballot over the stage.
 //
 // Forward: per pixel, front to back: window (Eq. 3) from cancellation-free edge functions,
 // alpha = min(alpha_max, o_F I), skip below alpha_min, stop before the face that would take T
@@ -18,6 +18,9 @@
 // per-face sums (barycentric-weighted gradients of the edge, colour and depth interpolants, and
 // of o_F).  A warp reduces the 24-word vector with a 27-shuffle reduce-scatter, leaving one sum
 // per lane, and issues a single 24-lane atomic add into the face's accumulator.
+//
+// Launch forms: one CTA per tile, or persistent CTAs (as many as fit on the GPU) that take tiles
+// from a device counter, keeping their mbarriers across tiles.
 #include <algorithm>
 
 #include "ts_internal.cuh"
@@ -28,6 +31,7 @@ struct RenderArgs {
   const TsView* views;
   int V;
   long long M, VM;
+  long long n_tiles;
   const float4* frec;
   const uint32_t* ids;
   const uint2* ranges;
@@ -43,14 +47,24 @@ struct RenderArgs {
   float sigma, alpha_min, alpha_max, T_min;
   float bg0, bg1, bg2;
   int S;
+  unsigned int* counter;
   TsDevHeader* hdr;
 };
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Shared state of a render CTA.
+struct RenderSmem {
+  uint64_t bar[2];
+  uint32_t smask[2][128];
+  int view;
+  int nmax;
+  int next_tile;
+  int fail;
+};
+
 template <int TW, int TH>
 struct TileGeom {
-  static constexpr int NT = TW * TH;
   static constexpr int NSBX = TW / 8;
   int view, X0, Y0, x, y;
   bool inimg;
@@ -59,12 +73,11 @@ struct TileGeom {
 };
 
 template <int TW, int TH>
-__device__ __forceinline__ TileGeom<TW, TH> tile_geom(const RenderArgs& a, int* s_view) {
+__device__ __forceinline__ TileGeom<TW, TH> tile_geom(const RenderArgs& a, long long tile, RenderSmem& sm) {
   TileGeom<TW, TH> g;
-  const long long tile = blockIdx.x;
-  if (threadIdx.x == 0) *s_view = ts_find_view(a.views, a.V, tile);
+  if (threadIdx.x == 0) sm.view = ts_find_view(a.views, a.V, tile);
   __syncthreads();
-  g.view = *s_view;
+  g.view = sm.view;
   g.vw = a.views[g.view];
   const long long lt = tile - g.vw.tile_off;
   const int ty = (int)(lt / g.vw.TX), tx = (int)(lt - (long long)ty * g.vw.TX);
@@ -141,51 +154,50 @@ __device__ __forceinline__ void count_add(unsigned long long* ctr, unsigned v) {
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
 }
 
+// Wait for stage sequence number `seq` (buffer seq & 1, phase (seq >> 1) & 1) in every thread.
+// Returns false on timeout (after latching the error and letting the late copies land).
+__device__ __forceinline__ bool wait_stage(const RenderArgs& a, RenderSmem& sm, int seq) {
+  const bool ok = ts_mbar_wait(&sm.bar[seq & 1], (uint32_t)(seq >> 1) & 1u);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicOr(&a.hdr->error_bits, TS_ERRBIT_TIMEOUT);
+      ts_mbar_wait(&sm.bar[seq & 1], (uint32_t)(seq >> 1) & 1u);
+    }
+    return false;
+  }
+  return true;
+}
+
+// Forward of one tile; seq counts the stages this CTA has waited for so far (mbarrier phases).
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
-  constexpr int NT = TW * TH;
-  extern __shared__ __align__(128) float4 smrec[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int s_view;
-  __shared__ uint32_t smask[2][128];
-  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, &s_view);
+__device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
+                                         int& seq) {
+  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint2 rg = a.ranges[blockIdx.x];
+  const uint2 rg = a.ranges[tile];
   const int n = (int)(rg.y - rg.x);
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
   int nl = 0;
   bool done = !g.inimg;
   unsigned contrib = 0;
+  bool ok = true;
   if (n > 0) {
     const int S = a.S;
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
-    if (threadIdx.x == 0) {
-      ts_mbar_init(&bar[0], 1);
-      ts_mbar_init(&bar[1], 1);
-      ts_fence_mbar_init();
-    }
-    __syncthreads();
-    if (warp == 0) issue_stage(a, smrec, bar, 0, 0, rg.x, n, vbase);
+    if (warp == 0) issue_stage(a, smrec, sm.bar, seq & 1, 0, rg.x, n, vbase);
     for (int st = 0; st < nst; ++st) {
-      const int b = st & 1;
+      const int b = seq & 1;
       const int cnt = min(S, n - st * S);
-      const bool ok = ts_mbar_wait(&bar[b], (uint32_t)(st >> 1) & 1u);
-      if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) {
-          atomicOr(&a.hdr->error_bits, TS_ERRBIT_TIMEOUT);
-          ts_mbar_wait(&bar[b], (uint32_t)(st >> 1) & 1u);  // let the late copies land before leaving
-        }
-        return;
-      }
+      if (!wait_stage(a, sm, seq)) { ok = false; break; }
+      ++seq;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
-      stage_masks<TW, TH>(rb, smask[b], cnt, g.X0, g.Y0);
+      stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
       __syncthreads();
-      if (warp == 0 && st + 1 < nst) issue_stage(a, smrec, bar, b ^ 1, st + 1, rg.x, n, vbase);
-      // this warp visits only the stage's faces whose mask has its bit (front to back)
+      if (warp == 0 && st + 1 < nst) issue_stage(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase);
       for (int q = 0; q * 32 < cnt; ++q) {
         const int jq = q * 32 + lane;
-        unsigned bits = __ballot_sync(FULL, jq < cnt && ((smask[b][min(jq, cnt - 1)] >> warp) & 1u));
+        unsigned bits = __ballot_sync(FULL, jq < cnt && ((sm.smask[b][min(jq, cnt - 1)] >> warp) & 1u));
         while (bits) {
           const int j = q * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
@@ -211,15 +223,16 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
         }
       }
       if (__syncthreads_count(!done) == 0) {
-        if (threadIdx.x == 0 && st + 1 < nst) {
-          if (!ts_mbar_wait(&bar[b ^ 1], (uint32_t)((st + 1) >> 1) & 1u)) atomicOr(&a.hdr->error_bits, TS_ERRBIT_TIMEOUT);
+        if (st + 1 < nst) {  // a prefetched stage is in flight: consume its phase before leaving
+          if (!wait_stage(a, sm, seq)) { ok = false; break; }
+          ++seq;
         }
         break;
       }
     }
   }
   count_add(&a.hdr->fwd_contrib, contrib);
-  if (g.inimg) {
+  if (ok && g.inimg) {
     const long long HW = (long long)g.vw.W * g.vw.H;
     const long long pi = (long long)g.y * g.vw.W + g.x;
     const long long o = g.vw.pix_off + pi;
@@ -234,19 +247,15 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
     a.tfin[o] = T;
     a.nlast[o] = nl;
   }
-  (void)NT;
+  return ok;
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
-  extern __shared__ __align__(128) float4 smrec[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int s_view;
-  __shared__ int s_nmax;
-  __shared__ uint32_t smask[2][128];
-  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, &s_view);
+__device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
+                                         int& seq) {
+  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint2 rg = a.ranges[blockIdx.x];
+  const uint2 rg = a.ranges[tile];
   float T = 0.f, Sacc = 0.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
   int nl = 0;
   if (g.inimg) {
@@ -263,164 +272,210 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
     gA = a.dA ? a.dA[o] : 0.f;
     Sacc = T * (gC0 * a.bg0 + gC1 * a.bg1 + gC2 * a.bg2);
   }
-  if (threadIdx.x == 0) s_nmax = 0;
+  if (threadIdx.x == 0) sm.nmax = 0;
   __syncthreads();
   {
     const int m = __reduce_max_sync(FULL, (unsigned)nl);
-    if (lane == 0 && m) atomicMax(&s_nmax, m);
+    if (lane == 0 && m) atomicMax(&sm.nmax, m);
   }
   __syncthreads();
   // positions come from the forward pass over the same lists; clamp in case the caller did not
   // run it after the last ts_bin
-  const int n = min(s_nmax, (int)(rg.y - rg.x));
+  const int n = min(sm.nmax, (int)(rg.y - rg.x));
   unsigned contrib = 0;
+  bool ok = true;
   if (n > 0) {
     const int S = a.S;
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
-    if (threadIdx.x == 0) {
-      ts_mbar_init(&bar[0], 1);
-      ts_mbar_init(&bar[1], 1);
-      ts_fence_mbar_init();
-    }
-    __syncthreads();
-    if (warp == 0) issue_stage(a, smrec, bar, 0, nst - 1, rg.x, n, vbase);
+    if (warp == 0) issue_stage(a, smrec, sm.bar, seq & 1, nst - 1, rg.x, n, vbase);
     const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
     const int q = lane & 3;
     const int widx = (hi16 ? 12 : 0) + (hi8 ? 6 : 0) + (hi4 ? 3 : 0) + q;
     for (int k = 0; k < nst; ++k) {
       const int st = nst - 1 - k;
-      const int b = k & 1;
+      const int b = seq & 1;
       const int cnt = min(S, n - st * S);
-      const bool ok = ts_mbar_wait(&bar[b], (uint32_t)(k >> 1) & 1u);
-      if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) {
-          atomicOr(&a.hdr->error_bits, TS_ERRBIT_TIMEOUT);
-          ts_mbar_wait(&bar[b], (uint32_t)(k >> 1) & 1u);  // let the late copies land before leaving
-        }
-        return;
-      }
+      if (!wait_stage(a, sm, seq)) { ok = false; break; }
+      ++seq;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
-      stage_masks<TW, TH>(rb, smask[b], cnt, g.X0, g.Y0);
+      stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
       __syncthreads();
-      if (warp == 0 && k + 1 < nst) issue_stage(a, smrec, bar, b ^ 1, st - 1, rg.x, n, vbase);
+      if (warp == 0 && k + 1 < nst) issue_stage(a, smrec, sm.bar, b ^ 1, st - 1, rg.x, n, vbase);
       // this warp visits only the stage's faces whose mask has its bit (back to front)
       for (int qq = (cnt - 1) >> 5; qq >= 0; --qq) {
         const int jq = qq * 32 + lane;
-        unsigned bits = __ballot_sync(FULL, jq < cnt && ((smask[b][min(jq, cnt - 1)] >> warp) & 1u));
+        unsigned bits = __ballot_sync(FULL, jq < cnt && ((sm.smask[b][min(jq, cnt - 1)] >> warp) & 1u));
         while (bits) {
-        const int hb = 31 - __clz(bits);
-        bits &= ~(1u << hb);
-        const int j = qq * 32 + hb;
-        const float* r = rb + j * TS_REC_WORDS;
-        const int pos = st * S + j;
-        bool cb = false;
-        TsPix e;
-        float I = 0.f, al = 0.f;
-        if (pos < nl) {
-          e = ts_eval_edges(r, g.px, g.py);
-          if (e.m > 0.f) {
-            I = ts_window(e.m, a.sigma);
-            al = fminf(r[R_OF] * I, a.alpha_max);
-            cb = al >= a.alpha_min;
+          const int hb = 31 - __clz(bits);
+          bits &= ~(1u << hb);
+          const int j = qq * 32 + hb;
+          const float* r = rb + j * TS_REC_WORDS;
+          const int pos = st * S + j;
+          bool cb = false;
+          TsPix e;
+          float I = 0.f, al = 0.f;
+          if (pos < nl) {
+            e = ts_eval_edges(r, g.px, g.py);
+            if (e.m > 0.f) {
+              I = ts_window(e.m, a.sigma);
+              al = fminf(r[R_OF] * I, a.alpha_max);
+              cb = al >= a.alpha_min;
+            }
+          }
+          if (!__any_sync(FULL, cb)) continue;
+          float v[24];
+#pragma unroll
+          for (int i = 0; i < 24; ++i) v[i] = 0.f;
+          if (cb) {
+            const float oma = 1.f - al;
+            const float Tn = T / oma;
+            const float invD = r[R_INVD];
+            const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
+            const float c0 = l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2];
+            const float c1 = l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1];
+            const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
+            const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
+            const float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
+            const float dal = val * Tn - Sacc / oma;
+            Sacc += val * al * Tn;
+            T = Tn;
+            const float w = al * Tn;
+            const float w0 = gC0 * w, w1 = gC1 * w, w2 = gC2 * w, wz = gD * w;
+            v[G_C + 0] = w0 * l0; v[G_C + 1] = w0 * l1; v[G_C + 2] = w0 * l2;
+            v[G_C + 3] = w1 * l0; v[G_C + 4] = w1 * l1; v[G_C + 5] = w1 * l2;
+            v[G_C + 6] = w2 * l0; v[G_C + 7] = w2 * l1; v[G_C + 8] = w2 * l2;
+            v[G_Z + 0] = wz * l0; v[G_Z + 1] = wz * l1; v[G_Z + 2] = wz * l2;
+            v[G_CNT] = 1.f;
+            const float oF = r[R_OF];
+            if (!(oF * I > a.alpha_max)) {
+              v[G_O] = dal * I;
+              const float dI = dal * oF;
+              const float dm = (a.sigma == 0.5f) ? dI * 0.5f / I : dI * a.sigma * I / e.m;
+              const float d0 = dm * l0, d1 = dm * l1, d2 = dm * l2;
+              v[G_E + 0] = e.arg == 0 ? d0 : 0.f; v[G_E + 1] = e.arg == 0 ? d1 : 0.f; v[G_E + 2] = e.arg == 0 ? d2 : 0.f;
+              v[G_E + 3] = e.arg == 1 ? d0 : 0.f; v[G_E + 4] = e.arg == 1 ? d1 : 0.f; v[G_E + 5] = e.arg == 1 ? d2 : 0.f;
+              v[G_E + 6] = e.arg == 2 ? d0 : 0.f; v[G_E + 7] = e.arg == 2 ? d1 : 0.f; v[G_E + 8] = e.arg == 2 ? d2 : 0.f;
+            }
+            ++contrib;
+          }
+          // reduce-scatter: 24 -> 12 -> 6 -> 3 values per lane, then a butterfly over 4 lanes
+#pragma unroll
+          for (int i = 0; i < 12; ++i) {
+            const float send = hi16 ? v[i] : v[i + 12];
+            const float keep = hi16 ? v[i + 12] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, 16);
+          }
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            const float send = hi8 ? v[i] : v[i + 6];
+            const float keep = hi8 ? v[i + 6] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, 8);
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const float send = hi4 ? v[i] : v[i + 3];
+            const float keep = hi4 ? v[i + 3] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, 4);
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            v[i] += __shfl_xor_sync(FULL, v[i], 2);
+            v[i] += __shfl_xor_sync(FULL, v[i], 1);
+          }
+          const float mine = q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
+          if (q < 3 && mine != 0.f) {
+            const uint32_t slot = __float_as_uint(r[R_SLOT]);
+            if ((long long)slot < a.VM) {
+              atomicAdd(a.grad + (size_t)slot * TS_GRAD_WORDS + widx, mine);
+            } else {
+              atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
+            }
           }
         }
-        if (!__any_sync(FULL, cb)) continue;
-        float v[24];
-#pragma unroll
-        for (int i = 0; i < 24; ++i) v[i] = 0.f;
-        if (cb) {
-          const float oma = 1.f - al;
-          const float Tn = T / oma;
-          const float invD = r[R_INVD];
-          const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
-          const float c0 = l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2];
-          const float c1 = l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1];
-          const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
-          const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
-          const float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
-          const float dal = val * Tn - Sacc / oma;
-          Sacc += val * al * Tn;
-          T = Tn;
-          const float w = al * Tn;
-          const float w0 = gC0 * w, w1 = gC1 * w, w2 = gC2 * w, wz = gD * w;
-          v[G_C + 0] = w0 * l0; v[G_C + 1] = w0 * l1; v[G_C + 2] = w0 * l2;
-          v[G_C + 3] = w1 * l0; v[G_C + 4] = w1 * l1; v[G_C + 5] = w1 * l2;
-          v[G_C + 6] = w2 * l0; v[G_C + 7] = w2 * l1; v[G_C + 8] = w2 * l2;
-          v[G_Z + 0] = wz * l0; v[G_Z + 1] = wz * l1; v[G_Z + 2] = wz * l2;
-          v[G_CNT] = 1.f;
-          const float oF = r[R_OF];
-          if (!(oF * I > a.alpha_max)) {
-            v[G_O] = dal * I;
-            const float dI = dal * oF;
-            const float dm = (a.sigma == 0.5f) ? dI * 0.5f / I : dI * a.sigma * I / e.m;
-            const float d0 = dm * l0, d1 = dm * l1, d2 = dm * l2;
-            v[G_E + 0] = e.arg == 0 ? d0 : 0.f; v[G_E + 1] = e.arg == 0 ? d1 : 0.f; v[G_E + 2] = e.arg == 0 ? d2 : 0.f;
-            v[G_E + 3] = e.arg == 1 ? d0 : 0.f; v[G_E + 4] = e.arg == 1 ? d1 : 0.f; v[G_E + 5] = e.arg == 1 ? d2 : 0.f;
-            v[G_E + 6] = e.arg == 2 ? d0 : 0.f; v[G_E + 7] = e.arg == 2 ? d1 : 0.f; v[G_E + 8] = e.arg == 2 ? d2 : 0.f;
-          }
-          ++contrib;
-        }
-        // reduce-scatter: 24 -> 12 -> 6 -> 3 values per lane, then a butterfly over 4 lanes
-#pragma unroll
-        for (int i = 0; i < 12; ++i) {
-          const float send = hi16 ? v[i] : v[i + 12];
-          const float keep = hi16 ? v[i + 12] : v[i];
-          v[i] = keep + __shfl_xor_sync(FULL, send, 16);
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          const float send = hi8 ? v[i] : v[i + 6];
-          const float keep = hi8 ? v[i + 6] : v[i];
-          v[i] = keep + __shfl_xor_sync(FULL, send, 8);
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const float send = hi4 ? v[i] : v[i + 3];
-          const float keep = hi4 ? v[i + 3] : v[i];
-          v[i] = keep + __shfl_xor_sync(FULL, send, 4);
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          v[i] += __shfl_xor_sync(FULL, v[i], 2);
-          v[i] += __shfl_xor_sync(FULL, v[i], 1);
-        }
-        const float mine = q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
-        if (q < 3 && mine != 0.f) {
-          const uint32_t slot = __float_as_uint(r[R_SLOT]);
-          if ((long long)slot < a.VM) {
-            atomicAdd(a.grad + (size_t)slot * TS_GRAD_WORDS + widx, mine);
-          } else {
-            atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
-          }
-        }
-        }  // while bits
-      }    // stage words
+      }
     }
   }
   count_add(&a.hdr->bwd_contrib, contrib);
+  return ok;
+}
+
+__device__ __forceinline__ void init_bars(RenderSmem& sm) {
+  if (threadIdx.x == 0) {
+    ts_mbar_init(&sm.bar[0], 1);
+    ts_mbar_init(&sm.bar[1], 1);
+    ts_fence_mbar_init();
+  }
+  __syncthreads();
+}
+
+// Next tile of a persistent CTA (the same value in every thread), or -1 when none is left.
+__device__ __forceinline__ long long next_tile(const RenderArgs& a, RenderSmem& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) sm.next_tile = (int)atomicAdd(a.counter, 1u);
+  __syncthreads();
+  return sm.next_tile < a.n_tiles ? (long long)sm.next_tile : -1;
+}
+
+template <int TW, int TH, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
+  extern __shared__ __align__(128) float4 smrec[];
+  __shared__ RenderSmem sm;
+  init_bars(sm);
+  int seq = 0;
+  if (!PERSIST) {
+    fwd_tile<TW, TH>(a, blockIdx.x, smrec, sm, seq);
+    return;
+  }
+  for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
+    if (!fwd_tile<TW, TH>(a, t, smrec, sm, seq)) return;
+}
+
+template <int TW, int TH, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
+  extern __shared__ __align__(128) float4 smrec[];
+  __shared__ RenderSmem sm;
+  init_bars(sm);
+  int seq = 0;
+  if (!PERSIST) {
+    bwd_tile<TW, TH>(a, blockIdx.x, smrec, sm, seq);
+    return;
+  }
+  for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
+    if (!bwd_tile<TW, TH>(a, t, smrec, sm, seq)) return;
 }
 
 template <int TW, int TH>
-cudaError_t launch_pair(bool fwd, const RenderArgs& a, long long n_tiles, cudaStream_t s) {
+cudaError_t launch_pair(bool fwd, bool persist, const RenderArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)2 * a.S * 128;
-  if (n_tiles == 0) return cudaSuccess;
-  if (fwd) {
-    k_render_fwd<TW, TH><<<(unsigned)n_tiles, TW * TH, smem, s>>>(a);
-  } else {
-    k_render_bwd<TW, TH><<<(unsigned)n_tiles, TW * TH, smem, s>>>(a);
+  if (a.n_tiles == 0) return cudaSuccess;
+  if (!persist) {
+    if (fwd) k_render_fwd<TW, TH, false><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
+    else k_render_bwd<TW, TH, false><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
+    return cudaGetLastError();
   }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<TW, TH, true>, TW * TH, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<TW, TH, true>, TW * TH, smem);
+  const long long grid = std::max(1LL, std::min<long long>(a.n_tiles, (long long)sms * std::max(per_sm, 1)));
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  if (fwd) k_render_fwd<TW, TH, true><<<(unsigned)grid, TW * TH, smem, s>>>(a);
+  else k_render_bwd<TW, TH, true><<<(unsigned)grid, TW * TH, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t dispatch(bool fwd, const TsPlanImpl* p, const RenderArgs& a, cudaStream_t s) {
   const int tw = p->prm.tile_w, th = p->prm.tile_h;
-  if (tw == 16 && th == 16) return launch_pair<16, 16>(fwd, a, p->n_tiles, s);
-  if (tw == 8 && th == 8) return launch_pair<8, 8>(fwd, a, p->n_tiles, s);
-  if (tw == 16 && th == 8) return launch_pair<16, 8>(fwd, a, p->n_tiles, s);
-  if (tw == 32 && th == 8) return launch_pair<32, 8>(fwd, a, p->n_tiles, s);
-  if (tw == 16 && th == 32) return launch_pair<16, 32>(fwd, a, p->n_tiles, s);
-  if (tw == 32 && th == 16) return launch_pair<32, 16>(fwd, a, p->n_tiles, s);
+  const bool persist = (p->prm.flags & TS_FLAG_PERSISTENT) != 0;
+  if (tw == 16 && th == 8) return launch_pair<16, 8>(fwd, persist, a, s);
+  if (tw == 16 && th == 16) return launch_pair<16, 16>(fwd, persist, a, s);
+  if (tw == 8 && th == 8) return launch_pair<8, 8>(fwd, persist, a, s);
+  if (tw == 32 && th == 8) return launch_pair<32, 8>(fwd, persist, a, s);
+  if (tw == 16 && th == 32) return launch_pair<16, 32>(fwd, persist, a, s);
+  if (tw == 32 && th == 16) return launch_pair<32, 16>(fwd, persist, a, s);
   return cudaErrorInvalidValue;
 }
 
@@ -430,6 +485,7 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.V = p->V;
   a.M = p->M;
   a.VM = (long long)p->V * p->M;
+  a.n_tiles = p->n_tiles;
   a.frec = w.frec;
   a.ids = w.vals[ts_sort_final_buffer(p)];
   a.ranges = w.ranges;
@@ -447,6 +503,7 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.bg2 = p->prm.bg[2];
   a.S = p->prm.tris_per_stage;
   a.hdr = w.hdr;
+  a.counter = &w.hdr->tile_counter;
   return a;
 }
 

@@ -65,7 +65,8 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   if (!valid_tile(prm->tile_w, prm->tile_h)) return TS_ERR_INVALID_ARG;
   if (prm->tris_per_stage != 32 && prm->tris_per_stage != 64 && prm->tris_per_stage != 128) return TS_ERR_INVALID_ARG;
   if (!(prm->sigma > 0.0f) || !(prm->alpha_max > 0.0f && prm->alpha_max < 1.0f) || !(prm->alpha_min >= 0.0f) ||
-      !(prm->T_min >= 0.0f && prm->T_min < 1.0f) || !(prm->z_near > 0.0f) || !(prm->r_min >= 0.0f) || prm->flags != 0)
+      !(prm->T_min >= 0.0f && prm->T_min < 1.0f) || !(prm->z_near > 0.0f) || !(prm->r_min >= 0.0f) ||
+      (prm->flags & ~TS_FLAG_PERSISTENT) != 0)
     return TS_ERR_INVALID_ARG;
   if (pair_capacity < 0) return TS_ERR_INVALID_ARG;
   memset(plan, 0, sizeof(ts_plan));
@@ -253,6 +254,17 @@ ts_status ts_pose_apply(const ts_plan* plan, ts_pose* poses, const float* step, 
   const TsPlanImpl* p = impl(plan);
   if (!p || !poses || !step) return TS_ERR_INVALID_ARG;
   return cuda_status(ts_launch_pose_apply(p, poses, step, (cudaStream_t)stream));
+}
+
+ts_status ts_pose_adam(const ts_plan* plan, ts_pose* poses, const float* dtau, float* state, float lr_rho,
+                       float lr_theta, float beta1, float beta2, float eps, ts_stream stream) {
+  const TsPlanImpl* p = impl(plan);
+  if (!p || !poses || !dtau || !state) return TS_ERR_INVALID_ARG;
+  if (!(lr_rho >= 0.f) || !(lr_theta >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+      !(eps > 0.f))
+    return TS_ERR_INVALID_ARG;
+  return cuda_status(ts_launch_pose_adam(p, poses, dtau, state, lr_rho, lr_theta, beta1, beta2, eps,
+                                         (cudaStream_t)stream));
 }
 
 ts_status ts_sync_status(const ts_plan* plan, void* ws, ts_stream stream, ts_counters* out) {

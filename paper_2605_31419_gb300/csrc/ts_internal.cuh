@@ -65,7 +65,8 @@ struct TsDevHeader {
   const float *px, *py, *pz, *cr, *cg, *cb, *op;
   const int32_t* faces;
   long long n_vertices;
-  unsigned int pad[14];
+  unsigned int tile_counter;  // work counter of the persistent raster launches
+  unsigned int pad[13];
 };
 
 struct TsPlanImpl {
@@ -153,6 +154,8 @@ cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* c
                               const float* tc, const float* td, float lambda_dep, float* loss, float* dC,
                               float* dD, cudaStream_t s);
 cudaError_t ts_launch_pose_apply(const TsPlanImpl* p, ts_pose* poses, const float* step, cudaStream_t s);
+cudaError_t ts_launch_pose_adam(const TsPlanImpl* p, ts_pose* poses, const float* dtau, float* state, float lr_rho,
+                                float lr_theta, float b1, float b2, float eps, cudaStream_t s);
 int ts_sort_final_buffer(const TsPlanImpl* p);  // 0 or 1: which key/val buffer holds the sorted pairs
 int ts_pose_blocks(long long M);                 // blocks of the projection-backward kernel
 

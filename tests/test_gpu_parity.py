@@ -230,3 +230,19 @@ def test_full_size_room_sampled_views(oracle, views):
     assert_grad(g["dcol"], r["dcol"], "dcol")
     assert_grad(g["dopa"], r["dopa"], "dopa")
     del pack_targets
+
+
+@pytest.mark.parametrize("name", ["c1", "ragged_room"])
+def test_persistent_launch_matches_oracle(name):
+    """Persistent raster CTAs taking tiles from a device counter give the same images."""
+    sc, p, po, g, r = run(name, (16, 8), 64, flags=1)
+    for k in ("color", "depth", "alpha", "T_final"):
+        assert_images(g[k], r[k], k)
+    assert np.array_equal(g["n_last"], r["n_last"])
+    assert_grad(g["dpos"], r["dpos"], "dpos")
+    assert_grad(g["dcol"], r["dcol"], "dcol")
+    assert_grad(g["dopa"], r["dopa"], "dopa")
+    assert_pose_grad(g["dtau"], r["dtau"], r["dtau_abs"])
+    _, _, _, g1, _ = run(name, (16, 8), 64)
+    for k in ("color", "depth", "alpha"):
+        assert np.array_equal(g[k], g1[k])
