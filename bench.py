@@ -221,6 +221,46 @@ def bench_tracking(ts, torch, dev, n_hyp=64, iters=100):
             "median_error_after": {"cm": float(np.median(e1[:, 0]) * 100), "deg": float(np.median(e1[:, 1]))}}
 
 
+def bench_serving(ts, torch, dev, rates=(200, 500, 1000, 2000), seconds=2.0, n_faces=2_000_000):
+    """Serving: device-resident 2M-face map; Poisson arrivals of render (one forward) and track
+    (10 pose iterations) requests, resolutions uniform over 256x256, 640x480 and 1200x680,
+    poses on a seeded trajectory; continuous batching; p50/p99 latency and Mpix/s per rate."""
+    from ts_synth.scenes import perturb_pose, request_stream, room_map, trajectory_poses
+    res = ((256, 256, 256.0), (640, 480, 525.0), (1200, 680, 600.0))
+    pos, col, opa = room_map(6, n_faces)
+    m = ts.Map.from_numpy(pos, col, opa, device=dev)
+    n_poses = 16
+    gts = trajectory_poses(1006, n_poses)
+    targets = {}
+    for (W_, H_, f) in res:
+        r = ts.Rasterizer(np.array([[f, f, W_ / 2, H_ / 2, W_, H_]]), m.n_faces)
+        for k in range(n_poses):
+            C, D, _ = r.forward(m, ts.poses_tensor(gts[k][None, :], device=dev))
+            targets[(W_, H_, k)] = (C.clone().view(3, H_, W_), D.clone().view(H_, W_))
+        del r
+    srv = ts.Server(m, max_views=32, max_pixels=16_000_000, track_iters=10)
+    out = {"workload": f"2M-face room, Poisson render/track 50/50, {seconds:.0f} s per rate, resolutions "
+                       "256x256 / 640x480 / 1200x680, track = 10 pose iterations"}
+    rng = np.random.default_rng(6)
+    for rate in rates:
+        reqs = []
+        for i, d in enumerate(request_stream(6 + rate, rate, seconds, resolutions=res, n_poses=n_poses)):
+            W_, H_, f = d["W"], d["H"], d["f"]
+            cam = np.array([f, f, W_ / 2, H_ / 2, W_, H_])
+            gt = gts[d["pose_index"]]
+            if d["kind"] == "render":
+                reqs.append(ts.Request(i, "render", cam, gt, d["t"]))
+            else:
+                tc, td = targets[(W_, H_, d["pose_index"])]
+                reqs.append(ts.Request(i, "track", cam, perturb_pose(gt, rng, 0.02, 1.0), d["t"], tc, td))
+        srv.stats.update(steps=0, pixels=0, rejected_for_memory=0)
+        srv.run(reqs, realtime=True, max_seconds=seconds * 5)
+        st = ts.latency_stats(reqs, srv.stats["seconds"])
+        st["steps"] = srv.stats["steps"]
+        out[f"{rate}_req_s"] = st
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -416,6 +456,8 @@ def main():
             torch.cuda.empty_cache()
             line["mapping_window"] = bench_mapping_window(ts, torch, dev)
             line["tracking"] = bench_tracking(ts, torch, dev)
+            torch.cuda.empty_cache()
+            line["serving"] = bench_serving(ts, torch, dev)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(sc)
         print(json.dumps(line), flush=True)

@@ -138,8 +138,9 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
 /* Bytes of device workspace the plan needs (256-byte aligned base required). */
 size_t ts_workspace_size(const ts_plan* plan);
 
-/* Zero the workspace's persistent state (counters and gradient accumulators).  Call once after
- * allocating the workspace and again after any device-side error.  Asynchronous. */
+/* Zero the workspace's persistent state (counters, error word, per-pixel backward state).  Call
+ * once after allocating the workspace and again after any device-side error; a workspace may then
+ * be reused by plans of any layout that fits it.  Asynchronous. */
 ts_status ts_workspace_init(const ts_plan* plan, void* ws, size_t ws_bytes, ts_stream stream);
 
 /* Eq. 1-3 per (view, face): rigid transform, projection, culling, the face's screen-space

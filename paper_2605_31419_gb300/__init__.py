@@ -19,3 +19,4 @@ from .rasterizer import Map, Rasterizer, poses_tensor  # noqa: E402,F401
 from .autograd import RenderFunction, render  # noqa: E402,F401
 from .tracking import Tracker, pose_error  # noqa: E402,F401
 from .batch import MultiViewStep, autotune, params_of  # noqa: E402,F401
+from .serve import Request, Server, latency_stats  # noqa: E402,F401

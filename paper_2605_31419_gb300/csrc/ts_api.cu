@@ -173,8 +173,10 @@ ts_status ts_workspace_init(const ts_plan* plan, void* ws, size_t ws_bytes, ts_s
   const TsPlanImpl* p = impl(plan);
   if (!p || !ws_ok(p, ws, ws_bytes)) return TS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  // the header (counters, error word) and the per-pixel state the backward reads; every other
+  // region is written before it is read within a call sequence (the projection clears the
+  // gradient slots of the visible faces)
   cudaError_t e = cudaMemsetAsync((char*)ws + p->o_hdr, 0, sizeof(TsDevHeader), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync((char*)ws + p->o_grad, 0, (size_t)p->V * p->M * TS_GRAD_WORDS * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)ws + p->o_tfin, 0, p->o_grad - p->o_tfin, s);
   return cuda_status(e);
 }
