@@ -56,6 +56,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t: float, device=None) -> float:
+    """The job's step time: the maximum of the ranks' times (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t)
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(pixels_per_rank: int, world: int, t_step: float) -> float:
+    """Whole-job Mpix/s: every rank renders its own replica of the workload (weak scaling)."""
+    return pixels_per_rank * world / t_step / 1e6
+
+
 def scene(args):
     from ts_synth import room_scene
     return room_scene(3, args.faces, args.views, W, H, F, target_seed=4)
@@ -349,14 +365,10 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ts.ts_set_stage_events(rast.plan, None)
-    t_step = float(np.sum(step_ms)) / args.steps / 1e3
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(float(np.sum(step_ms)) / args.steps / 1e3, dev if world > 1 else None)
     stage_ms /= args.steps
     pixels = sc.pixels()
-    value = pixels * world / t_step / 1e6
+    value = job_value(pixels, world, t_step)
 
     # -- plain per-view: the same work, one view per call sequence (its own plan) ------------------
     plain_ms = None

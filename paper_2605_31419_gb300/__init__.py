@@ -10,7 +10,7 @@ from .binding import (  # noqa: F401
     ts_render_fwd, ts_render_bwd, ts_pose_grad, ts_l1_loss, ts_l1_loss_noalloc, ts_pose_apply, ts_pose_adam,
     ts_sync_status,
     ts_plan_layout,
-    ts_debug_copy, ts_set_stage_events, ts_status_string,
+    ts_debug_copy, ts_debug_timeout_probe, ts_set_stage_events, ts_status_string,
 )
 
 binding.lib()  # fail loudly here if libts.so is missing

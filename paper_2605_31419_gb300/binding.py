@@ -94,6 +94,7 @@ SIGNATURES = {
     "ts_plan_layout": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp]),
     "ts_debug_copy": (_st, [C.POINTER(TsPlan), _vp, _i32, _vp, _sz, _vp]),
     "ts_set_stage_events": (_st, [C.POINTER(TsPlan), _vp]),
+    "ts_debug_timeout_probe": (_st, [C.POINTER(TsPlan), _vp, C.c_uint32, _vp]),
     "ts_status_string": (C.c_char_p, [_st]),
 }
 
@@ -272,6 +273,11 @@ def ts_sync_status(plan, ws, stream=None, raise_on_error: bool = True) -> dict:
 def ts_debug_copy(plan, ws, what: str, dst, stream=None):
     _check(lib().ts_debug_copy(C.byref(plan), _ptr(ws), DEBUG[what], _ptr(dst), dst.numel() * dst.element_size(),
                                _stream(stream)), f"ts_debug_copy({what})")
+
+
+def ts_debug_timeout_probe(plan, ws, limit_us: int, stream=None):
+    _check(lib().ts_debug_timeout_probe(C.byref(plan), _ptr(ws), int(limit_us), _stream(stream)),
+           "ts_debug_timeout_probe")
 
 
 def ts_set_stage_events(plan, events: Optional[Sequence]):

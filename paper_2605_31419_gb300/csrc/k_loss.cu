@@ -168,7 +168,23 @@ __global__ void k_pose_adam(ts_pose* poses, const float* __restrict__ dtau, floa
   pose_left_step(poses, v, st);
 }
 
+// Failure-detection probe: one thread waits on an mbarrier phase that nothing completes (no
+// arrival, no copy in flight), with the same bounded wait the raster kernels use, and latches the
+// timeout bit when the limit passes.
+__global__ void k_timeout_probe(TsDevHeader* hdr, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  ts_mbar_init(&bar, 1);
+  ts_fence_mbar_init();
+  if (!ts_mbar_wait(&bar, 0u, limit_ns)) atomicOr(&hdr->error_bits, TS_ERRBIT_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t ts_launch_timeout_probe(const TsWs& w, unsigned long long limit_ns, cudaStream_t s) {
+  k_timeout_probe<<<1, 32, 0, s>>>(w.hdr, limit_ns);
+  return cudaGetLastError();
+}
 
 cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* color, const float* depth,
                               const float* tc, const float* td, float lambda_dep, float* loss, float* dC, float* dD,

@@ -314,6 +314,13 @@ ts_status ts_debug_copy(const ts_plan* plan, void* ws, int32_t what, void* dst, 
   return cuda_status(cudaMemcpyAsync(dst, (char*)ws + off, bytes, cudaMemcpyDefault, (cudaStream_t)stream));
 }
 
+ts_status ts_debug_timeout_probe(const ts_plan* plan, void* ws, uint32_t limit_us, ts_stream stream) {
+  const TsPlanImpl* p = impl(plan);
+  if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) || limit_us == 0 || limit_us > 5000000u)
+    return TS_ERR_INVALID_ARG;
+  return cuda_status(ts_launch_timeout_probe(ts_ws(p, ws), (unsigned long long)limit_us * 1000ull, (cudaStream_t)stream));
+}
+
 const char* ts_status_string(ts_status s) {
   switch (s) {
     case TS_OK: return "ok";

@@ -156,6 +156,7 @@ cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* c
 cudaError_t ts_launch_pose_apply(const TsPlanImpl* p, ts_pose* poses, const float* step, cudaStream_t s);
 cudaError_t ts_launch_pose_adam(const TsPlanImpl* p, ts_pose* poses, const float* dtau, float* state, float lr_rho,
                                 float lr_theta, float b1, float b2, float eps, cudaStream_t s);
+cudaError_t ts_launch_timeout_probe(const TsWs& w, unsigned long long limit_ns, cudaStream_t s);
 int ts_sort_final_buffer(const TsPlanImpl* p);  // 0 or 1: which key/val buffer holds the sorted pairs
 int ts_pose_blocks(long long M);                 // blocks of the projection-backward kernel
 
