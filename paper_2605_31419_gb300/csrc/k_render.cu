@@ -10,14 +10,16 @@
 // Forward: per pixel, front to back: window (Eq. 3) from cancellation-free edge functions,
 // alpha = min(alpha_max, o_F I), skip below alpha_min, stop before the face that would take T
 // below T_min, accumulate colour, depth and opacity (Eq. 4).  Writes C + T bg, D, A = 1 - T, and
-// per pixel T_final and the list position after the last contribution.
+// per pixel T_final and the list position after the last contribution, and per sorted pair the
+// mask of warps that blended the face at one of their pixels.
 //
 // Backward: per pixel, back to front from that position: recover T_n = T_{n+1} / (1 - alpha_n),
 // keep the suffix sum S of later contributions (including the background term), form
 // dL/dalpha_n = T_n v_n - S / (1 - alpha_n) with v_n = gC . c_n + gD z_n + gA, and chain into 22
 // per-face sums (barycentric-weighted gradients of the edge, colour and depth interpolants, and
 // of o_F).  A warp reduces the 24-word vector with a 27-shuffle reduce-scatter, leaving one sum
-// per lane, and issues a single 24-lane atomic add into the face's accumulator.
+// per lane, and issues a single 24-lane atomic add into the face's accumulator.  A warp visits
+// only the faces whose forward mask holds its bit.
 //
 // Launch forms: one CTA per tile, or persistent CTAs (as many as fit on the GPU) that take tiles
 // from a device counter, keeping their mbarriers across tiles.
@@ -48,6 +50,7 @@ struct RenderArgs {
   float bg0, bg1, bg2;
   int S;
   unsigned int* counter;
+  uint16_t* cmask;
   TsDevHeader* hdr;
 };
 
@@ -57,6 +60,7 @@ constexpr unsigned FULL = 0xffffffffu;
 struct RenderSmem {
   uint64_t bar[2];
   uint32_t smask[2][128];
+  uint32_t cm[2][128];  // forward: warps of the tile that blended each staged face
   int view;
   int nmax;
   int next_tile;
@@ -75,13 +79,22 @@ struct TileGeom {
 template <int TW, int TH>
 __device__ __forceinline__ TileGeom<TW, TH> tile_geom(const RenderArgs& a, long long tile, RenderSmem& sm) {
   TileGeom<TW, TH> g;
-  if (threadIdx.x == 0) sm.view = ts_find_view(a.views, a.V, tile);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {  // the view owning the tile: one coalesced load and a ballot per 32 views
+    int below = 0;
+    for (int base = 0; base < a.V; base += 32) {
+      const int v = base + lane;
+      const unsigned b = __ballot_sync(FULL, v < a.V && a.views[v].tile_off <= tile);
+      below += __popc(b);
+      if (b != FULL) break;
+    }
+    if (lane == 0) sm.view = below - 1;
+  }
   __syncthreads();
   g.view = sm.view;
   g.vw = a.views[g.view];
   const long long lt = tile - g.vw.tile_off;
   const int ty = (int)(lt / g.vw.TX), tx = (int)(lt - (long long)ty * g.vw.TX);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   g.X0 = tx * TW;
   g.Y0 = ty * TH;
   g.x = g.X0 + (warp % TileGeom<TW, TH>::NSBX) * 8 + (lane & 7);
@@ -193,6 +206,7 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
       ++seq;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
+      for (int j = threadIdx.x; j < cnt; j += TW * TH) sm.cm[b][j] = 0u;
       __syncthreads();
       if (warp == 0 && st + 1 < nst) issue_stage(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase);
       for (int q = 0; q * 32 < cnt; ++q) {
@@ -201,28 +215,40 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
         while (bits) {
           const int j = q * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          if (done) continue;
-          const float* r = rb + j * TS_REC_WORDS;
-          const TsPix e = ts_eval_edges(r, g.px, g.py);
-          if (!(e.m > 0.f)) continue;
-          const float I = ts_window(e.m, a.sigma);
-          const float al = fminf(r[R_OF] * I, a.alpha_max);
-          if (al < a.alpha_min) continue;
-          const float Tn = T * (1.f - al);
-          if (Tn < a.T_min) { done = true; continue; }
-          const float invD = r[R_INVD];
-          const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
-          const float w = al * T;
-          C0 += w * (l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2]);
-          C1 += w * (l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1]);
-          C2 += w * (l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2]);
-          D += w * (l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2]);
-          T = Tn;
-          nl = st * S + j + 1;
-          ++contrib;
+          bool blended = false;
+          if (!done) {
+            const float* r = rb + j * TS_REC_WORDS;
+            const TsPix e = ts_eval_edges(r, g.px, g.py);
+            if (e.m > 0.f) {
+              const float I = ts_window(e.m, a.sigma);
+              const float al = fminf(r[R_OF] * I, a.alpha_max);
+              if (al >= a.alpha_min) {
+                const float Tn = T * (1.f - al);
+                if (Tn < a.T_min) {
+                  done = true;
+                } else {
+                  const float invD = r[R_INVD];
+                  const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
+                  const float w = al * T;
+                  C0 += w * (l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2]);
+                  C1 += w * (l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1]);
+                  C2 += w * (l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2]);
+                  D += w * (l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2]);
+                  T = Tn;
+                  nl = st * S + j + 1;
+                  ++contrib;
+                  blended = true;
+                }
+              }
+            }
+          }
+          // the backward revisits exactly the (warp, face) pairs that blended somewhere
+          if (__any_sync(FULL, blended) && lane == 0) atomicOr(&sm.cm[b][j], 1u << warp);
         }
       }
-      if (__syncthreads_count(!done) == 0) {
+      const int alive = __syncthreads_count(!done);
+      for (int j = threadIdx.x; j < cnt; j += TW * TH) a.cmask[rg.x + st * S + j] = (uint16_t)sm.cm[b][j];
+      if (alive == 0) {
         if (st + 1 < nst) {  // a prefetched stage is in flight: consume its phase before leaving
           if (!wait_stage(a, sm, seq)) { ok = false; break; }
           ++seq;
@@ -299,10 +325,12 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
       if (!wait_stage(a, sm, seq)) { ok = false; break; }
       ++seq;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
-      stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
+      // the forward's record of which warps blended each face (positions below the tile's
+      // largest list position after a contribution were all written by the forward)
+      for (int j = threadIdx.x; j < cnt; j += TW * TH) sm.smask[b][j] = a.cmask[rg.x + st * S + j];
       __syncthreads();
       if (warp == 0 && k + 1 < nst) issue_stage(a, smrec, sm.bar, b ^ 1, st - 1, rg.x, n, vbase);
-      // this warp visits only the stage's faces whose mask has its bit (back to front)
+      // this warp visits only the stage's faces it blended in the forward (back to front)
       for (int qq = (cnt - 1) >> 5; qq >= 0; --qq) {
         const int jq = qq * 32 + lane;
         unsigned bits = __ballot_sync(FULL, jq < cnt && ((sm.smask[b][min(jq, cnt - 1)] >> warp) & 1u));
@@ -328,8 +356,9 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
 #pragma unroll
           for (int i = 0; i < 24; ++i) v[i] = 0.f;
           if (cb) {
-            const float oma = 1.f - al;
-            const float Tn = T / oma;
+            const float oma = 1.f - al;  // >= 1 - alpha_max
+            const float ro = ts_rcp_approx(oma);
+            const float Tn = T * ro;
             const float invD = r[R_INVD];
             const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
             const float c0 = l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2];
@@ -337,7 +366,7 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
             const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
             const float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
-            const float dal = val * Tn - Sacc / oma;
+            const float dal = val * Tn - Sacc * ro;
             Sacc += val * al * Tn;
             T = Tn;
             const float w = al * Tn;
@@ -351,7 +380,8 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             if (!(oF * I > a.alpha_max)) {
               v[G_O] = dal * I;
               const float dI = dal * oF;
-              const float dm = (a.sigma == 0.5f) ? dI * 0.5f / I : dI * a.sigma * I / e.m;
+              // I >= alpha_min / o_F here, far from zero
+              const float dm = (a.sigma == 0.5f) ? dI * 0.5f * ts_rcp_approx(I) : dI * a.sigma * I / e.m;
               const float d0 = dm * l0, d1 = dm * l1, d2 = dm * l2;
               v[G_E + 0] = e.arg == 0 ? d0 : 0.f; v[G_E + 1] = e.arg == 0 ? d1 : 0.f; v[G_E + 2] = e.arg == 0 ? d2 : 0.f;
               v[G_E + 3] = e.arg == 1 ? d0 : 0.f; v[G_E + 4] = e.arg == 1 ? d1 : 0.f; v[G_E + 5] = e.arg == 1 ? d2 : 0.f;
@@ -504,6 +534,7 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.S = p->prm.tris_per_stage;
   a.hdr = w.hdr;
   a.counter = &w.hdr->tile_counter;
+  a.cmask = w.cmask;
   return a;
 }
 

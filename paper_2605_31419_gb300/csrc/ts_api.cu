@@ -131,6 +131,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_grad = take((size_t)VM * TS_GRAD_WORDS * 4);
   p->o_pose = take((size_t)n_views * p->n_pose_blocks * 6 * 4);
   p->o_loss = take((size_t)n_views * p->n_loss_blocks * 2 * 4);
+  p->o_cmask = take((size_t)cap * 2);
   p->total = o;
   p->magic = TS_PLAN_MAGIC;
   return TS_OK;

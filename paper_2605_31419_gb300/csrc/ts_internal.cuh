@@ -80,7 +80,7 @@ struct TsPlanImpl {
   int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks;
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
-      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, total;
+      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
   TsView views[TS_MAX_VIEWS];
@@ -108,6 +108,7 @@ struct TsWs {
   float* grad;
   float* pose;
   float* loss;
+  uint16_t* cmask;  // per sorted pair: the warps of its tile that blended the face in the forward
 };
 
 inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
@@ -134,6 +135,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.grad = (float*)(b + p->o_grad);
   w.pose = (float*)(b + p->o_pose);
   w.loss = (float*)(b + p->o_loss);
+  w.cmask = (uint16_t*)(b + p->o_cmask);
   return w;
 }
 
@@ -220,9 +222,22 @@ __device__ __forceinline__ TsPix ts_eval_edges(const float* r, float px, float p
   return o;
 }
 
-// Eq. 3 window: I = ratio^sigma for ratio > 0.
+__device__ __forceinline__ float ts_sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float ts_rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Eq. 3 window: I = ratio^sigma for ratio > 0 (hardware square root / exp2-log2, ~1-2 ulp; the
+// forward and backward passes share this function, so they see identical values).
 __device__ __forceinline__ float ts_window(float m, float sigma) {
-  if (sigma == 0.5f) return sqrtf(m);
+  if (sigma == 0.5f) return ts_sqrt_approx(m);
   return exp2f(sigma * __log2f(m));
 }
 
