@@ -142,6 +142,8 @@ class Oracle:
         L.oracle_backward_ex.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_l1_loss.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, vp]
         L.oracle_l1_loss.restype = d
+        L.oracle_pho_loss.argtypes = [vp, vp, vp, vp, vp, d, d, vp, vp, vp, vp]
+        L.oracle_pho_loss.restype = d
         L.oracle_window.argtypes = [vp, d, d, d, vp]
         L.oracle_window.restype = d
         L.oracle_se3_exp.argtypes = [vp, vp]
@@ -216,6 +218,22 @@ class Oracle:
         tot = self.lib.oracle_l1_loss(C.byref(sc), _ptr(color), _ptr(depth), _ptr(tgt_color), _ptr(tgt_depth),
                                       float(lambda_dep), _ptr(loss_v), _ptr(dC), _ptr(dD))
         return dict(loss=tot, loss_v=loss_v, dC=dC, dD=dD)
+
+    def pho_loss(self, sa: SceneArrays, color, depth, tgt_color, tgt_depth, lambda_ssim: float = 0.2,
+                 lambda_dep: float = 0.05, grads: bool = True):
+        """Eq. 8-10: (1 - lambda) L1 + lambda D-SSIM colour terms plus the L1 depth term, per view."""
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+        color, depth, tgt_color, tgt_depth = f(color), f(depth), f(tgt_color), f(tgt_depth)
+        V = len(sa.cams)
+        loss_v = np.empty(V)
+        dC = np.empty_like(color) if grads else None
+        dD = np.empty_like(depth) if grads else None
+        smap = np.empty_like(color)
+        sc = sa.c()
+        tot = self.lib.oracle_pho_loss(C.byref(sc), _ptr(color), _ptr(depth), _ptr(tgt_color), _ptr(tgt_depth),
+                                       float(lambda_ssim), float(lambda_dep), _ptr(loss_v), _ptr(dC), _ptr(dD),
+                                       _ptr(smap))
+        return dict(loss=tot, loss_v=loss_v, dC=dC, dD=dD, ssim_map=smap)
 
     # -- small pieces used by the pins ---------------------------------------------------
     def window(self, tri2d, sigma: float, px: float, py: float):

@@ -16,7 +16,9 @@
 //             with depth and opacity images composited the same way;
 //   * the adjoint of all of the above w.r.t. vertex positions, colours,
 //     opacities, and the pose through the left perturbation Exp(tau) o T
-//     (Eq. 5-7, tau = (rho, theta), translation first).
+//     (Eq. 5-7, tau = (rho, theta), translation first);
+//   * Eq. 8-10 the tracking loss: L1 and D-SSIM photometric terms and the L1
+//     depth term, with their gradients w.r.t. the rendered images.
 //
 // How: the forward pass walks each pixel's depth-sorted list literally.  The
 // backward pass stores every contribution of a pixel front to back, forms the
@@ -43,6 +45,14 @@
 //      ceil(min - 0.5) .. floor(max - 0.5) clamped to the image;
 //   R11 loss = mean |C - Cbar| over 3HW + lambda_dep * sum_{Dbar>0} |D - Dbar| / HW
 //      per view, summed over views; sign(0) = 0;
+//   R15 the D-SSIM term of Eq. 8 is 1 - SSIM, SSIM the mean over the 3HW channel pixels of the
+//      per-pixel structural similarity (Wang et al. 2004) with the common defaults: 11 x 11
+//      Gaussian window, sigma 1.5, normalised to sum 1; C1 = 0.01^2, C2 = 0.03^2 (colours in
+//      [0, 1]);
+//   R16 the window sums see zeros outside the image ("same"-size output, zero padding), and
+//      every image pixel carries one SSIM value;
+//   R17 E_pho weights the same mean L1 colour term as R11 by (1 - lambda), lambda = 0.2
+//      (Table S5); the depth term is that of R11;
 //   R14 in FP32 mode the projection follows one fixed operation order with
 //      no fused multiply-add (build with -ffp-contract=off), so that culling,
 //      pixel boxes, tiles and depth keys are bit-identical to any other
@@ -771,6 +781,120 @@ double oracle_l1_loss(const or_scene* sc, const double* color, const double* dep
       if (dD) dD[off + i] = valid ? lambda_dep * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (double)HW : 0.0;
     }
     const double l = lc / nc + lambda_dep * ld / (double)HW;
+    if (loss_v) loss_v[v] = l;
+    total += l;
+    off += HW;
+  }
+  return total;
+}
+
+// Photometric loss of Eq. 8 with the depth term of Eq. 9 (R15-R17), per view:
+//   loss_v = (1 - lambda) mean_{3HW} |C - Cbar| + lambda (1 - mean_{3HW} SSIM(C, Cbar))
+//            + lambda_dep sum_{Dbar > 0} |D - Dbar| / HW.
+// SSIM at a pixel p of one channel is the structural similarity of Wang et al. (2004) with local
+// statistics taken under the 11 x 11 Gaussian window w (sigma 1.5, normalised), centred on p, with
+// zeros outside the image:
+//   mu_x = sum w x,  e_xx = sum w x^2,  e_xy = sum w x y  (and likewise for y),
+//   SSIM = (2 mu_x mu_y + C1)(2 (e_xy - mu_x mu_y) + C2) / ((mu_x^2 + mu_y^2 + C1)(e_xx - mu_x^2 + e_yy - mu_y^2 + C2)),
+// C1 = 0.01^2, C2 = 0.03^2.  The gradient w.r.t. C follows the chain rule through the three
+// moments that depend on x: dSSIM(p)/dx(q) = w(q - p) (dS/dmu_x + 2 x(q) dS/de_xx + y(q) dS/de_xy).
+// Every sum is the plain 121-term window sum (no separable filtering).  ssim_map [3P] optional.
+double oracle_pho_loss(const or_scene* sc, const double* color, const double* depth, const double* tC,
+                       const double* tD, double lambda, double lambda_dep, double* loss_v, double* dC, double* dD,
+                       double* ssim_map) {
+  const int R = 5;
+  double g1[2 * R + 1], gs = 0;
+  for (int k = -R; k <= R; ++k) gs += (g1[k + R] = std::exp(-(double)(k * k) / (2.0 * 1.5 * 1.5)));
+  for (int k = 0; k <= 2 * R; ++k) g1[k] /= gs;
+  double w[2 * R + 1][2 * R + 1];
+  for (int i = 0; i <= 2 * R; ++i)
+    for (int j = 0; j <= 2 * R; ++j) w[i][j] = g1[i] * g1[j];
+#if ORACLE_MUTANT == 13
+  const double C1 = 0.01 * 0.01, C2 = C1;
+#else
+  const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+#endif
+  double total = 0;
+  int64_t off = 0;
+  for (int v = 0; v < sc->n_views; ++v) {
+    const int W = (int)sc->cams[6 * v + 4], H = (int)sc->cams[6 * v + 5];
+    const int64_t HW = (int64_t)W * H;
+    const double nc = 3.0 * (double)HW;
+    double lc = 0, ls = 0, ld = 0;
+    std::vector<double> m0(HW), m1(HW), m2(HW), S(HW);
+    for (int ch = 0; ch < 3; ++ch) {
+      const double* x = color + 3 * off + ch * HW;
+      const double* y = tC + 3 * off + ch * HW;
+      auto inside = [&](int px, int py) { return px >= 0 && px < W && py >= 0 && py < H; };
+#if ORACLE_MUTANT == 15
+      auto at = [&](const double* a, int px, int py) {  // clamp to the edge instead of zeros
+        px = std::min(std::max(px, 0), W - 1);
+        py = std::min(std::max(py, 0), H - 1);
+        return a[(int64_t)py * W + px];
+      };
+#else
+      auto at = [&](const double* a, int px, int py) { return inside(px, py) ? a[(int64_t)py * W + px] : 0.0; };
+#endif
+#pragma omp parallel for schedule(static) reduction(+ : ls)
+      for (int py = 0; py < H; ++py) {
+        for (int px = 0; px < W; ++px) {
+          double mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+          for (int i = -R; i <= R; ++i) {
+            for (int j = -R; j <= R; ++j) {
+              const double ww = w[i + R][j + R];
+              const double a = at(x, px + j, py + i), b = at(y, px + j, py + i);
+              mx += ww * a;
+              my += ww * b;
+              exx += ww * a * a;
+              eyy += ww * b * b;
+              exy += ww * a * b;
+            }
+          }
+          const double A1 = 2 * mx * my + C1, A2 = 2 * (exy - mx * my) + C2;
+          const double B1 = mx * mx + my * my + C1, B2 = (exx - mx * mx) + (eyy - my * my) + C2;
+          const double s = A1 * A2 / (B1 * B2);
+          const int64_t p = (int64_t)py * W + px;
+          S[p] = s;
+          // partial derivatives of s w.r.t. mu_x, e_xx, e_xy
+          m0[p] = (2 * my * (A2 - A1) - 2 * mx * s * (B2 - B1)) / (B1 * B2);
+          m1[p] = -s / B2;
+          m2[p] = 2 * A1 / (B1 * B2);
+          ls += s;
+        }
+      }
+      if (ssim_map)
+        for (int64_t p = 0; p < HW; ++p) ssim_map[3 * off + ch * HW + p] = S[p];
+      for (int64_t q = 0; q < HW; ++q) lc += std::fabs(x[q] - y[q]);
+      if (!dC) continue;
+#pragma omp parallel for schedule(static)
+      for (int qy = 0; qy < H; ++qy) {
+        for (int qx = 0; qx < W; ++qx) {
+          const int64_t q = (int64_t)qy * W + qx;
+          double gsum = 0;  // sum over the pixels p whose window holds q
+          for (int i = -R; i <= R; ++i) {
+            for (int j = -R; j <= R; ++j) {
+              const int px = qx + j, py = qy + i;
+              if (!inside(px, py)) continue;
+              const int64_t p = (int64_t)py * W + px;
+#if ORACLE_MUTANT == 14
+              gsum += w[i + R][j + R] * (m0[p] + x[q] * m1[p] + y[q] * m2[p]);
+#else
+              gsum += w[i + R][j + R] * (m0[p] + 2 * x[q] * m1[p] + y[q] * m2[p]);
+#endif
+            }
+          }
+          const double r = x[q] - y[q];
+          dC[3 * off + ch * HW + q] = (1 - lambda) * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / nc - lambda * gsum / nc;
+        }
+      }
+    }
+    for (int64_t i = 0; i < HW; ++i) {
+      const bool valid = tD[off + i] > 0;
+      const double r = depth[off + i] - tD[off + i];
+      if (valid) ld += std::fabs(r);
+      if (dD) dD[off + i] = valid ? lambda_dep * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (double)HW : 0.0;
+    }
+    const double l = (1 - lambda) * lc / nc + lambda * (1 - ls / nc) + lambda_dep * ld / (double)HW;
     if (loss_v) loss_v[v] = l;
     total += l;
     off += HW;

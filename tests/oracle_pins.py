@@ -351,6 +351,98 @@ def pin_l1_loss(o: Oracle):
 
 
 # ---------------------------------------------------------------------------------------------
+# D-SSIM (Eq. 8, R15-R17): scipy's Gaussian filter, closed forms, finite differences
+# ---------------------------------------------------------------------------------------------
+SSIM_C1, SSIM_C2 = 0.01 ** 2, 0.03 ** 2
+
+
+def _loss_cams(sizes):
+    """SceneArrays carrying only cameras of the given (W, H) sizes (the loss needs no faces)."""
+    sc = random_triangles_scene(seed=3, n_faces=4, W=sizes[0][0], H=sizes[0][1], f=10.0)
+    cams = np.asarray([[10.0, 10.0, W / 2, H / 2, W, H] for W, H in sizes], np.float64)
+    poses = np.repeat(sc.poses[:1], len(sizes), axis=0)
+    return SceneArrays.of(Scene(sc.pos, sc.col, sc.opa, None, cams, poses))
+
+
+def ssim_map_scipy(x, y):
+    """Per-pixel SSIM of two HxW images, local statistics by scipy.ndimage.gaussian_filter
+    (sigma 1.5, radius 5, zero padding)."""
+    import scipy.ndimage as ndi
+
+    g = lambda a: ndi.gaussian_filter(a, sigma=1.5, truncate=5.0 / 1.5, mode="constant", cval=0.0)  # noqa: E731
+    mx, my = g(x), g(y)
+    sxx, syy, sxy = g(x * x) - mx * mx, g(y * y) - my * my, g(x * y) - mx * my
+    return ((2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)) / ((mx * mx + my * my + SSIM_C1) * (sxx + syy + SSIM_C2))
+
+
+def pin_ssim_scipy(o: Oracle):
+    sizes = [(23, 17), (8, 13)]
+    sa = _loss_cams(sizes)
+    rng = np.random.default_rng(31)
+    P = sum(W * H for W, H in sizes)
+    C, tC = rng.random(3 * P), rng.random(3 * P)
+    tC[: 3 * 23 * 17] = np.clip(C[: 3 * 23 * 17] + 0.1 * rng.normal(size=3 * 23 * 17), 0, 1)  # correlated view
+    D, tD = rng.random(P), rng.random(P)
+    r = o.pho_loss(sa, C, D, tC, tD, lambda_ssim=0.2, lambda_dep=0.05, grads=False)
+    off = 0
+    for v, (W, H) in enumerate(sizes):
+        HW = W * H
+        ref = np.concatenate([ssim_map_scipy(C[3 * off + c * HW:3 * off + (c + 1) * HW].reshape(H, W),
+                                             tC[3 * off + c * HW:3 * off + (c + 1) * HW].reshape(H, W)).ravel()
+                              for c in range(3)])
+        got = r["ssim_map"][3 * off:3 * off + 3 * HW]
+        assert np.abs(got - ref).max() < 1e-12, (v, np.abs(got - ref).max())
+        l1 = np.abs(C[3 * off:3 * off + 3 * HW] - tC[3 * off:3 * off + 3 * HW]).mean()
+        dep = np.abs(D[off:off + HW] - tD[off:off + HW]).sum() / HW
+        expect = 0.8 * l1 + 0.2 * (1 - ref.mean()) + 0.05 * dep
+        assert abs(r["loss_v"][v] - expect) < 1e-12, (v, r["loss_v"][v], expect)
+        off += HW
+
+
+def pin_ssim_closed_forms(o: Oracle):
+    # identical images: SSIM = 1 everywhere, and x = y is a stationary point (zero gradient)
+    sa = _loss_cams([(19, 14)])
+    rng = np.random.default_rng(32)
+    C = rng.random(3 * 19 * 14)
+    D = rng.random(19 * 14)
+    r = o.pho_loss(sa, C, D, C.copy(), D.copy(), lambda_ssim=0.2, lambda_dep=0.05)
+    assert np.abs(r["ssim_map"] - 1).max() < 1e-12
+    assert abs(r["loss"]) < 1e-12
+    assert np.abs(r["dC"]).max() < 1e-12
+    # constant images a, b: SSIM = (2ab + C1) / (a^2 + b^2 + C1) wherever the window lies inside
+    W, H = 21, 16
+    sa = _loss_cams([(W, H)])
+    for a, b in ((0.3, 0.7), (0.9, 0.05), (0.5, 0.5)):
+        C = np.full(3 * W * H, a)
+        tC = np.full(3 * W * H, b)
+        r = o.pho_loss(sa, C, np.ones(W * H), tC, np.ones(W * H), grads=False)
+        smap = r["ssim_map"].reshape(3, H, W)[:, 5:H - 5, 5:W - 5]
+        assert np.abs(smap - (2 * a * b + SSIM_C1) / (a * a + b * b + SSIM_C1)).max() < 1e-12
+
+
+def pin_pho_fd(o: Oracle):
+    sizes = [(9, 7), (6, 5)]
+    sa = _loss_cams(sizes)
+    rng = np.random.default_rng(33)
+    P = sum(W * H for W, H in sizes)
+    tC = rng.random(3 * P)
+    # keep |C - Cbar| >= 0.05 so that the L1 term is differentiable at every entry
+    C = np.clip(tC + rng.choice([-1, 1], size=3 * P) * rng.uniform(0.05, 0.4, size=3 * P), -0.5, 1.5)
+    D, tD = rng.random(P) + 1, rng.random(P) + 1
+    lam = 0.35
+    an = o.pho_loss(sa, C, D, tC, tD, lambda_ssim=lam, lambda_dep=0.05)
+    h = 1e-6
+    scale = np.abs(an["dC"]).max()
+    for i in range(3 * P):
+        cp, cm = C.copy(), C.copy()
+        cp[i] += h
+        cm[i] -= h
+        fd = (o.pho_loss(sa, cp, D, tC, tD, lam, 0.05, grads=False)["loss"] -
+              o.pho_loss(sa, cm, D, tC, tD, lam, 0.05, grads=False)["loss"]) / (2 * h)
+        assert abs(fd - an["dC"][i]) <= 1e-7 * scale + 1e-5 * abs(fd), (i, fd, an["dC"][i])
+
+
+# ---------------------------------------------------------------------------------------------
 # SE(3) exponential against scipy's matrix exponential of the twist
 # ---------------------------------------------------------------------------------------------
 def twist_expm(tau):
@@ -427,4 +519,5 @@ def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
 
 ALL_PINS = [pin_window_closed_form, pin_barycentric, pin_projection, pin_single_triangle, pin_coverage_bruteforce,
             pin_fronto_parallel_depth, pin_transmittance_product, pin_termination_stack, pin_binning_bruteforce,
-            pin_sort_ties, pin_l1_loss, pin_se3_exp, pin_fd_gradients]
+            pin_sort_ties, pin_l1_loss, pin_ssim_scipy, pin_ssim_closed_forms, pin_pho_fd, pin_se3_exp,
+            pin_fd_gradients]

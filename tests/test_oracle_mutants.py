@@ -12,7 +12,7 @@ import pytest
 import oracle_pins as P
 from oracle.oracle import Oracle
 
-MUTANTS = list(range(1, 13))
+MUTANTS = list(range(1, 16))
 
 
 @pytest.mark.parametrize("k", MUTANTS)
