@@ -181,10 +181,26 @@ ts_status ts_pose_grad(const ts_plan* plan, void* ws, float* dtau, ts_stream str
 /* Mean-L1 colour + depth loss used by tracking and mapping (Eq. 8 L1 part, Eq. 9): per view,
  *   loss_v = sum |C - Cbar| / (3HW) + lambda_dep * sum_{Dbar > 0} |D - Dbar| / (HW),
  * with dC = dloss/dC and dD = dloss/dD (overwritten; sign(0) = 0).  All pointers device, packed
- * per view; loss: float [n_views], overwritten.  Deterministic. */
+ * per view; loss: float [n_views], overwritten.  Deterministic.  Uses only the workspace's
+ * partial-sum region: no earlier call on the workspace is needed. */
 ts_status ts_l1_loss(const ts_plan* plan, void* ws, const float* color, const float* depth,
                      const float* tgt_color, const float* tgt_depth, float lambda_dep, float* loss,
                      float* dC, float* dD, ts_stream stream);
+
+/* Tracking / mapping photometric loss of Eq. 8 with the depth term of Eq. 9-10, per view:
+ *   loss_v = (1 - lambda_ssim) sum |C - Cbar| / (3HW) + lambda_ssim (1 - sum SSIM / (3HW))
+ *            + lambda_dep sum_{Dbar > 0} |D - Dbar| / (HW),
+ * SSIM the per-pixel, per-channel structural similarity (Wang et al. 2004) under an 11 x 11
+ * Gaussian window (sigma 1.5, normalised, zeros outside the image), C1 = 0.01^2, C2 = 0.03^2;
+ * the paper weights D-SSIM by lambda_ssim = 0.2 (Table S5).  Writes dC = dloss/dC and
+ * dD = dloss/dD (overwritten; sign(0) = 0).  Pointers and packing as in ts_l1_loss; loss: device
+ * float [n_views], overwritten.  lambda_ssim = 0 gives the ts_l1_loss value.  lambda_ssim outside
+ * [0, 1] or a negative or non-finite lambda_dep returns TS_ERR_INVALID_ARG.  Deterministic: the
+ * partial sums per 32 x 32 tile are reduced in a fixed order.  Like ts_l1_loss it needs no earlier
+ * call on the workspace. */
+ts_status ts_pho_loss(const ts_plan* plan, void* ws, const float* color, const float* depth,
+                      const float* tgt_color, const float* tgt_depth, float lambda_ssim, float lambda_dep,
+                      float* loss, float* dC, float* dD, ts_stream stream);
 
 /* The same loss as ts_l1_loss for callers that cannot give the library any device memory of its
  * own: an application that owns the whole device budget and lends out only the image buffers,

@@ -142,7 +142,7 @@ class Oracle:
         L.oracle_backward_ex.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_l1_loss.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, vp]
         L.oracle_l1_loss.restype = d
-        L.oracle_pho_loss.argtypes = [vp, vp, vp, vp, vp, d, d, vp, vp, vp, vp]
+        L.oracle_pho_loss.argtypes = [vp, vp, vp, vp, vp, d, d, vp, vp, vp, vp, vp]
         L.oracle_pho_loss.restype = d
         L.oracle_window.argtypes = [vp, d, d, d, vp]
         L.oracle_window.restype = d
@@ -228,12 +228,13 @@ class Oracle:
         loss_v = np.empty(V)
         dC = np.empty_like(color) if grads else None
         dD = np.empty_like(depth) if grads else None
+        dC_abs = np.empty_like(color) if grads else None
         smap = np.empty_like(color)
         sc = sa.c()
         tot = self.lib.oracle_pho_loss(C.byref(sc), _ptr(color), _ptr(depth), _ptr(tgt_color), _ptr(tgt_depth),
                                        float(lambda_ssim), float(lambda_dep), _ptr(loss_v), _ptr(dC), _ptr(dD),
-                                       _ptr(smap))
-        return dict(loss=tot, loss_v=loss_v, dC=dC, dD=dD, ssim_map=smap)
+                                       _ptr(smap), _ptr(dC_abs))
+        return dict(loss=tot, loss_v=loss_v, dC=dC, dD=dD, ssim_map=smap, dC_abs=dC_abs)
 
     # -- small pieces used by the pins ---------------------------------------------------
     def window(self, tri2d, sigma: float, px: float, py: float):

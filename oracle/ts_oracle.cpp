@@ -799,9 +799,14 @@ double oracle_l1_loss(const or_scene* sc, const double* color, const double* dep
 // C1 = 0.01^2, C2 = 0.03^2.  The gradient w.r.t. C follows the chain rule through the three
 // moments that depend on x: dSSIM(p)/dx(q) = w(q - p) (dS/dmu_x + 2 x(q) dS/de_xx + y(q) dS/de_xy).
 // Every sum is the plain 121-term window sum (no separable filtering).  ssim_map [3P] optional.
+// dC_abs [3P] (optional) receives the scale of the rounding error of an evaluation of dC in
+// finite precision: the sum for dC with every term replaced by its absolute value (and dS/dmu_x
+// by the sum of the absolute values of its parts), each term p weighted by 1 + kappa_p, kappa_p = (e_xx + e_yy + mu_x^2 + mu_y^2 + 2|e_xy| + 2|mu_x mu_y|) /
+// (sigma_x^2 + sigma_y^2 + C2): the factor by which rounding of the window sums is amplified
+// when the variances are formed as differences of second moments and means.
 double oracle_pho_loss(const or_scene* sc, const double* color, const double* depth, const double* tC,
                        const double* tD, double lambda, double lambda_dep, double* loss_v, double* dC, double* dD,
-                       double* ssim_map) {
+                       double* ssim_map, double* dC_abs) {
   const int R = 5;
   double g1[2 * R + 1], gs = 0;
   for (int k = -R; k <= R; ++k) gs += (g1[k + R] = std::exp(-(double)(k * k) / (2.0 * 1.5 * 1.5)));
@@ -821,7 +826,7 @@ double oracle_pho_loss(const or_scene* sc, const double* color, const double* de
     const int64_t HW = (int64_t)W * H;
     const double nc = 3.0 * (double)HW;
     double lc = 0, ls = 0, ld = 0;
-    std::vector<double> m0(HW), m1(HW), m2(HW), S(HW);
+    std::vector<double> m0(HW), m1(HW), m2(HW), S(HW), kap(HW), m0a(HW);
     for (int ch = 0; ch < 3; ++ch) {
       const double* x = color + 3 * off + ch * HW;
       const double* y = tC + 3 * off + ch * HW;
@@ -859,6 +864,8 @@ double oracle_pho_loss(const or_scene* sc, const double* color, const double* de
           m0[p] = (2 * my * (A2 - A1) - 2 * mx * s * (B2 - B1)) / (B1 * B2);
           m1[p] = -s / B2;
           m2[p] = 2 * A1 / (B1 * B2);
+          kap[p] = (exx + eyy + mx * mx + my * my + 2 * std::fabs(exy) + 2 * std::fabs(mx * my)) / B2;
+          m0a[p] = 2 * (std::fabs(my) * (std::fabs(A2) + A1) + std::fabs(mx * s) * (B2 + B1)) / (B1 * B2);
           ls += s;
         }
       }
@@ -870,7 +877,7 @@ double oracle_pho_loss(const or_scene* sc, const double* color, const double* de
       for (int qy = 0; qy < H; ++qy) {
         for (int qx = 0; qx < W; ++qx) {
           const int64_t q = (int64_t)qy * W + qx;
-          double gsum = 0;  // sum over the pixels p whose window holds q
+          double gsum = 0, gabs = 0;  // sums over the pixels p whose window holds q
           for (int i = -R; i <= R; ++i) {
             for (int j = -R; j <= R; ++j) {
               const int px = qx + j, py = qy + i;
@@ -881,10 +888,12 @@ double oracle_pho_loss(const or_scene* sc, const double* color, const double* de
 #else
               gsum += w[i + R][j + R] * (m0[p] + 2 * x[q] * m1[p] + y[q] * m2[p]);
 #endif
+              gabs += w[i + R][j + R] * (m0a[p] + std::fabs(2 * x[q] * m1[p]) + std::fabs(y[q] * m2[p])) * (1 + kap[p]);
             }
           }
           const double r = x[q] - y[q];
           dC[3 * off + ch * HW + q] = (1 - lambda) * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / nc - lambda * gsum / nc;
+          if (dC_abs) dC_abs[3 * off + ch * HW + q] = ((1 - lambda) * (r != 0 ? 1.0 : 0.0) + lambda * gabs) / nc;
         }
       }
     }

@@ -87,6 +87,7 @@ SIGNATURES = {
     "ts_pose_grad": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
     "ts_l1_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
     "ts_pose_apply": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
+    "ts_pho_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
     "ts_l1_loss_noalloc": (_st, [C.POINTER(TsCamera), _i32, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
     "ts_pose_adam": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
                            _vp]),
@@ -241,6 +242,12 @@ def ts_pose_grad(plan, ws, dtau, stream=None):
 def ts_l1_loss(plan, ws, color, depth, tgt_color, tgt_depth, lambda_dep, loss, dC, dD, stream=None):
     _check(lib().ts_l1_loss(C.byref(plan), _ptr(ws), _ptr(color), _ptr(depth), _ptr(tgt_color), _ptr(tgt_depth),
                             float(lambda_dep), _ptr(loss), _ptr(dC), _ptr(dD), _stream(stream)), "ts_l1_loss")
+
+
+def ts_pho_loss(plan, ws, color, depth, tgt_color, tgt_depth, lambda_ssim, lambda_dep, loss, dC, dD, stream=None):
+    _check(lib().ts_pho_loss(C.byref(plan), _ptr(ws), _ptr(color), _ptr(depth), _ptr(tgt_color), _ptr(tgt_depth),
+                             float(lambda_ssim), float(lambda_dep), _ptr(loss), _ptr(dC), _ptr(dD), _stream(stream)),
+           "ts_pho_loss")
 
 
 def ts_l1_loss_noalloc(cams, color, depth, tgt_color, tgt_depth, lambda_dep, loss, dC, dD, stream=None):

@@ -14,15 +14,15 @@ namespace {
 constexpr int LOSS_T = 256;
 constexpr int LOSS_PER = 8;  // pixels per thread; 2048 per block
 
-__global__ void __launch_bounds__(LOSS_T) k_loss_partial(const TsView* __restrict__ views, const float* __restrict__ C,
+__global__ void __launch_bounds__(LOSS_T) k_loss_partial(const TsImageTable tab, const float* __restrict__ C,
                                                          const float* __restrict__ D, const float* __restrict__ tC,
                                                          const float* __restrict__ tD, float lambda_dep,
                                                          float* __restrict__ dC, float* __restrict__ dD,
                                                          float* __restrict__ part, int nblk) {
   __shared__ float red[LOSS_T / 32][2];
   const int v = blockIdx.y;
-  const TsView vw = views[v];
-  const long long HW = (long long)vw.W * vw.H;
+  const long long HW = (long long)tab.W[v] * tab.H[v];
+  const long long pix_off = tab.pix_off[v];
   const long long base = (long long)blockIdx.x * LOSS_T * LOSS_PER;
   float lc = 0.f, ld = 0.f;
   if (base < HW) {
@@ -33,12 +33,12 @@ __global__ void __launch_bounds__(LOSS_T) k_loss_partial(const TsView* __restric
       if (i >= HW) break;
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
-        const long long o = 3 * vw.pix_off + ch * HW + i;
+        const long long o = 3 * pix_off + ch * HW + i;
         const float r = C[o] - tC[o];
         lc += fabsf(r);
         dC[o] = r > 0.f ? ic : (r < 0.f ? -ic : 0.f);
       }
-      const long long o = vw.pix_off + i;
+      const long long o = pix_off + i;
       const float t = tD[o];
       const float r = D[o] - t;
       const bool valid = t > 0.f;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(LOSS_T) k_loss_partial(const TsView* __restric
   }
 }
 
-__global__ void __launch_bounds__(LOSS_T) k_loss_final(const TsView* __restrict__ views, const float* __restrict__ part,
+__global__ void __launch_bounds__(LOSS_T) k_loss_final(const TsImageTable tab, const float* __restrict__ part,
                                                        int nblk, float lambda_dep, float* __restrict__ loss) {
   __shared__ float red[LOSS_T][2];
   const int v = blockIdx.x;
@@ -84,8 +84,7 @@ __global__ void __launch_bounds__(LOSS_T) k_loss_final(const TsView* __restrict_
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const TsView vw = views[v];
-    const double HW = (double)vw.W * vw.H;
+    const double HW = (double)tab.W[v] * tab.H[v];
     loss[v] = (float)((double)red[0][0] / (3.0 * HW) + (double)lambda_dep * (double)red[0][1] / HW);
   }
 }
@@ -191,8 +190,9 @@ cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* c
                               cudaStream_t s) {
   const int nblk = (int)p->n_loss_blocks;
   dim3 grid((unsigned)nblk, (unsigned)p->V);
-  k_loss_partial<<<grid, LOSS_T, 0, s>>>(w.views, color, depth, tc, td, lambda_dep, dC, dD, w.loss, nblk);
-  k_loss_final<<<p->V, LOSS_T, 0, s>>>(w.views, w.loss, nblk, lambda_dep, loss);
+  const TsImageTable tab = ts_image_table(p);
+  k_loss_partial<<<grid, LOSS_T, 0, s>>>(tab, color, depth, tc, td, lambda_dep, dC, dD, w.loss, nblk);
+  k_loss_final<<<p->V, LOSS_T, 0, s>>>(tab, w.loss, nblk, lambda_dep, loss);
   return cudaGetLastError();
 }
 

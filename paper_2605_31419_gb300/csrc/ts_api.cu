@@ -106,6 +106,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   int64_t max_hw = 0;
   for (int v = 0; v < n_views; ++v) max_hw = std::max<int64_t>(max_hw, (int64_t)p->views[v].W * p->views[v].H);
   p->n_loss_blocks = (max_hw + 2047) / 2048;
+  p->n_pho_blocks = ts_pho_blocks(p->views, n_views);
   // layout
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -132,6 +133,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_pose = take((size_t)n_views * p->n_pose_blocks * 6 * 4);
   p->o_loss = take((size_t)n_views * p->n_loss_blocks * 2 * 4);
   p->o_cmask = take((size_t)cap * 2);
+  p->o_pho = take((size_t)n_views * p->n_pho_blocks * 3 * 4);
   p->total = o;
   p->magic = TS_PLAN_MAGIC;
   return TS_OK;
@@ -251,6 +253,19 @@ ts_status ts_l1_loss(const ts_plan* plan, void* ws, const float* color, const fl
   cudaStream_t s = (cudaStream_t)stream;
   StageTimer t(p, TS_STAGE_LOSS, s);
   return cuda_status(ts_launch_l1_loss(p, ts_ws(p, ws), color, depth, tgt_color, tgt_depth, lambda_dep, loss, dC, dD, s));
+}
+
+ts_status ts_pho_loss(const ts_plan* plan, void* ws, const float* color, const float* depth, const float* tgt_color,
+                      const float* tgt_depth, float lambda_ssim, float lambda_dep, float* loss, float* dC, float* dD,
+                      ts_stream stream) {
+  const TsPlanImpl* p = impl(plan);
+  if (!p || !ws || !color || !depth || !tgt_color || !tgt_depth || !loss || !dC || !dD) return TS_ERR_INVALID_ARG;
+  if (!(lambda_ssim >= 0.0f && lambda_ssim <= 1.0f) || !(lambda_dep >= 0.0f) || !std::isfinite(lambda_dep))
+    return TS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  StageTimer t(p, TS_STAGE_LOSS, s);
+  return cuda_status(ts_launch_pho_loss(p, ts_ws(p, ws), color, depth, tgt_color, tgt_depth, lambda_ssim, lambda_dep,
+                                        loss, dC, dD, s));
 }
 
 ts_status ts_pose_apply(const ts_plan* plan, ts_pose* poses, const float* step, ts_stream stream) {

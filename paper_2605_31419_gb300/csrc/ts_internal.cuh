@@ -54,6 +54,13 @@ struct TsViewTable {
   TsView v[TS_MAX_VIEWS];
 };
 
+// Image sizes and packing offsets of the views, handed to the loss kernels by value so that a
+// loss call needs no earlier call on the workspace.
+struct TsImageTable {
+  int32_t W[TS_MAX_VIEWS], H[TS_MAX_VIEWS];
+  long long pix_off[TS_MAX_VIEWS];
+};
+
 // Device-side header at the start of the workspace.
 struct TsDevHeader {
   unsigned long long n_pairs;
@@ -77,10 +84,10 @@ struct TsPlanImpl {
   ts_raster_params prm;
   int64_t n_tiles, n_pix;
   int32_t tile_bits, sort_passes;
-  int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks;
+  int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks, n_pho_blocks;
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
-      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, total;
+      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
   TsView views[TS_MAX_VIEWS];
@@ -108,6 +115,7 @@ struct TsWs {
   float* grad;
   float* pose;
   float* loss;
+  float* pho;  // per (view, 32 x 32 tile): L1, SSIM and depth partial sums of the photometric loss
   uint16_t* cmask;  // per sorted pair: the warps of its tile that blended the face in the forward
 };
 
@@ -135,6 +143,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.grad = (float*)(b + p->o_grad);
   w.pose = (float*)(b + p->o_pose);
   w.loss = (float*)(b + p->o_loss);
+  w.pho = (float*)(b + p->o_pho);
   w.cmask = (uint16_t*)(b + p->o_cmask);
   return w;
 }
@@ -152,6 +161,19 @@ cudaError_t ts_launch_render_bwd(const TsPlanImpl* p, const TsWs& w, const float
                                  const float* dA, cudaStream_t s);
 cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_map_grad* g, cudaStream_t s);
 cudaError_t ts_launch_pose_reduce(const TsPlanImpl* p, const TsWs& w, float* dtau, cudaStream_t s);
+inline TsImageTable ts_image_table(const TsPlanImpl* p) {
+  TsImageTable t;
+  for (int v = 0; v < p->V; ++v) {
+    t.W[v] = p->views[v].W;
+    t.H[v] = p->views[v].H;
+    t.pix_off[v] = p->views[v].pix_off;
+  }
+  return t;
+}
+int64_t ts_pho_blocks(const TsView* views, int V);
+cudaError_t ts_launch_pho_loss(const TsPlanImpl* p, const TsWs& w, const float* color, const float* depth,
+                               const float* tc, const float* td, float lambda, float lambda_dep, float* loss,
+                               float* dC, float* dD, cudaStream_t s);
 cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* color, const float* depth,
                               const float* tc, const float* td, float lambda_dep, float* loss, float* dC,
                               float* dD, cudaStream_t s);

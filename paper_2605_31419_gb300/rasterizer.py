@@ -118,6 +118,13 @@ class Rasterizer:
                      self.dC, self.dD, stream)
         return self.loss_v, self.dC, self.dD
 
+    def pho_loss(self, tgt_color, tgt_depth, lambda_ssim: float = 0.2, lambda_dep: float = 0.05, stream=None):
+        """Eq. 8-10: (1 - lambda) L1 + lambda D-SSIM colour terms and the L1 depth term of the last
+        forward's images, with their gradients (the rasterizer's loss buffers, overwritten)."""
+        B.ts_pho_loss(self.plan, self.ws, self.color, self.depth, tgt_color, tgt_depth, lambda_ssim, lambda_dep,
+                      self.loss_v, self.dC, self.dD, stream)
+        return self.loss_v, self.dC, self.dD
+
     def plan_passes(self) -> int:
         """Radix-sort passes per ts_bin: 8 bits each over 32 depth bits + ceil(log2 tiles) tile bits."""
         n_tiles = int(self.layout["tile_off"][-1])

@@ -89,6 +89,13 @@ def test_device_calls_reject_null_arguments(ts):
     assert L.ts_render_fwd(C.byref(plan), None, None, None, None, None) == 1
     assert L.ts_render_bwd(C.byref(plan), C.c_void_p(256), None, None, None, None, None) == 1
     assert L.ts_pose_grad(C.byref(plan), None, None, None) == 1
+    vp = [C.c_void_p(256)] * 4
+    # photometric loss: null buffers, lambda_ssim outside [0, 1], negative or non-finite lambda_dep
+    assert L.ts_pho_loss(C.byref(plan), C.c_void_p(256), *vp, C.c_float(0.2), C.c_float(0.05), None, None, None,
+                         None) == 1
+    for lam, lam_dep in ((-0.1, 0.05), (1.5, 0.05), (0.2, -1.0), (0.2, float("inf")), (float("nan"), 0.05)):
+        assert L.ts_pho_loss(C.byref(plan), C.c_void_p(256), *vp, C.c_float(lam), C.c_float(lam_dep), *vp,
+                             None) == 1
     # misaligned workspace
     assert L.ts_bin(C.byref(plan), C.c_void_p(8), None) == 1
     assert ts.ts_status_string(3) == "pair capacity exceeded"

@@ -140,6 +140,40 @@ def noise_targets(seed: int, cams: np.ndarray, depth_lo: float = 0.5, depth_hi: 
     return tc, td
 
 
+
+def loss_images(seed: int, cams: np.ndarray, shift: int = 2, noise: float = 0.05, flat: float = 0.25,
+                invalid: float = 0.1):
+    """Packed per-view image pairs for the loss: a "render" C of smooth noise (per channel, the
+    clamp to [0, 1] of 0.5 + 0.5 * a sum of 4 random sinusoids in x, y) with a ``flat`` fraction of
+    8 x 8 blocks set to a constant colour (the flat regions of real renders), and a target Cbar =
+    C shifted by ``shift`` pixels plus N(0, noise), clamped to [0, 1]; depth D ~ U[0.5, 4] and
+    Dbar = D (1 + 0.01 N(0, 1)) with an ``invalid`` fraction of zeros.  Returns float32 flat arrays
+    (C [3P], D [P], Cbar [3P], Dbar [P]) in the library's packing."""
+    rng = np.random.default_rng(seed)
+    Cs, Ds, tCs, tDs = [], [], [], []
+    for c in cams:
+        W, H = int(c[4]), int(c[5])
+        yy, xx = np.mgrid[0:H + shift, 0:W + shift].astype(np.float64)
+        img = np.empty((3, H + shift, W + shift))
+        for ch in range(3):
+            acc = np.zeros_like(xx)
+            for _ in range(4):
+                w = rng.uniform(0.05, 0.5, size=2)
+                acc += np.sin(w[0] * xx + w[1] * yy + rng.uniform(0, 2 * np.pi))
+            img[ch] = np.clip(0.5 + 0.5 * acc / 2.0, 0.0, 1.0)
+        for by in range(0, H + shift, 8):
+            for bx in range(0, W + shift, 8):
+                if rng.random() < flat:
+                    img[:, by:by + 8, bx:bx + 8] = rng.random((3, 1, 1))
+        C = img[:, :H, :W]
+        tC = np.clip(img[:, shift:, shift:] + rng.normal(0.0, noise, size=(3, H, W)), 0.0, 1.0)
+        D = rng.uniform(0.5, 4.0, size=(H, W))
+        tD = D * (1.0 + 0.01 * rng.normal(size=(H, W)))
+        tD[rng.random((H, W)) < invalid] = 0.0
+        Cs.append(C.ravel()); tCs.append(tC.ravel()); Ds.append(D.ravel()); tDs.append(tD.ravel())
+    f = lambda xs: np.concatenate(xs).astype(np.float32)  # noqa: E731
+    return f(Cs), f(Ds), f(tCs), f(tDs)
+
 # --------------------------------------------------------------------------
 # workloads
 # --------------------------------------------------------------------------
