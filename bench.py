@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 FLOPS_FWD = 35.0   # algorithmic flops per blended (pixel, face) contribution, forward
 FLOPS_BWD = 90.0   # per differentiated contribution, backward raster
+# fused L1 + D-SSIM + depth loss, per pixel and channel: 5 window moments as separable 11 + 11-tap
+# sums (FMA = 2 flops: 220) and their 3 products, SSIM with its 3 partials (~30), the adjoint as 3
+# separable window sums (132), and the gradient and L1 terms (~9)
+FLOPS_PHO = 394.0
 W, H, F, N_FACES, N_VIEWS = 1200, 680, 600.0, 300_000, 20
 WORKLOAD = "room 1200x680 f=600, 300k faces, 20 poses, fwd+bwd (L1 colour+depth), batched"
 
@@ -231,10 +235,36 @@ def bench_tracking(ts, torch, dev, n_hyp=64, iters=100):
     e0 = ts.pose_error(init, np.tile(gt, (n_hyp, 1)))
     e1 = ts.pose_error(trk.poses.cpu().numpy(), np.tile(gt, (n_hyp, 1)))
     px = n_hyp * W_ * H_ * iters
-    return {"workload": f"640x480 f=525, 150k-face room, {n_hyp} hypotheses x {iters} iterations (graph replay)",
+    return {"workload": f"640x480 f=525, 150k-face room, {n_hyp} hypotheses x {iters} iterations (graph replay), "
+                        "E_track = 0.8 L1 + 0.2 D-SSIM + 0.05 depth L1",
             "mpix_s": px / ms / 1e3, "ms_per_iteration": ms / iters,
             "median_error_before": {"cm": float(np.median(e0[:, 0]) * 100), "deg": float(np.median(e0[:, 1]))},
             "median_error_after": {"cm": float(np.median(e1[:, 0]) * 100), "deg": float(np.median(e1[:, 1]))}}
+
+
+def bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max, reps=10):
+    """The fused photometric loss of Eq. 8-10 ((1 - 0.2) L1 + 0.2 D-SSIM on colour, 0.05 L1 on depth)
+    with its image gradients, on the bench's rendered views; device time with the L2 flushed."""
+    call = (rast.plan, rast.ws, rast.color, rast.depth, tgt_c, tgt_d, 0.2, 0.05, rast.loss_v, rast.dC, rast.dD)
+    for _ in range(3):
+        ts.ts_pho_loss(*call)
+    ms = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ts.ts_pho_loss(*call)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.median(ms))
+    ach = FLOPS_PHO * 3 * pixels / (t / 1e3) / 1e12
+    return {"workload": WORKLOAD.split(",")[0] + ", 20 rendered views vs noise targets", "ms": t,
+            "mpix_s": pixels / (t / 1e3) / 1e6,
+            "roofline": {"kernel": "k_pho_tile", "bound": "alu", "achieved": ach, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                         "work": f"{3 * pixels} pixel-channels x {FLOPS_PHO:.0f} flops"}}
 
 
 def bench_serving(ts, torch, dev, rates=(200, 500, 1000, 2000), seconds=2.0, n_faces=2_000_000):
@@ -464,6 +494,7 @@ def main():
             "clocks": clocks,
         }
         if not args.no_extras:
+            line["pho_loss"] = bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max)
             del rast
             torch.cuda.empty_cache()
             line["mapping_window"] = bench_mapping_window(ts, torch, dev)

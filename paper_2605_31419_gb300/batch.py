@@ -25,16 +25,19 @@ STAGE_SIZES = (32, 64, 128)
 
 
 class MultiViewStep:
-    """Forward, L1 loss and backward of all views of ``cams`` on ``m`` in one batched pass."""
+    """Forward, loss and backward of all views of ``cams`` on ``m`` in one batched pass.
+
+    The loss is E_pho + lambda_dep E_dep (Eq. 8, 13): (1 - lambda_ssim) L1 + lambda_ssim D-SSIM on
+    colour, L1 on depth; lambda_ssim = 0 uses the plain L1 kernel."""
 
     def __init__(self, m: Map, cams, poses: torch.Tensor, tgt_color: torch.Tensor, tgt_depth: torch.Tensor,
                  params: Optional[B.TsRasterParams] = None, grad: Optional[Map] = None, lambda_dep: float = 0.05,
-                 pair_capacity: int = 0, want_pose: bool = True):
+                 pair_capacity: int = 0, want_pose: bool = True, lambda_ssim: float = 0.0):
         self.map, self.poses = m, poses
         self.tc, self.td = tgt_color, tgt_depth
         self.rast = Rasterizer(cams, m.n_faces, params, pair_capacity=pair_capacity)
         self.grad = grad
-        self.lambda_dep = float(lambda_dep)
+        self.lambda_dep, self.lambda_ssim = float(lambda_dep), float(lambda_ssim)
         self.want_pose = want_pose
         self.graph: Optional[torch.cuda.CUDAGraph] = None
 
@@ -43,7 +46,10 @@ class MultiViewStep:
         r.project(self.map, self.poses)
         r.bin()
         r.render_fwd()
-        r.l1_loss(self.tc, self.td, self.lambda_dep)
+        if self.lambda_ssim > 0:
+            r.pho_loss(self.tc, self.td, self.lambda_ssim, self.lambda_dep)
+        else:
+            r.l1_loss(self.tc, self.td, self.lambda_dep)
         r.backward(r.dC, r.dD, None, self.grad)
         if self.want_pose:
             r.pose_grad()

@@ -15,7 +15,8 @@
 // values, such as the zeros of a clamped or black background.)
 //
 // One CTA owns a 32 x 32 output tile of one view and walks the three channels.  It stages x and y
-// over the tile widened by 10 pixels (the window of a window), filters the five moment maps along
+// over the tile widened by 10 pixels (the window of a window) with asynchronous copies, the next
+// channel's while the current one is processed, filters the five moment maps along
 // rows and then columns over the tile widened by 5, evaluates SSIM and m0..m2 there, filters those
 // three maps back over the tile, and writes dL/dC.  Every filter pass is register-blocked: a
 // thread produces R consecutive outputs along the filter direction from R + 10 shared-memory
@@ -38,14 +39,40 @@ constexpr int MO = OT + 2 * RAD, MS = MO + 1;   // moment / partial maps: 42 x 4
 constexpr int OS = OT + 1;                      // column-filtered partials: 42 rows x 32, stride 33
 constexpr int R_H1 = 7, R_V1 = 7, R_H2 = 8, R_V2 = 4;
 static_assert(MO % R_H1 == 0 && MO % R_V1 == 0 && OT % R_H2 == 0 && OT % R_V2 == 0, "blocking");
-constexpr int SM_X = 0, SM_Y = SM_X + IN * IS, SM_H = SM_Y + IN * IS, SM_M = SM_H + 5 * IN * MS,
-              SM_FLOATS = SM_M + 3 * MO * MS;
+// two staging buffers (x, y) so that the next channel streams in while this one is filtered
+constexpr int SM_XY = 0, SM_H = SM_XY + 4 * IN * IS, SM_M = SM_H + 5 * IN * MS, SM_FLOATS = SM_M + 3 * MO * MS;
 static_assert(3 * MO * OS <= 5 * IN * MS, "column-filtered partials alias the moment rows");
 constexpr size_t PHO_SMEM = (size_t)SM_FLOATS * 4;
 
 struct Taps {
   float w[NT];
 };
+
+// 4-byte asynchronous global-to-shared copy; valid == false writes a zero and reads nothing.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Issue the copies of x and y over image rows Y0-10 .. Y0+41 and columns X0-10 .. X0+41 (zeros
+// outside the image) into one staging buffer.
+__device__ __forceinline__ void stage_channel(float* sx, float* sy, const float* xc, const float* yc, int X0, int Y0,
+                                              int W, int H) {
+  for (int i = threadIdx.x; i < IN * IN; i += PT) {
+    const int r = i / IN, c = i - r * IN;
+    const int gy = Y0 - 2 * RAD + r, gx = X0 - 2 * RAD + c;
+    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+    const long long o = in ? (long long)gy * W + gx : 0;
+    cp_async4(sx + r * IS + c, xc + o, in);
+    cp_async4(sy + r * IS + c, yc + o, in);
+  }
+  cp_async_commit();
+}
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
 #pragma unroll
@@ -74,30 +101,24 @@ __global__ void __launch_bounds__(PT, 2)
   const long long HW = (long long)W * H;
   const float inv3 = 1.0f / (3.0f * (float)HW);
   const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-  float* sx = sm + SM_X;
-  float* sy = sm + SM_Y;
   float* hmo = sm + SM_H;  // 5 maps [IN][MS]: row-filtered moments
   float* mp = sm + SM_M;   // 3 maps [MO][MS]: partials m0, m1, m2
   float* hm = sm + SM_H;   // 3 maps [MO][OS]: column-filtered partials (aliases hmo)
   float l1 = 0.f, ss = 0.f, dep = 0.f;
 
+  stage_channel(sm + SM_XY, sm + SM_XY + IN * IS, C + 3 * pix_off, tC + 3 * pix_off, X0, Y0, W, H);
   for (int ch = 0; ch < 3; ++ch) {
-    const float* xc = C + 3 * pix_off + ch * HW;
-    const float* yc = tC + 3 * pix_off + ch * HW;
-    // stage x, y over image rows Y0-10 .. Y0+41 and columns X0-10 .. X0+41, zeros outside
-    for (int i = threadIdx.x; i < IN * IN; i += PT) {
-      const int r = i / IN, c = i - r * IN;
-      const int gy = Y0 - 2 * RAD + r, gx = X0 - 2 * RAD + c;
-      float a = 0.f, b = 0.f;
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-        const long long o = (long long)gy * W + gx;
-        a = __ldg(xc + o);
-        b = __ldg(yc + o);
-      }
-      sx[r * IS + c] = a;
-      sy[r * IS + c] = b;
+    if (ch + 1 < 3) {
+      float* nb = sm + SM_XY + ((ch + 1) & 1) * 2 * IN * IS;
+      stage_channel(nb, nb + IN * IS, C + 3 * pix_off + (ch + 1) * HW, tC + 3 * pix_off + (ch + 1) * HW, X0, Y0, W,
+                    H);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const float* sx = sm + SM_XY + (ch & 1) * 2 * IN * IS;
+    const float* sy = sx + IN * IS;
     // rows: moments at staged row r, columns cm in [0, MO) (image column X0 - 5 + cm)
     for (int it = threadIdx.x; it < IN * (MO / R_H1); it += PT) {
       const int r = it % IN, c0 = (it / IN) * R_H1;
@@ -230,11 +251,12 @@ __global__ void __launch_bounds__(PT, 2)
         }
       }
     }
-    __syncthreads();  // the next channel restages x, y and reuses every map
+    __syncthreads();  // the channel after next restages into this buffer; every map is reused
   }
   // depth term of Eq. 9 over the tile's own pixels
   {
     const float id = lambda_dep / (float)HW;
+#pragma unroll
     for (int i = threadIdx.x; i < OT * OT; i += PT) {
       const int gy = Y0 + i / OT, gx = X0 + i % OT;
       if (gx < W && gy < H) {

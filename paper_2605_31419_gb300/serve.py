@@ -66,10 +66,11 @@ class Server:
     def __init__(self, m: Map, params: Optional[B.TsRasterParams] = None, max_views: int = 32,
                  max_pixels: int = 32 * 1200 * 680, pair_capacity: Optional[int] = None, track_iters: int = 10,
                  lr_rot: float = 0.003, lr_trans: float = 0.001, lambda_dep: float = 0.05,
-                 hbm_fraction: float = 0.5, device="cuda"):
+                 lambda_ssim: float = 0.2, hbm_fraction: float = 0.5, device="cuda"):
         self.map, self.params = m, (params if params is not None else B.ts_default_params())
         self.max_views, self.max_pixels = int(max_views), int(max_pixels)
         self.track_iters, self.lambda_dep = int(track_iters), float(lambda_dep)
+        self.lambda_ssim = float(lambda_ssim)
         self.lr_rot, self.lr_trans = float(lr_rot), float(lr_trans)
         self.device = torch.device(device)
         M = m.n_faces
@@ -157,8 +158,12 @@ class Server:
             B.ts_project(plan, self.map.ts(), poses, lane.ws, s)
             B.ts_bin(plan, lane.ws, s)
             B.ts_render_fwd(plan, lane.ws, lane.color, lane.depth, lane.alpha, s)
-            B.ts_l1_loss(plan, lane.ws, lane.color, lane.depth, tc, td, self.lambda_dep, self.loss, self.dC,
-                         self.dD, s)
+            if self.lambda_ssim > 0:
+                B.ts_pho_loss(plan, lane.ws, lane.color, lane.depth, tc, td, self.lambda_ssim, self.lambda_dep,
+                              self.loss, self.dC, self.dD, s)
+            else:
+                B.ts_l1_loss(plan, lane.ws, lane.color, lane.depth, tc, td, self.lambda_dep, self.loss, self.dC,
+                             self.dD, s)
             B.ts_render_bwd(plan, lane.ws, self.dC, self.dD, None, None, s)
             B.ts_pose_grad(plan, lane.ws, self.dtau, s)
             B.ts_pose_adam(plan, poses, self.dtau, adam, self.lr_trans, self.lr_rot, stream=s)

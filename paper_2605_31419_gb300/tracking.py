@@ -1,8 +1,8 @@
 """Differentiable camera tracking (Triangle Splatting SLAM, Sec. 3.3-3.4 "Tracking").
 
 Many pose hypotheses of one frame are rendered as the views of one plan, so every iteration is a
-single batched pass: project, bin, forward blend, L1 colour + depth loss (Eq. 8 L1 part, Eq. 9,
-Eq. 10 with lambda_dep), backward to the pose (Eq. 5-7, map gradients skipped) and an Adam step
+single batched pass: project, bin, forward blend, the tracking loss E_track (Eq. 8-10: (1 - lambda)
+L1 + lambda D-SSIM colour terms, lambda = 0.2, and the L1 depth term with lambda_dep), backward to the pose (Eq. 5-7, map gradients skipped) and an Adam step
 on the manifold gradient applied as T <- Exp(-step) o T.  One iteration is captured once in a CUDA
 graph and replayed, so 100 iterations cost 100 graph launches.  All arithmetic runs in libts.
 """
@@ -21,10 +21,13 @@ class Tracker:
     """Track ``len(init_poses)`` hypotheses of one camera against one RGB-D target.
 
     target_color: [3, H, W] and target_depth: [H, W] (numpy or tensors); the target is shared by
-    all hypotheses.  Learning rates default to Table S5 (rotation 0.003, translation 0.001)."""
+    all hypotheses.  Learning rates and loss weights default to Table S5 (rotation 0.003,
+    translation 0.001, D-SSIM weight 0.2, depth weight 0.05); lambda_ssim = 0 drops the D-SSIM term
+    and uses the plain L1 kernel."""
 
     def __init__(self, m: Map, cam, target_color, target_depth, init_poses, params: Optional[B.TsRasterParams] = None,
-                 lr_rot: float = 0.003, lr_trans: float = 0.001, lambda_dep: float = 0.05, device="cuda"):
+                 lr_rot: float = 0.003, lr_trans: float = 0.001, lambda_dep: float = 0.05, lambda_ssim: float = 0.2,
+                 device="cuda"):
         cam = np.asarray(cam, np.float64).reshape(6)
         init_poses = np.asarray(init_poses, np.float32).reshape(-1, 12)
         self.n_hyp = len(init_poses)
@@ -39,6 +42,7 @@ class Tracker:
         self.td = td.repeat(self.n_hyp).contiguous()
         self.state = torch.zeros(self.n_hyp, 13, dtype=torch.float32, device=device)
         self.lr_rot, self.lr_trans, self.lambda_dep = float(lr_rot), float(lr_trans), float(lambda_dep)
+        self.lambda_ssim = float(lambda_ssim)
         self.graph: Optional[torch.cuda.CUDAGraph] = None
 
     def step(self):
@@ -47,7 +51,10 @@ class Tracker:
         r.project(self.map, self.poses)
         r.bin()
         r.render_fwd()
-        r.l1_loss(self.tc, self.td, self.lambda_dep)
+        if self.lambda_ssim > 0:
+            r.pho_loss(self.tc, self.td, self.lambda_ssim, self.lambda_dep)
+        else:
+            r.l1_loss(self.tc, self.td, self.lambda_dep)
         r.backward(r.dC, r.dD, None, None)
         r.pose_grad()
         B.ts_pose_adam(r.plan, self.poses, r.dtau, self.state, self.lr_trans, self.lr_rot)

@@ -58,7 +58,8 @@ def _tracking_scene(n_faces=60000, W=160, H=120, f=131.25):
     return Scene(pos, col, opa, None, cams, gt[None, :])
 
 
-def test_tracking_converges_with_graph_replay(oracle):
+@pytest.mark.parametrize("lambda_ssim", [0.2, 0.0])
+def test_tracking_converges_with_graph_replay(oracle, lambda_ssim):
     import torch
     import paper_2605_31419_gb300 as ts
     from oracle.oracle import SceneArrays
@@ -72,7 +73,7 @@ def test_tracking_converges_with_graph_replay(oracle):
     gt = sc.poses[0]
     init = np.stack([perturb_pose(gt, rng, trans=0.03, rot_deg=1.5) for _ in range(8)])
     m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa)
-    trk = ts.Tracker(m, sc.cams[0], tc, td, init, p)
+    trk = ts.Tracker(m, sc.cams[0], tc, td, init, p, lambda_ssim=lambda_ssim)
     trk.run(100, use_graph=True)
     torch.cuda.synchronize()
     err0 = ts.pose_error(init, np.tile(gt, (8, 1)))
@@ -82,9 +83,9 @@ def test_tracking_converges_with_graph_replay(oracle):
     # eager execution of the same iterations matches the graph replay (over a few iterations:
     # Adam normalises each step, so last-bit differences of the atomic gradient sums can flip
     # individual steps and the two trajectories drift apart by ~1 mm over 100 iterations)
-    a = ts.Tracker(m, sc.cams[0], tc, td, init, p)
+    a = ts.Tracker(m, sc.cams[0], tc, td, init, p, lambda_ssim=lambda_ssim)
     a.run(3, use_graph=True)
-    b = ts.Tracker(m, sc.cams[0], tc, td, init, p)
+    b = ts.Tracker(m, sc.cams[0], tc, td, init, p, lambda_ssim=lambda_ssim)
     b.run(3, use_graph=False)
     torch.cuda.synchronize()
     assert np.allclose(a.poses.cpu().numpy(), b.poses.cpu().numpy(), atol=2e-5)
