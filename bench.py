@@ -34,6 +34,10 @@ FLOPS_BWD = 90.0   # per differentiated contribution, backward raster
 # sums (FMA = 2 flops: 220) and their 3 products, SSIM with its 3 partials (~30), the adjoint as 3
 # separable window sums (132), and the gradient and L1 terms (~9)
 FLOPS_PHO = 394.0
+# DRAM bytes (read + write) per view of one k_render_bwd launch of this workload, from the ncu
+# capture in profiles/render_kernels_room_4views_full.md (4 views, tile 16x8, 64 faces per stage),
+# scaled by the views of the launch; reported only for that launch configuration
+BWD_TRAFFIC_PER_VIEW = (178.1312e6 + 23.51104e6) / 4
 W, H, F, N_FACES, N_VIEWS = 1200, 680, 600.0, 300_000, 20
 WORKLOAD = "room 1200x680 f=600, 300k faces, 20 poses, fwd+bwd (L1 colour+depth), batched"
 
@@ -45,7 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the mapping-window and tracking measurements")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mapping-window, tracking and serving measurements")
     ap.add_argument("--faces", type=int, default=N_FACES)
     ap.add_argument("--views", type=int, default=N_VIEWS)
     ap.add_argument("--tile", default="16x8")
@@ -259,7 +264,7 @@ def bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_pea
         ms.append(a.elapsed_time(b))
     t = float(np.median(ms))
     ach = FLOPS_PHO * 3 * pixels / (t / 1e3) / 1e12
-    return {"workload": WORKLOAD.split(",")[0] + ", 20 rendered views vs noise targets", "ms": t,
+    return {"workload": WORKLOAD.split(",")[0] + f", {rast.V} rendered views vs noise targets", "ms": t,
             "mpix_s": pixels / (t / 1e3) / 1e6,
             "roofline": {"kernel": "k_pho_tile", "bound": "alu", "achieved": ach, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
@@ -470,7 +475,9 @@ def main():
             flops = (FLOPS_BWD if names[dom] == "bwd_raster" else FLOPS_FWD) * contrib
             ach = flops / (stage_ms[dom] / 1e3) / 1e12
             roof = {"kernel": f"k_render_{'bwd' if names[dom] == 'bwd_raster' else 'fwd'}", "bound": "alu",
-                    "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                    "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                    "traffic": (BWD_TRAFFIC_PER_VIEW * sc.n_views if names[dom] == "bwd_raster" and args.tile == "16x8"
+                                and args.stage == 64 else None),
                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                     "work": f"{contrib} (pixel, face) contributions x {FLOPS_BWD if names[dom] == 'bwd_raster' else FLOPS_FWD:.0f} flops"}
         else:
@@ -493,8 +500,8 @@ def main():
             "roofline": roof, "peaks": peak_src, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clocks,
         }
+        line["pho_loss"] = bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max)
         if not args.no_extras:
-            line["pho_loss"] = bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max)
             del rast
             torch.cuda.empty_cache()
             line["mapping_window"] = bench_mapping_window(ts, torch, dev)

@@ -45,13 +45,13 @@
 //      ceil(min - 0.5) .. floor(max - 0.5) clamped to the image;
 //   R11 loss = mean |C - Cbar| over 3HW + lambda_dep * sum_{Dbar>0} |D - Dbar| / HW
 //      per view, summed over views; sign(0) = 0;
-//   R15 the D-SSIM term of Eq. 8 is 1 - SSIM, SSIM the mean over the 3HW channel pixels of the
+//   R16 the D-SSIM term of Eq. 8 is 1 - SSIM, SSIM the mean over the 3HW channel pixels of the
 //      per-pixel structural similarity (Wang et al. 2004) with the common defaults: 11 x 11
 //      Gaussian window, sigma 1.5, normalised to sum 1; C1 = 0.01^2, C2 = 0.03^2 (colours in
 //      [0, 1]);
-//   R16 the window sums see zeros outside the image ("same"-size output, zero padding), and
+//   R17 the window sums see zeros outside the image ("same"-size output, zero padding), and
 //      every image pixel carries one SSIM value;
-//   R17 E_pho weights the same mean L1 colour term as R11 by (1 - lambda), lambda = 0.2
+//   R18 E_pho weights the same mean L1 colour term as R11 by (1 - lambda), lambda = 0.2
 //      (Table S5); the depth term is that of R11;
 //   R14 in FP32 mode the projection follows one fixed operation order with
 //      no fused multiply-add (build with -ffp-contract=off), so that culling,
@@ -788,7 +788,7 @@ double oracle_l1_loss(const or_scene* sc, const double* color, const double* dep
   return total;
 }
 
-// Photometric loss of Eq. 8 with the depth term of Eq. 9 (R15-R17), per view:
+// Photometric loss of Eq. 8 with the depth term of Eq. 9 (R16-R18), per view:
 //   loss_v = (1 - lambda) mean_{3HW} |C - Cbar| + lambda (1 - mean_{3HW} SSIM(C, Cbar))
 //            + lambda_dep sum_{Dbar > 0} |D - Dbar| / HW.
 // SSIM at a pixel p of one channel is the structural similarity of Wang et al. (2004) with local
