@@ -144,6 +144,8 @@ class Oracle:
         L.oracle_l1_loss.restype = d
         L.oracle_pho_loss.argtypes = [vp, vp, vp, vp, vp, d, d, vp, vp, vp, vp, vp]
         L.oracle_pho_loss.restype = d
+        L.oracle_equilateral.argtypes = [vp, vp]
+        L.oracle_equilateral.restype = d
         L.oracle_window.argtypes = [vp, d, d, d, vp]
         L.oracle_window.restype = d
         L.oracle_se3_exp.argtypes = [vp, vp]
@@ -235,6 +237,13 @@ class Oracle:
                                        float(lambda_ssim), float(lambda_dep), _ptr(loss_v), _ptr(dC), _ptr(dD),
                                        _ptr(smap), _ptr(dC_abs))
         return dict(loss=tot, loss_v=loss_v, dC=dC, dD=dD, ssim_map=smap, dC_abs=dC_abs)
+
+    def equilateral(self, sa: SceneArrays, grads: bool = True):
+        """Eq. 14: mean over faces of the mean squared deviation of the angle cosines from 0.5."""
+        dpos = np.zeros((len(sa.pos), 3)) if grads else None
+        sc = sa.c()
+        e = self.lib.oracle_equilateral(C.byref(sc), _ptr(dpos))
+        return dict(loss=e, dpos=dpos)
 
     # -- small pieces used by the pins ---------------------------------------------------
     def window(self, tri2d, sigma: float, px: float, py: float):

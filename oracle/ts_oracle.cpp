@@ -18,7 +18,9 @@
 //     opacities, and the pose through the left perturbation Exp(tau) o T
 //     (Eq. 5-7, tau = (rho, theta), translation first);
 //   * Eq. 8-10 the tracking loss: L1 and D-SSIM photometric terms and the L1
-//     depth term, with their gradients w.r.t. the rendered images.
+//     depth term, with their gradients w.r.t. the rendered images;
+//   * Eq. 14 the equilateral regulariser of the mapping loss and its gradient
+//     w.r.t. vertex positions.
 //
 // How: the forward pass walks each pixel's depth-sorted list literally.  The
 // backward pass stores every contribution of a pixel front to back, forms the
@@ -53,6 +55,8 @@
 //      every image pixel carries one SSIM value;
 //   R18 E_pho weights the same mean L1 colour term as R11 by (1 - lambda), lambda = 0.2
 //      (Table S5); the depth term is that of R11;
+//   R19 Eq. 14 averages over all M faces; a face with a zero-length edge has no defined angle
+//      and adds 0 (no gradient);
 //   R14 in FP32 mode the projection follows one fixed operation order with
 //      no fused multiply-add (build with -ffp-contract=off), so that culling,
 //      pixel boxes, tiles and depth keys are bit-identical to any other
@@ -917,6 +921,58 @@ double oracle_window(const double* q, double sigma, double px, double py, double
   const double I = window_and_bary<double>(qx, qy, px, py, sigma, lam, &ratio);
   if (lam_out) for (int k = 0; k < 3; ++k) lam_out[k] = lam[k];
   return I;
+}
+
+// Equilateral regulariser of Eq. 14 (R19): E = (1/M) sum_faces (1/3) sum_n (cos theta_n - 0.5)^2,
+// theta_n the internal angle at vertex n, cos theta_n from the normalised edge vectors leaving
+// vertex n.  A face with a zero-length edge adds 0 (it still counts in M).  dpos [N][3]
+// (optional) receives dE/dpos, added over the faces that share a vertex; each face is
+// differentiated with forward-mode dual numbers over its 9 vertex coordinates.
+double oracle_equilateral(const or_scene* sc, double* dpos) {
+  const int64_t M = sc->n_faces;
+  if (dpos) std::memset(dpos, 0, sizeof(double) * 3 * sc->n_vertices);
+  if (M == 0) return 0.0;
+  double total = 0;
+  for (int64_t m = 0; m < M; ++m) {
+    Dual P[3][3];
+    int64_t vi[3];
+    for (int k = 0; k < 3; ++k) {
+      vi[k] = vidx(sc, m, k);
+      for (int c = 0; c < 3; ++c) {
+        P[k][c] = Dual(sc->pos[3 * vi[k] + c]);
+        P[k][c].d[3 * k + c] = 1.0;
+      }
+    }
+    bool degenerate = false;
+    Dual e(0.0);
+    for (int n = 0; n < 3; ++n) {
+#if ORACLE_MUTANT == 16
+      const int i1 = (n + 1) % 3, i2 = (n + 2) % 3, i0 = i1;  // second edge leaves the wrong vertex
+#else
+      const int i1 = (n + 1) % 3, i2 = (n + 2) % 3, i0 = n;
+#endif
+      Dual a[3], b[3];
+      for (int c = 0; c < 3; ++c) {
+        a[c] = P[i1][c] - P[n][c];
+        b[c] = P[i2][c] - P[i0][c];
+      }
+      const Dual aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+      const Dual bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+      if (!(aa.v > 0) || !(bb.v > 0)) {
+        degenerate = true;
+        break;
+      }
+      const Dual cs = (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / (sqrt_(aa) * sqrt_(bb));
+      const Dual d = cs - Dual(0.5);
+      e = e + d * d;
+    }
+    if (degenerate) continue;
+    total += e.v / 3.0;
+    if (dpos)
+      for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c) dpos[3 * vi[k] + c] += e.d[3 * k + c] / (3.0 * (double)M);
+  }
+  return total / (double)M;
 }
 
 // SE(3) exponential (closed form of Sola et al., "A micro Lie theory"):

@@ -443,6 +443,53 @@ def pin_pho_fd(o: Oracle):
 
 
 # ---------------------------------------------------------------------------------------------
+# Equilateral regulariser (Eq. 14, R19): closed forms, invariances, finite differences
+# ---------------------------------------------------------------------------------------------
+def _soup(tris, seed=0):
+    tris = np.asarray(tris, np.float64).reshape(-1, 3)
+    n = len(tris)
+    return SceneArrays.of(Scene(tris.astype(np.float32), np.full((n, 3), 0.5, np.float32), np.full(n, 0.8, np.float32),
+                                None, np.array([[10.0, 10.0, 5.0, 5.0, 10, 10]]),
+                                np.array([[1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0]], np.float32)), pos=tris)
+
+
+def pin_equilateral_closed_forms(o: Oracle):
+    s3 = np.sqrt(3.0)
+    # equilateral: every cosine is 0.5
+    r = o.equilateral(_soup([[0, 0, 1], [2, 0, 1], [1, s3, 1]]))
+    assert abs(r["loss"]) < 1e-15 and np.abs(r["dpos"]).max() < 1e-12
+    # 3-4-5 right triangle: cosines 0, 4/5, 3/5 -> (0.25 + 0.09 + 0.01) / 3 = 7/60
+    assert abs(o.equilateral(_soup([[0, 0, 0], [4, 0, 0], [0, 3, 0]]))["loss"] - 7.0 / 60.0) < 1e-15
+    # right isosceles: cosines 0, 1/sqrt2, 1/sqrt2
+    c = 1 / np.sqrt(2.0)
+    expect = (0.25 + 2 * (c - 0.5) ** 2) / 3
+    assert abs(o.equilateral(_soup([[0, 0, 0], [1, 0, 0], [0, 1, 0]]))["loss"] - expect) < 1e-15
+    # the mean over faces, with a degenerate face (zero-length edge) adding 0 but counting
+    r = o.equilateral(_soup([[0, 0, 0], [4, 0, 0], [0, 3, 0], [1, 1, 1], [1, 1, 1], [2, 0, 0]]))
+    assert abs(r["loss"] - 7.0 / 120.0) < 1e-15
+    assert np.all(r["dpos"][3:] == 0)
+
+
+def pin_equilateral_invariance_and_fd(o: Oracle):
+    rng = np.random.default_rng(41)
+    tris = rng.normal(size=(30, 3, 3))
+    base = o.equilateral(_soup(tris.reshape(-1, 3)))
+    # similarity transforms leave every angle unchanged
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    moved = 2.7 * tris.reshape(-1, 3) @ Q.T + np.array([0.3, -1.0, 4.0])
+    assert abs(o.equilateral(_soup(moved))["loss"] - base["loss"]) < 1e-13
+    # central differences of every coordinate
+    flat = tris.reshape(-1, 3)
+    h = 1e-6
+    for idx in np.ndindex(flat.shape):
+        xp, xm = flat.copy(), flat.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (o.equilateral(_soup(xp), grads=False)["loss"] - o.equilateral(_soup(xm), grads=False)["loss"]) / (2 * h)
+        assert abs(fd - base["dpos"][idx]) <= 1e-8 + 1e-5 * abs(fd), (idx, fd, base["dpos"][idx])
+
+
+# ---------------------------------------------------------------------------------------------
 # SE(3) exponential against scipy's matrix exponential of the twist
 # ---------------------------------------------------------------------------------------------
 def twist_expm(tau):
@@ -519,5 +566,5 @@ def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
 
 ALL_PINS = [pin_window_closed_form, pin_barycentric, pin_projection, pin_single_triangle, pin_coverage_bruteforce,
             pin_fronto_parallel_depth, pin_transmittance_product, pin_termination_stack, pin_binning_bruteforce,
-            pin_sort_ties, pin_l1_loss, pin_ssim_scipy, pin_ssim_closed_forms, pin_pho_fd, pin_se3_exp,
-            pin_fd_gradients]
+            pin_sort_ties, pin_l1_loss, pin_ssim_scipy, pin_ssim_closed_forms, pin_pho_fd,
+            pin_equilateral_closed_forms, pin_equilateral_invariance_and_fd, pin_se3_exp, pin_fd_gradients]

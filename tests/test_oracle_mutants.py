@@ -5,14 +5,17 @@ edge normals (Eq. 2), a transposed rotation (Eq. 1), compositing with the transm
 face instead of before it (Eq. 4), a dropped background term, integer instead of half-integer
 pixel centres, a rotated barycentric index for depth, a flipped cross product in the pose
 Jacobian (Eq. 7), a missing 1/(1 - alpha) in the adjoint, a descending depth sort, an
-off-by-one tile box, and a wrong loss normalisation.
+off-by-one tile box, a wrong loss normalisation; in the D-SSIM term of Eq. 8 the luminance
+constant used for the contrast term, a dropped factor 2 in d(x^2)/dx, and edge clamping instead
+of zero padding; and in the equilateral regulariser (Eq. 14) an angle measured between edges that
+leave different vertices.
 """
 import pytest
 
 import oracle_pins as P
 from oracle.oracle import Oracle
 
-MUTANTS = list(range(1, 16))
+MUTANTS = list(range(1, 17))
 
 
 @pytest.mark.parametrize("k", MUTANTS)
