@@ -218,6 +218,21 @@ ts_status ts_l1_loss_noalloc(const ts_camera* cams, int32_t n_views, const float
                              const float* tgt_color, const float* tgt_depth, float lambda_dep, float* loss,
                              float* dC, float* dD, ts_stream stream);
 
+/* Equilateral regulariser of the mapping loss (Eq. 14), over the plan's n_faces faces of map:
+ *   E = (1/M) sum_faces (1/3) sum_n (cos theta_n - 0.5)^2,
+ * theta_n the internal angle at vertex n, its cosine from the normalised edge vectors leaving
+ * vertex n.  A face with a zero-length edge adds 0 and no gradient (it still counts in M).
+ *   map:    device buffers as for ts_project (only positions and faces are read).
+ *   ws:     the plan's workspace (only its partial-sum region is written; no earlier call needed).
+ *   loss:   device float [1], overwritten with E (unweighted).
+ *   grad:   NULL, or device buffers whose gpx, gpy, gpz (each may be NULL) receive
+ *           += weight * dE/dpos; the paper weights E by lambda_equi = 1.2 (Table S5).
+ * Deterministic for soup maps; indexed meshes add shared-vertex terms with atomics.  A face
+ * index outside [0, n_vertices) latches the bounds bit (TS_ERR_CUDA at ts_sync_status) and the
+ * face is skipped. */
+ts_status ts_equilateral(const ts_plan* plan, const ts_map* map, void* ws, size_t ws_bytes, float weight,
+                         float* loss, const ts_map_grad* grad, ts_stream stream);
+
 /* Pose update for tracking: poses[v] <- Exp(-step[v]) o poses[v] (left perturbation, closed-form
  * SE(3) exponential), step = (rho, theta) device float [n_views][6]; poses device [n_views]. */
 ts_status ts_pose_apply(const ts_plan* plan, ts_pose* poses, const float* step, ts_stream stream);

@@ -87,6 +87,8 @@ SIGNATURES = {
     "ts_pose_grad": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
     "ts_l1_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
     "ts_pose_apply": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
+    "ts_equilateral": (_st, [C.POINTER(TsPlan), C.POINTER(TsMap), _vp, C.c_size_t, C.c_float, _vp,
+                             C.POINTER(TsMapGrad), _vp]),
     "ts_pho_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
     "ts_l1_loss_noalloc": (_st, [C.POINTER(TsCamera), _i32, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
     "ts_pose_adam": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
@@ -233,6 +235,12 @@ def ts_render_bwd(plan, ws, dC, dD, dA, grad: Optional[TsMapGrad], stream=None):
     g = grad if grad is not None else TsMapGrad()
     _check(lib().ts_render_bwd(C.byref(plan), _ptr(ws), _ptr(dC), _ptr(dD), _ptr(dA), C.byref(g), _stream(stream)),
            "ts_render_bwd")
+
+
+def ts_equilateral(plan, tsmap: TsMap, ws, weight, loss, grad: Optional[TsMapGrad] = None, stream=None):
+    _check(lib().ts_equilateral(C.byref(plan), C.byref(tsmap), _ptr(ws), ws.numel() * ws.element_size(),
+                                float(weight), _ptr(loss), C.byref(grad) if grad is not None else None,
+                                _stream(stream)), "ts_equilateral")
 
 
 def ts_pose_grad(plan, ws, dtau, stream=None):

@@ -134,6 +134,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_loss = take((size_t)n_views * p->n_loss_blocks * 2 * 4);
   p->o_cmask = take((size_t)cap * 2);
   p->o_pho = take((size_t)n_views * p->n_pho_blocks * 3 * 4);
+  p->o_equi = take((size_t)ts_equi_blocks(n_faces) * 4);
   p->total = o;
   p->magic = TS_PLAN_MAGIC;
   return TS_OK;
@@ -266,6 +267,19 @@ ts_status ts_pho_loss(const ts_plan* plan, void* ws, const float* color, const f
   StageTimer t(p, TS_STAGE_LOSS, s);
   return cuda_status(ts_launch_pho_loss(p, ts_ws(p, ws), color, depth, tgt_color, tgt_depth, lambda_ssim, lambda_dep,
                                         loss, dC, dD, s));
+}
+
+ts_status ts_equilateral(const ts_plan* plan, const ts_map* map, void* ws, size_t ws_bytes, float weight, float* loss,
+                         const ts_map_grad* grad, ts_stream stream) {
+  const TsPlanImpl* p = impl(plan);
+  if (!p || !map || !loss || !ws_ok(p, ws, ws_bytes) || !std::isfinite(weight)) return TS_ERR_INVALID_ARG;
+  if (map->n_faces != p->M) return TS_ERR_INVALID_ARG;
+  if (p->M > 0) {
+    if (!map->px || !map->py || !map->pz) return TS_ERR_INVALID_ARG;
+    if (!map->faces && map->n_vertices != 3 * map->n_faces) return TS_ERR_INVALID_ARG;
+    if (map->faces && map->n_vertices < 1) return TS_ERR_INVALID_ARG;
+  }
+  return cuda_status(ts_launch_equilateral(p, ts_ws(p, ws), map, weight, loss, grad, (cudaStream_t)stream));
 }
 
 ts_status ts_pose_apply(const ts_plan* plan, ts_pose* poses, const float* step, ts_stream stream) {

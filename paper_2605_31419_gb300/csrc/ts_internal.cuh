@@ -87,7 +87,7 @@ struct TsPlanImpl {
   int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks, n_pho_blocks;
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
-      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, total;
+      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, o_equi, total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
   TsView views[TS_MAX_VIEWS];
@@ -116,6 +116,7 @@ struct TsWs {
   float* pose;
   float* loss;
   float* pho;  // per (view, 32 x 32 tile): L1, SSIM and depth partial sums of the photometric loss
+  float* equi;  // per block of 256 faces: partial sums of the equilateral regulariser
   uint16_t* cmask;  // per sorted pair: the warps of its tile that blended the face in the forward
 };
 
@@ -144,6 +145,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.pose = (float*)(b + p->o_pose);
   w.loss = (float*)(b + p->o_loss);
   w.pho = (float*)(b + p->o_pho);
+  w.equi = (float*)(b + p->o_equi);
   w.cmask = (uint16_t*)(b + p->o_cmask);
   return w;
 }
@@ -171,6 +173,9 @@ inline TsImageTable ts_image_table(const TsPlanImpl* p) {
   return t;
 }
 int64_t ts_pho_blocks(const TsView* views, int V);
+int64_t ts_equi_blocks(int64_t M);
+cudaError_t ts_launch_equilateral(const TsPlanImpl* p, const TsWs& w, const ts_map* map, float weight, float* loss,
+                                  const ts_map_grad* grad, cudaStream_t s);
 cudaError_t ts_launch_pho_loss(const TsPlanImpl* p, const TsWs& w, const float* color, const float* depth,
                                const float* tc, const float* td, float lambda, float lambda_dep, float* loss,
                                float* dC, float* dD, cudaStream_t s);

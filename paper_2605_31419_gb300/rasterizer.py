@@ -125,6 +125,13 @@ class Rasterizer:
                       self.loss_v, self.dC, self.dD, stream)
         return self.loss_v, self.dC, self.dD
 
+    def equilateral(self, m: Map, weight: float = 1.2, grad: Optional[Map] = None, out=None, stream=None):
+        """Eq. 14 on the map's faces: returns E (device [1]); adds weight * dE/dpos into grad.pos."""
+        out = torch.empty(1, dtype=torch.float32, device=self.ws.device) if out is None else out
+        g = B.make_grad(grad.pos, None, None) if grad is not None else None
+        B.ts_equilateral(self.plan, m.ts(), self.ws, weight, out, g, stream)
+        return out
+
     def plan_passes(self) -> int:
         """Radix-sort passes per ts_bin: 8 bits each over 32 depth bits + ceil(log2 tiles) tile bits."""
         n_tiles = int(self.layout["tile_off"][-1])

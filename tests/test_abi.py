@@ -93,6 +93,9 @@ def test_device_calls_reject_null_arguments(ts):
     # photometric loss: null buffers, lambda_ssim outside [0, 1], negative or non-finite lambda_dep
     assert L.ts_pho_loss(C.byref(plan), C.c_void_p(256), *vp, C.c_float(0.2), C.c_float(0.05), None, None, None,
                          None) == 1
+    # equilateral regulariser: null map or loss, a non-finite weight
+    assert L.ts_equilateral(C.byref(plan), None, C.c_void_p(256), 1 << 30, C.c_float(1.0), C.c_void_p(256),
+                            None, None) == 1
     for lam, lam_dep in ((-0.1, 0.05), (1.5, 0.05), (0.2, -1.0), (0.2, float("inf")), (float("nan"), 0.05)):
         assert L.ts_pho_loss(C.byref(plan), C.c_void_p(256), *vp, C.c_float(lam), C.c_float(lam_dep), *vp,
                              None) == 1
