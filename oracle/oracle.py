@@ -135,11 +135,13 @@ class Oracle:
         L.oracle_bin.restype = i64
         L.oracle_total_tiles.argtypes = [vp, vp]
         L.oracle_total_tiles.restype = i64
-        L.oracle_forward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_forward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_pixel_trace.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, i32, vp]
         L.oracle_pixel_trace.restype = i32
         L.oracle_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
-        L.oracle_backward_ex.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_backward_ex.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_normal_loss.argtypes = [vp, vp, vp, d, vp, vp]
+        L.oracle_normal_loss.restype = d
         L.oracle_l1_loss.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, vp]
         L.oracle_l1_loss.restype = d
         L.oracle_pho_loss.argtypes = [vp, vp, vp, vp, vp, d, d, vp, vp, vp, vp, vp]
@@ -179,12 +181,13 @@ class Oracle:
     def forward(self, sa: SceneArrays, prm: Params):
         off = sa.pix_offsets()
         P = int(off[-1])
-        color = np.empty(3 * P)
+        color, normal = np.empty(3 * P), np.empty(3 * P)
         depth, alpha, T = np.empty(P), np.empty(P), np.empty(P)
         n_last = np.empty(P, np.int32)
         sc, p = sa.c(), prm.c()
-        self.lib.oracle_forward(C.byref(sc), C.byref(p), _ptr(color), _ptr(depth), _ptr(alpha), _ptr(T), _ptr(n_last))
-        return dict(color=color, depth=depth, alpha=alpha, T_final=T, n_last=n_last, pix_off=off)
+        self.lib.oracle_forward(C.byref(sc), C.byref(p), _ptr(color), _ptr(depth), _ptr(alpha), _ptr(T), _ptr(n_last),
+                                _ptr(normal))
+        return dict(color=color, depth=depth, alpha=alpha, T_final=T, n_last=n_last, normal=normal, pix_off=off)
 
     def pixel_trace(self, sa: SceneArrays, prm: Params, view: int, x: int, y: int, cap: int = 4096):
         faces = np.empty(cap, np.int32)
@@ -197,17 +200,17 @@ class Oracle:
         return dict(faces=faces[:n], alpha=alphas[:n], T_before=Tb[:n], T_final=Tf.value)
 
     # -- adjoint ---------------------------------------------------------------------------
-    def backward(self, sa: SceneArrays, prm: Params, dC, dD=None, dA=None):
+    def backward(self, sa: SceneArrays, prm: Params, dC, dD=None, dA=None, dN=None):
         N = len(sa.pos)
         dpos, dcol = np.zeros((N, 3)), np.zeros((N, 3))
         dopa = np.zeros(N)
         dtau = np.zeros((len(sa.cams), 6))
         dtau_abs = np.zeros((len(sa.cams), 6))
         f = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
-        dC, dD, dA = f(dC), f(dD), f(dA)
+        dC, dD, dA, dN = f(dC), f(dD), f(dA), f(dN)
         sc, p = sa.c(), prm.c()
-        self.lib.oracle_backward_ex(C.byref(sc), C.byref(p), _ptr(dC), _ptr(dD), _ptr(dA), _ptr(dpos), _ptr(dcol),
-                                    _ptr(dopa), _ptr(dtau), _ptr(dtau_abs))
+        self.lib.oracle_backward_ex(C.byref(sc), C.byref(p), _ptr(dC), _ptr(dD), _ptr(dA), _ptr(dN), _ptr(dpos),
+                                    _ptr(dcol), _ptr(dopa), _ptr(dtau), _ptr(dtau_abs))
         return dict(dpos=dpos, dcol=dcol, dopa=dopa, dtau=dtau, dtau_abs=dtau_abs)
 
     def l1_loss(self, sa: SceneArrays, color, depth, tgt_color, tgt_depth, lambda_dep: float = 0.05):
@@ -237,6 +240,17 @@ class Oracle:
                                        float(lambda_ssim), float(lambda_dep), _ptr(loss_v), _ptr(dC), _ptr(dD),
                                        _ptr(smap), _ptr(dC_abs))
         return dict(loss=tot, loss_v=loss_v, dC=dC, dD=dD, ssim_map=smap, dC_abs=dC_abs)
+
+    def normal_loss(self, sa: SceneArrays, normal, tgt_normal, weight: float = 1.0):
+        """Eq. 12: sum over pixels with a sensor normal of (1 - N . Nbar) / HW, per view; dN of weight x that."""
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+        normal, tgt_normal = f(normal), f(tgt_normal)
+        loss_v = np.empty(len(sa.cams))
+        dN = np.empty_like(normal)
+        sc = sa.c()
+        tot = self.lib.oracle_normal_loss(C.byref(sc), _ptr(normal), _ptr(tgt_normal), float(weight), _ptr(loss_v),
+                                          _ptr(dN))
+        return dict(loss=tot, loss_v=loss_v, dN=dN)
 
     def equilateral(self, sa: SceneArrays, grads: bool = True):
         """Eq. 14: mean over faces of the mean squared deviation of the angle cosines from 0.5."""

@@ -19,6 +19,8 @@
 //     (Eq. 5-7, tau = (rho, theta), translation first);
 //   * Eq. 8-10 the tracking loss: L1 and D-SSIM photometric terms and the L1
 //     depth term, with their gradients w.r.t. the rendered images;
+//   * Eq. 12 the rendered normal map and the normal loss, with the normal's
+//     gradient folded into the adjoint above;
 //   * Eq. 14 the equilateral regulariser of the mapping loss and its gradient
 //     w.r.t. vertex positions.
 //
@@ -57,6 +59,13 @@
 //      (Table S5); the depth term is that of R11;
 //   R19 Eq. 14 averages over all M faces; a face with a zero-length edge has no defined angle
 //      and adds 0 (no gradient);
+//   R20 the rendered normal map of Eq. 12 is composited like colour, N = sum alpha_n T_n n_F,
+//      with the face's unit normal n_F in camera space and no background term;
+//   R21 n_F is turned towards the camera: the normalised (v1 - v0) x (v2 - v0) of the
+//      camera-space vertices, negated when it has a positive dot product with v0 + v1 + v2
+//      (triangles are two-sided, so the winding carries no orientation);
+//   R22 Eq. 12 sums 1 - N . Nbar over the pixels with a sensor normal (Nbar != 0), divided by
+//      HW like the depth term of R11; N is used as rendered (not renormalised);
 //   R14 in FP32 mode the projection follows one fixed operation order with
 //      no fused multiply-add (build with -ffp-contract=off), so that culling,
 //      pixel boxes, tiles and depth keys are bit-identical to any other
@@ -367,9 +376,27 @@ inline double face_opacity(double o0, double o1, double o2) {
 
 // Per (pixel, face) quantities used by the compositing.
 struct Term {
-  double alpha, I, ratio, col[3], z;
+  double alpha, I, ratio, col[3], z, nrm[3];
   bool clamped;
 };
+
+// Unit normal of face m in camera space, turned towards the camera (R20, R21): the normalised
+// cross product (v1 - v0) x (v2 - v0) of the camera-space vertices, negated when it points away
+// from the camera (positive dot product with the vertex sum).  S is double or Dual; vc [3][3].
+template <class S>
+void face_normal(const S vc[3][3], S n[3]) {
+  S e1[3], e2[3];
+  for (int r = 0; r < 3; ++r) { e1[r] = vc[1][r] - vc[0][r]; e2[r] = vc[2][r] - vc[0][r]; }
+  S u[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  const S len = sqrt_(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  double facing = 0;
+  for (int r = 0; r < 3; ++r) facing += val(u[r]) * (val(vc[0][r]) + val(vc[1][r]) + val(vc[2][r]));
+#if ORACLE_MUTANT == 17
+  facing = -1.0;  // never turned: the winding decides
+#endif
+  const S sgn(facing > 0 ? -1.0 : 1.0);
+  for (int r = 0; r < 3; ++r) n[r] = sgn * u[r] / len;
+}
 
 Term eval_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px, double py) {
   const or_scene* sc = c.sc;
@@ -392,7 +419,18 @@ Term eval_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px, dou
 #else
   t.z = lam[0] * pr.z[0] + lam[1] * pr.z[1] + lam[2] * pr.z[2];
 #endif
-  (void)view;
+  const double* P = sc->poses + 12 * view;
+  double vc[3][3];
+  for (int k = 0; k < 3; ++k) {
+    const double* X = sc->pos + 3 * vidx(sc, m, k);
+    for (int r = 0; r < 3; ++r)
+#if ORACLE_MUTANT == 18
+      vc[k][r] = X[r];  // world instead of camera space
+#else
+      vc[k][r] = P[3 * r] * X[0] + P[3 * r + 1] * X[1] + P[3 * r + 2] * X[2] + P[9 + r];
+#endif
+  }
+  face_normal<double>(vc, t.nrm);
   return t;
 }
 
@@ -492,7 +530,7 @@ double walk_pixel(const Ctx& c, const Bins& b, int view, int x, int y, std::vect
 
 // ---------------------------------------------------------------- dual evaluation for the adjoint
 struct DualTerm {
-  Dual alpha, col[3], z;
+  Dual alpha, col[3], z, nrm[3];
 };
 
 // alpha, colour and depth of face m at pixel (px, py) as functions of the
@@ -509,7 +547,7 @@ DualTerm dual_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px,
   const or_scene* sc = c.sc;
   const View& w = c.views[view];
   const double* P = sc->poses + 12 * view;
-  Dual qx[3], qy[3], zc[3], col[3][3], op[3];
+  Dual qx[3], qy[3], zc[3], col[3][3], op[3], vcs[3][3];
   Dual rho[3], th[3];
   for (int i = 0; i < 3; ++i) {
     rho[i] = Dual(0.0); rho[i].d[21 + i] = 1.0;
@@ -535,6 +573,7 @@ DualTerm dual_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px,
     cr[2] = th[0] * vc[1] - th[1] * vc[0];
 #endif
     for (int r = 0; r < 3; ++r) vc[r] = vc[r] + rho[r] + cr[r];
+    for (int r = 0; r < 3; ++r) vcs[k][r] = vc[r];
     qx[k] = Dual(w.fx) * (vc[0] / vc[2]) + Dual(w.cx);
     qy[k] = Dual(w.fy) * (vc[1] / vc[2]) + Dual(w.cy);
     zc[k] = vc[2];
@@ -559,6 +598,7 @@ DualTerm dual_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px,
 #else
   t.z = lam[0] * zc[0] + lam[1] * zc[1] + lam[2] * zc[2];
 #endif
+  face_normal<Dual>(vcs, t.nrm);
   return t;
 }
 
@@ -614,9 +654,10 @@ int64_t oracle_bin(const or_scene* sc, const or_params* p, uint64_t* keys, uint3
 
 int64_t oracle_total_tiles(const or_scene* sc, const or_params* p) { return make_ctx(sc, p).n_tiles; }
 
-// Eq. 4 forward.  Images are packed per view: colour [3][H][W], the others [H][W].
+// Eq. 4 forward.  Images are packed per view: colour and normal [3][H][W], the others [H][W].
+// normal (optional): the rendered normal map of Eq. 12, sum_n alpha_n T_n n_F (R20), no background.
 int oracle_forward(const or_scene* sc, const or_params* p, double* color, double* depth, double* alpha,
-                   double* T_final, int32_t* n_last) {
+                   double* T_final, int32_t* n_last, double* normal) {
   Ctx c = make_ctx(sc, p);
   Bins b = make_bins(c);
   const int nt = threads_of(p);
@@ -629,10 +670,11 @@ int oracle_forward(const or_scene* sc, const or_params* p, double* color, double
       for (int x = 0; x < w.W; ++x) {
         int64_t nl;
         const double T = walk_pixel(c, b, v, x, y, &list, &nl);
-        double C[3] = {0, 0, 0}, D = 0, A = 0;
+        double C[3] = {0, 0, 0}, D = 0, A = 0, N[3] = {0, 0, 0};
         for (const Contrib& k : list) {
           const double wgt = k.alpha * k.T;
           for (int ch = 0; ch < 3; ++ch) C[ch] += wgt * k.term.col[ch];
+          for (int ch = 0; ch < 3; ++ch) N[ch] += wgt * k.term.nrm[ch];
           D += wgt * k.term.z;
           A += wgt;
         }
@@ -645,6 +687,7 @@ int oracle_forward(const or_scene* sc, const or_params* p, double* color, double
         if (alpha) alpha[w.pix_off + pi] = A;
         if (T_final) T_final[w.pix_off + pi] = T;
         if (n_last) n_last[w.pix_off + pi] = (int32_t)nl;
+        if (normal) for (int ch = 0; ch < 3; ++ch) normal[3 * w.pix_off + ch * HW + pi] = N[ch];
       }
     }
   }
@@ -668,13 +711,13 @@ int oracle_pixel_trace(const or_scene* sc, const or_params* p, int view, int x, 
   return n;
 }
 
-// Adjoint of Eq. 4 and Eq. 1-3 for the loss gradients dC, dD, dA (same packing
-// as the images).  Gradients are ADDED to dpos [N][3], dcol [N][3], dopa [N],
+// Adjoint of Eq. 4 and Eq. 1-3 for the loss gradients dC, dD, dA, dN (same packing
+// as the images; dN, the gradient w.r.t. the normal map, may be NULL).  Gradients are ADDED to dpos [N][3], dcol [N][3], dopa [N],
 // dtau [V][6] (rho then theta).  dtau_abs (optional, [V][6]) receives the sum of the absolute
 // values of the per-(pixel, face) pose terms: the scale against which the cancelling sum dtau is
 // compared.
 int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC, const double* dD, const double* dA,
-                       double* dpos, double* dcol, double* dopa, double* dtau, double* dtau_abs) {
+                       const double* dN, double* dpos, double* dcol, double* dopa, double* dtau, double* dtau_abs) {
   Ctx c = make_ctx(sc, p);
   Bins b = make_bins(c);
   const int nt = threads_of(p);
@@ -689,8 +732,9 @@ int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC,
         int64_t nl;
         const double Tf = walk_pixel(c, b, v, x, y, &list, &nl);
         const int64_t pi = (int64_t)y * w.W + x;
-        double gC[3], gD, gA;
+        double gC[3], gD, gA, gN[3];
         for (int ch = 0; ch < 3; ++ch) gC[ch] = dC ? dC[3 * w.pix_off + ch * HW + pi] : 0.0;
+        for (int ch = 0; ch < 3; ++ch) gN[ch] = dN ? dN[3 * w.pix_off + ch * HW + pi] : 0.0;
         gD = dD ? dD[w.pix_off + pi] : 0.0;
         gA = dA ? dA[w.pix_off + pi] : 0.0;
         const size_t n = list.size();
@@ -703,14 +747,16 @@ int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC,
 #endif
         for (size_t k = n; k-- > 0;) {
           const Contrib& q = list[k];
-          const double valk = gC[0] * q.term.col[0] + gC[1] * q.term.col[1] + gC[2] * q.term.col[2] + gD * q.term.z + gA;
+          const double valk = gC[0] * q.term.col[0] + gC[1] * q.term.col[1] + gC[2] * q.term.col[2] + gD * q.term.z + gA +
+                              gN[0] * q.term.nrm[0] + gN[1] * q.term.nrm[1] + gN[2] * q.term.nrm[2];
           suffix[k] = suffix[k + 1] + valk * q.alpha * q.T;
         }
         double px, py;
         pixel_centre(x, y, &px, &py);
         for (size_t k = 0; k < n; ++k) {
           const Contrib& q = list[k];
-          const double valk = gC[0] * q.term.col[0] + gC[1] * q.term.col[1] + gC[2] * q.term.col[2] + gD * q.term.z + gA;
+          const double valk = gC[0] * q.term.col[0] + gC[1] * q.term.col[1] + gC[2] * q.term.col[2] + gD * q.term.z + gA +
+                              gN[0] * q.term.nrm[0] + gN[1] * q.term.nrm[1] + gN[2] * q.term.nrm[2];
 #if ORACLE_MUTANT == 9
           const double dalpha = valk * q.T - suffix[k + 1];
 #else
@@ -721,7 +767,7 @@ int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC,
           double g[NT];
           for (int i = 0; i < NT; ++i) {
             g[i] = dalpha * dt.alpha.d[i] + gD * wgt * dt.z.d[i];
-            for (int ch = 0; ch < 3; ++ch) g[i] += gC[ch] * wgt * dt.col[ch].d[i];
+            for (int ch = 0; ch < 3; ++ch) g[i] += gC[ch] * wgt * dt.col[ch].d[i] + gN[ch] * wgt * dt.nrm[ch].d[i];
           }
           for (int kk = 0; kk < 3; ++kk) {
             const int64_t vi = vidx(sc, q.face, kk);
@@ -755,7 +801,7 @@ int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC,
 
 int oracle_backward(const or_scene* sc, const or_params* p, const double* dC, const double* dD, const double* dA,
                     double* dpos, double* dcol, double* dopa, double* dtau) {
-  return oracle_backward_ex(sc, p, dC, dD, dA, dpos, dcol, dopa, dtau, nullptr);
+  return oracle_backward_ex(sc, p, dC, dD, dA, nullptr, dpos, dcol, dopa, dtau, nullptr);
 }
 
 // L1 colour + depth loss (R11).  Returns the total over views; loss_v [V];
@@ -921,6 +967,37 @@ double oracle_window(const double* q, double sigma, double px, double py, double
   const double I = window_and_bary<double>(qx, qy, px, py, sigma, lam, &ratio);
   if (lam_out) for (int k = 0; k < 3; ++k) lam_out[k] = lam[k];
   return I;
+}
+
+// Normal loss of Eq. 12 (R22), per view: loss_v = sum_{p valid} (1 - N_p . Nbar_p) / HW, a pixel
+// valid where the sensor normal Nbar_p is not the zero vector; dN = weight * dloss_v/dN (written;
+// the weight is lambda_norm of Eq. 15).
+double oracle_normal_loss(const or_scene* sc, const double* normal, const double* tgt_normal, double weight,
+                          double* loss_v, double* dN) {
+  double total = 0;
+  int64_t off = 0;
+  for (int v = 0; v < sc->n_views; ++v) {
+    const int W = (int)sc->cams[6 * v + 4], H = (int)sc->cams[6 * v + 5];
+    const int64_t HW = (int64_t)W * H;
+    double l = 0;
+    for (int64_t i = 0; i < HW; ++i) {
+      double nb[3], dot = 0;
+      bool valid = false;
+      for (int ch = 0; ch < 3; ++ch) {
+        nb[ch] = tgt_normal[3 * off + ch * HW + i];
+        valid = valid || nb[ch] != 0.0;
+        dot += normal[3 * off + ch * HW + i] * nb[ch];
+      }
+      if (valid) l += 1.0 - dot;
+      if (dN)
+        for (int ch = 0; ch < 3; ++ch) dN[3 * off + ch * HW + i] = valid ? -weight * nb[ch] / (double)HW : 0.0;
+    }
+    l /= (double)HW;
+    if (loss_v) loss_v[v] = l;
+    total += l;
+    off += HW;
+  }
+  return total;
 }
 
 // Equilateral regulariser of Eq. 14 (R19): E = (1/M) sum_faces (1/3) sum_n (cos theta_n - 0.5)^2,

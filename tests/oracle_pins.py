@@ -443,6 +443,75 @@ def pin_pho_fd(o: Oracle):
 
 
 # ---------------------------------------------------------------------------------------------
+# Rendered normal map (Eq. 12, R20-R22): plane normals in camera space, winding, the loss
+# ---------------------------------------------------------------------------------------------
+def _rot(axis, deg):
+    a = np.asarray(axis, np.float64) / np.linalg.norm(axis)
+    th = np.radians(deg)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+
+
+def pin_normal_closed_forms(o: Oracle):
+    prm = Params(alpha_min=0.0)
+    # fronto-parallel face at z = 2 under the identity pose: N = A (0, 0, -1) (towards the camera)
+    sc = _single_face_scene([[-0.6, -0.5, 2.0], [0.7, -0.4, 2.0], [0.0, 0.6, 2.0]], [[0.5] * 3] * 3, [0.9, 0.6, 0.8],
+                            cam=(20.0, 20.0, 16.0, 16.0, 32, 32))
+    f = o.forward(SceneArrays.of(sc), prm)
+    P = 32 * 32
+    N = f["normal"].reshape(3, P)
+    assert f["alpha"].max() > 0.5
+    assert np.abs(N[0]).max() < 1e-12 and np.abs(N[1]).max() < 1e-12
+    assert np.abs(N[2] + f["alpha"]).max() < 1e-12
+    # a tilted face under a rotated, translated camera: N = A n_C, n_C = R n_W turned to the camera
+    R = _rot([0.3, -1.0, 0.4], 25.0)
+    t = np.array([0.1, -0.2, 2.5])
+    n_w = np.array([0.2, 0.5, -1.0]) / np.linalg.norm([0.2, 0.5, -1.0])
+    b1 = np.cross(n_w, [1.0, 0.0, 0.0]); b1 /= np.linalg.norm(b1)
+    b2 = np.cross(n_w, b1)
+    c_w = R.T @ (np.array([0.05, 0.0, 2.6]) - t)  # a point in front of the camera
+    verts = [c_w + 0.8 * b1, c_w - 0.5 * b1 + 0.7 * b2, c_w - 0.4 * b1 - 0.8 * b2]
+    pose = np.concatenate([R.reshape(-1), t]).astype(np.float32)
+    for order in ((0, 1, 2), (0, 2, 1)):  # both windings give the same map
+        sc = _single_face_scene([verts[i] for i in order], [[0.5] * 3] * 3, [0.9, 0.6, 0.8],
+                                cam=(24.0, 24.0, 16.0, 16.0, 32, 32), pose=pose)
+        sa = SceneArrays.of(sc)
+        f = o.forward(sa, prm)
+        # the plane's normal carried into the camera frame (R rounded to float32 is orthonormal to
+        # ~1e-8, hence the tolerance), turned towards the camera centre
+        n_c = R @ n_w
+        if n_c @ (R @ c_w + t) > 0:
+            n_c = -n_c
+        A = f["alpha"]
+        assert A.max() > 0.5
+        N = f["normal"].reshape(3, P)
+        assert np.abs(N - n_c[:, None] * A[None, :]).max() < 1e-7, order
+
+
+def pin_normal_loss(o: Oracle):
+    sizes = [(9, 7), (5, 4)]
+    sa = _loss_cams(sizes)
+    rng = np.random.default_rng(51)
+    P = sum(W * H for W, H in sizes)
+    N = rng.normal(size=3 * P)
+    Nb = rng.normal(size=(3, P))
+    Nb /= np.linalg.norm(Nb, axis=0)
+    Nb[:, ::4] = 0.0  # no sensor normal at every fourth pixel
+    Nb = Nb.reshape(-1)
+    r = o.normal_loss(sa, N, Nb, weight=0.05)
+    off = 0
+    for v, (W, H) in enumerate(sizes):
+        HW = W * H
+        n = N[3 * off:3 * off + 3 * HW].reshape(3, HW)
+        nb = Nb[3 * off:3 * off + 3 * HW].reshape(3, HW)
+        valid = np.abs(nb).sum(0) > 0
+        expect = (1 - (n * nb).sum(0))[valid].sum() / HW
+        assert abs(r["loss_v"][v] - expect) < 1e-12
+        assert np.allclose(r["dN"][3 * off:3 * off + 3 * HW].reshape(3, HW), -0.05 * nb * valid / HW, atol=1e-15)
+        off += HW
+
+
+# ---------------------------------------------------------------------------------------------
 # Equilateral regulariser (Eq. 14, R19): closed forms, invariances, finite differences
 # ---------------------------------------------------------------------------------------------
 def _soup(tris, seed=0):
@@ -514,9 +583,9 @@ def pin_se3_exp(o: Oracle):
 # ---------------------------------------------------------------------------------------------
 # Adjoint vs central finite differences (FP64 mode) on tiny scenes
 # ---------------------------------------------------------------------------------------------
-def _linear_functional(sa, prm, o, wC, wD, wA):
+def _linear_functional(sa, prm, o, wC, wD, wA, wN):
     f = o.forward(sa, prm)
-    return float(wC @ f["color"] + wD @ f["depth"] + wA @ f["alpha"])
+    return float(wC @ f["color"] + wD @ f["depth"] + wA @ f["alpha"] + wN @ f["normal"])
 
 
 def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
@@ -529,11 +598,12 @@ def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
                 rng = np.random.default_rng(seed + 100)
                 P = int(base.pix_offsets()[-1])
                 wC, wD, wA = rng.normal(size=3 * P), rng.normal(size=P), rng.normal(size=P)
-                an = o.backward(base, prm, wC, wD, wA)
+                wN = rng.normal(size=3 * P)
+                an = o.backward(base, prm, wC, wD, wA, wN)
                 h = 1e-6
 
                 def J(**kw):
-                    return _linear_functional(SceneArrays.of(sc, **kw), prm, o, wC, wD, wA)
+                    return _linear_functional(SceneArrays.of(sc, **kw), prm, o, wC, wD, wA, wN)
 
                 for name, arr, key in (("pos", base.pos, "dpos"), ("col", base.col, "dcol"), ("opa", base.opa, "dopa")):
                     g = an[key]
@@ -567,4 +637,5 @@ def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
 ALL_PINS = [pin_window_closed_form, pin_barycentric, pin_projection, pin_single_triangle, pin_coverage_bruteforce,
             pin_fronto_parallel_depth, pin_transmittance_product, pin_termination_stack, pin_binning_bruteforce,
             pin_sort_ties, pin_l1_loss, pin_ssim_scipy, pin_ssim_closed_forms, pin_pho_fd,
-            pin_equilateral_closed_forms, pin_equilateral_invariance_and_fd, pin_se3_exp, pin_fd_gradients]
+            pin_normal_closed_forms, pin_normal_loss, pin_equilateral_closed_forms, pin_equilateral_invariance_and_fd,
+            pin_se3_exp, pin_fd_gradients]

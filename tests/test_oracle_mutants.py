@@ -8,14 +8,15 @@ Jacobian (Eq. 7), a missing 1/(1 - alpha) in the adjoint, a descending depth sor
 off-by-one tile box, a wrong loss normalisation; in the D-SSIM term of Eq. 8 the luminance
 constant used for the contrast term, a dropped factor 2 in d(x^2)/dx, and edge clamping instead
 of zero padding; and in the equilateral regulariser (Eq. 14) an angle measured between edges that
-leave different vertices.
+leave different vertices; and for the rendered normal map (Eq. 12) a normal left as the winding
+gives it and a normal in world instead of camera space.
 """
 import pytest
 
 import oracle_pins as P
 from oracle.oracle import Oracle
 
-MUTANTS = list(range(1, 17))
+MUTANTS = list(range(1, 19))
 
 
 @pytest.mark.parametrize("k", MUTANTS)
