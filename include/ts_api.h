@@ -83,6 +83,12 @@ typedef struct {
  * Results are identical; it helps when tiles of very uneven cost (mixed resolutions) are batched. */
 #define TS_FLAG_PERSISTENT 1
 
+/* ts_raster_params.flags: also render the normal map of Eq. 12 (ts_render_fwd_n) and take its
+ * gradient (ts_render_bwd_n).  The projection then stores each visible face's unit normal in
+ * camera space, turned towards the camera (triangles are two-sided), 16 bytes per (view, face),
+ * and the raster kernels stage it beside the face's record. */
+#define TS_FLAG_NORMALS 2
+
 /* The map (Sec. 3.1): N vertices with position, colour, opacity as structure-of-arrays float32
  * device buffers, and M faces.  faces = NULL selects triangle-soup mode (face m uses vertices
  * 3m, 3m+1, 3m+2; N = 3M); otherwise faces is device int32 [M][3].  The buffers must stay valid
@@ -164,6 +170,13 @@ ts_status ts_bin(const ts_plan* plan, void* ws, ts_stream stream);
 ts_status ts_render_fwd(const ts_plan* plan, void* ws, float* color, float* depth, float* alpha,
                         ts_stream stream);
 
+/* ts_render_fwd that also writes the rendered normal map of Eq. 12: normal [3][H][W] packed per
+ * view like color, N = sum alpha_n T_n n_F with n_F the face's camera-space unit normal turned
+ * towards the camera, no background term.  normal != NULL needs a plan with TS_FLAG_NORMALS
+ * (else TS_ERR_INVALID_ARG) and must not alias the other outputs. */
+ts_status ts_render_fwd_n(const ts_plan* plan, void* ws, float* color, float* depth, float* alpha, float* normal,
+                          ts_stream stream);
+
 /* Adjoint of Eq. 1-4: back-to-front re-traversal from each pixel's last contribution, recovering
  * transmittance by division, warp-level reduction of per-face gradients before global atomics,
  * then the chain rule through the projection into the map gradients (added, see ts_map_grad)
@@ -172,6 +185,20 @@ ts_status ts_render_fwd(const ts_plan* plan, void* ws, float* color, float* dept
  *   grad may be NULL or have NULL members to skip map gradients. */
 ts_status ts_render_bwd(const ts_plan* plan, void* ws, const float* dC, const float* dD,
                         const float* dA, const ts_map_grad* grad, ts_stream stream);
+
+/* ts_render_bwd with the gradient dN [3][H][W] of the loss w.r.t. the normal map (device, packed
+ * per view; NULL = zero), which reaches the vertex positions and the pose through each face's
+ * normal and through alpha and T.  dN != NULL needs a plan with TS_FLAG_NORMALS. */
+ts_status ts_render_bwd_n(const ts_plan* plan, void* ws, const float* dC, const float* dD, const float* dA,
+                          const float* dN, const ts_map_grad* grad, ts_stream stream);
+
+/* Normal loss of Eq. 12 per view: loss_v = sum over pixels with a sensor normal (tgt_normal not
+ * the zero vector) of (1 - N . Nbar) / (HW), N as rendered (not renormalised); dN = weight *
+ * dloss_v/dN (written; weight is lambda_norm of Eq. 15, 0.05 in Table S5).  normal, tgt_normal
+ * and dN: device [3][H][W] packed per view; loss: device float [n_views], overwritten.
+ * Deterministic.  Needs no earlier call on the workspace. */
+ts_status ts_normal_loss(const ts_plan* plan, void* ws, const float* normal, const float* tgt_normal, float weight,
+                         float* loss, float* dN, ts_stream stream);
 
 /* Eq. 5-7: dL/dtau per view for the left perturbation Exp(tau) o T_CW, tau = (rho, theta), as
  * sum over the view's visible face vertices of [g_C ; v_C x g_C], reduced deterministically.

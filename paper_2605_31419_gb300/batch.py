@@ -138,7 +138,7 @@ def autotune(m: Map, cams, poses, tgt_color, tgt_depth, grad: Optional[Map] = No
     return best, results
 
 
-B_FLAG_PERSISTENT = 1  # TS_FLAG_PERSISTENT of include/ts_api.h
+B_FLAG_PERSISTENT = B.TS_FLAG_PERSISTENT
 
 
 def params_of(choice: dict, **overrides) -> B.TsRasterParams:

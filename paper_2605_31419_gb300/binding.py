@@ -20,6 +20,8 @@ TS_PLAN_BYTES = 24576
 STATUS = {0: "TS_OK", 1: "TS_ERR_INVALID_ARG", 2: "TS_ERR_CUDA", 3: "TS_ERR_CAPACITY", 4: "TS_ERR_TIMEOUT",
           5: "TS_ERR_UNSUPPORTED"}
 STAGES = ["project", "bin", "fwd", "bwd_raster", "bwd_project", "pose", "loss"]
+TS_FLAG_PERSISTENT = 1  # ts_raster_params.flags bits of include/ts_api.h
+TS_FLAG_NORMALS = 2
 DEBUG = dict(keys=0, ids=1, ranges=2, rect=3, zbits=4, count=5, T_final=6, n_last=7, records=8)
 
 
@@ -83,6 +85,9 @@ SIGNATURES = {
     "ts_project": (_st, [C.POINTER(TsPlan), C.POINTER(TsMap), _vp, _vp, _sz, _vp]),
     "ts_bin": (_st, [C.POINTER(TsPlan), _vp, _vp]),
     "ts_render_fwd": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp]),
+    "ts_render_fwd_n": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "ts_render_bwd_n": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.POINTER(TsMapGrad), _vp]),
+    "ts_normal_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, C.c_float, _vp, _vp, _vp]),
     "ts_render_bwd": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, C.POINTER(TsMapGrad), _vp]),
     "ts_pose_grad": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
     "ts_l1_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
@@ -229,6 +234,22 @@ def ts_bin(plan, ws, stream=None):
 def ts_render_fwd(plan, ws, color, depth, alpha, stream=None):
     _check(lib().ts_render_fwd(C.byref(plan), _ptr(ws), _ptr(color), _ptr(depth), _ptr(alpha), _stream(stream)),
            "ts_render_fwd")
+
+
+def ts_render_fwd_n(plan, ws, color, depth, alpha, normal, stream=None):
+    _check(lib().ts_render_fwd_n(C.byref(plan), _ptr(ws), _ptr(color), _ptr(depth), _ptr(alpha), _ptr(normal),
+                                 _stream(stream)), "ts_render_fwd_n")
+
+
+def ts_render_bwd_n(plan, ws, dC, dD, dA, dN, grad: Optional[TsMapGrad], stream=None):
+    g = grad if grad is not None else TsMapGrad()
+    _check(lib().ts_render_bwd_n(C.byref(plan), _ptr(ws), _ptr(dC), _ptr(dD), _ptr(dA), _ptr(dN), C.byref(g),
+                                 _stream(stream)), "ts_render_bwd_n")
+
+
+def ts_normal_loss(plan, ws, normal, tgt_normal, weight, loss, dN, stream=None):
+    _check(lib().ts_normal_loss(C.byref(plan), _ptr(ws), _ptr(normal), _ptr(tgt_normal), float(weight), _ptr(loss),
+                                _ptr(dN), _stream(stream)), "ts_normal_loss")
 
 
 def ts_render_bwd(plan, ws, dC, dD, dA, grad: Optional[TsMapGrad], stream=None):

@@ -2,7 +2,8 @@
 //
 // Loss (Eq. 8 L1 part and Eq. 9, per view): sum |C - Cbar| / (3HW) + lambda_dep *
 // sum_{Dbar > 0} |D - Dbar| / (HW), with its gradient written in the same pass; partial sums
-// per block are reduced in a fixed order so the loss is deterministic.
+// per block are reduced in a fixed order so the loss is deterministic.  The normal loss of
+// Eq. 12 follows the same pattern.
 // Pose update: T <- Exp(-step) o T with the closed-form SE(3) exponential (left perturbation,
 // step = (rho, theta)), used by gradient-descent tracking (Sec. 3.3).
 #include <algorithm>
@@ -87,6 +88,64 @@ __global__ void __launch_bounds__(LOSS_T) k_loss_final(const TsImageTable tab, c
     const double HW = (double)tab.W[v] * tab.H[v];
     loss[v] = (float)((double)red[0][0] / (3.0 * HW) + (double)lambda_dep * (double)red[0][1] / HW);
   }
+}
+
+// Normal loss of Eq. 12 per view: sum over pixels with a sensor normal (Nbar != 0) of
+// (1 - N . Nbar) / HW, with dN = weight * dloss/dN = -weight Nbar / HW there and 0 elsewhere.
+__global__ void __launch_bounds__(LOSS_T) k_nloss_partial(const TsImageTable tab, const float* __restrict__ N,
+                                                          const float* __restrict__ tN, float weight,
+                                                          float* __restrict__ dN, float* __restrict__ part, int nblk) {
+  __shared__ float red[LOSS_T / 32];
+  const int v = blockIdx.y;
+  const long long HW = (long long)tab.W[v] * tab.H[v];
+  const long long pix_off = tab.pix_off[v];
+  const long long base = (long long)blockIdx.x * LOSS_T * LOSS_PER;
+  float l = 0.f;
+  if (base < HW) {
+    const float sc = -weight / (float)HW;
+#pragma unroll
+    for (int k = 0; k < LOSS_PER; ++k) {
+      const long long i = base + (long long)k * LOSS_T + threadIdx.x;
+      if (i >= HW) break;
+      float nb[3], dot = 0.f;
+      bool valid = false;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const long long o = 3 * pix_off + ch * HW + i;
+        nb[ch] = tN[o];
+        valid = valid || nb[ch] != 0.f;
+        dot += N[o] * nb[ch];
+      }
+      if (valid) l += 1.f - dot;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) dN[3 * pix_off + ch * HW + i] = valid ? sc * nb[ch] : 0.f;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < LOSS_T / 32; ++w) s += red[w];
+    part[(long long)v * nblk + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(LOSS_T) k_nloss_final(const TsImageTable tab, const float* __restrict__ part,
+                                                        int nblk, float* __restrict__ loss) {
+  __shared__ double red[LOSS_T];
+  const int v = blockIdx.x;
+  double a = 0;
+  for (int k = threadIdx.x; k < nblk; k += LOSS_T) a += part[(long long)v * nblk + k];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = LOSS_T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[v] = (float)(red[0] / ((double)tab.W[v] * tab.H[v]));
 }
 
 // T <- Exp(-st) o T for one view (closed-form SE(3) exponential, st = (rho, theta)).
@@ -193,6 +252,15 @@ cudaError_t ts_launch_l1_loss(const TsPlanImpl* p, const TsWs& w, const float* c
   const TsImageTable tab = ts_image_table(p);
   k_loss_partial<<<grid, LOSS_T, 0, s>>>(tab, color, depth, tc, td, lambda_dep, dC, dD, w.loss, nblk);
   k_loss_final<<<p->V, LOSS_T, 0, s>>>(tab, w.loss, nblk, lambda_dep, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t ts_launch_normal_loss(const TsPlanImpl* p, const TsWs& w, const float* normal, const float* tgt,
+                                  float weight, float* loss, float* dN, cudaStream_t s) {
+  const int nblk = (int)p->n_loss_blocks;
+  const TsImageTable tab = ts_image_table(p);
+  k_nloss_partial<<<dim3((unsigned)nblk, (unsigned)p->V), LOSS_T, 0, s>>>(tab, normal, tgt, weight, dN, w.nloss, nblk);
+  k_nloss_final<<<p->V, LOSS_T, 0, s>>>(tab, w.nloss, nblk, loss);
   return cudaGetLastError();
 }
 

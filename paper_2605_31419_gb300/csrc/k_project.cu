@@ -45,6 +45,7 @@ struct ProjArgs {
   float z_near, r_min, alpha_min;
   int tile_w, tile_h;
   float4* frec;
+  float4* nrm;  // camera-space unit normals (TS_FLAG_NORMALS), else null
   float* grad;
   short4* rect;
   uint32_t* zbits;
@@ -66,17 +67,22 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
     } else {
       vi[0] = 3 * m; vi[1] = 3 * m + 1; vi[2] = 3 * m + 2;
     }
-    float u[3], v[3], z[3], o[3];
+    float u[3], v[3], z[3], o[3], xv[3], yv[3], wp[3][3];
     vis = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const long long j = vi[k];
       if (j < 0 || j >= a.map.n_vertices) { vis = false; break; }
       float xc, yc, zc;
-      ts_rigid_f32(P, __ldg(a.map.px + j), __ldg(a.map.py + j), __ldg(a.map.pz + j), xc, yc, zc);
+      wp[k][0] = __ldg(a.map.px + j);
+      wp[k][1] = __ldg(a.map.py + j);
+      wp[k][2] = __ldg(a.map.pz + j);
+      ts_rigid_f32(P, wp[k][0], wp[k][1], wp[k][2], xc, yc, zc);
       if (!(zc > a.z_near)) { vis = false; break; }
       ts_pinhole_f32(vw, xc, yc, zc, u[k], v[k]);
       z[k] = zc;
+      xv[k] = xc;
+      yv[k] = yc;
       o[k] = __ldg(a.map.op + j);
     }
     float area2 = 0.f, len[3] = {0.f, 0.f, 0.f}, per = 0.f, oF = 0.f;
@@ -141,6 +147,28 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
       const int tx0 = x0 / a.tile_w, tx1 = x1 / a.tile_w, ty0 = y0 / a.tile_h, ty1 = y1 / a.tile_h;
       a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
       a.count[idx] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+      if (a.nrm) {
+        // unit normal (v1 - v0) x (v2 - v0), turned towards the camera.  The edge vectors are
+        // taken in world space, where nearby float32 positions subtract almost exactly, and the
+        // unit normal is then rotated by R: camera-space edges would be differences of
+        // metre-sized coordinates and lose ~1e-5 of the normal for centimetre faces.
+        float e1[3], e2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          e1[c] = wp[1][c] - wp[0][c];
+          e2[c] = wp[2][c] - wp[0][c];
+        }
+        const float wx = e1[1] * e2[2] - e1[2] * e2[1], wy = e1[2] * e2[0] - e1[0] * e2[2];
+        const float wz = e1[0] * e2[1] - e1[1] * e2[0];
+        const float inv = rsqrtf(wx * wx + wy * wy + wz * wz);
+        float nc[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) nc[r] = (P.R[3 * r] * wx + P.R[3 * r + 1] * wy + P.R[3 * r + 2] * wz) * inv;
+        const float facing =
+            nc[0] * (xv[0] + xv[1] + xv[2]) + nc[1] * (yv[0] + yv[1] + yv[2]) + nc[2] * (z[0] + z[1] + z[2]);
+        const float sg = facing > 0.f ? -1.f : 1.f;
+        a.nrm[idx] = make_float4(sg * nc[0], sg * nc[1], sg * nc[2], 0.f);
+      }
     } else {
       a.rect[idx] = make_short4(-1, -1, -1, -1);
       a.count[idx] = 0u;
@@ -178,6 +206,7 @@ cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* 
   a.V = p->V;
   a.grad = w.grad;
   a.frec = w.frec;
+  a.nrm = w.nrm;
   a.rect = w.rect;
   a.zbits = w.zbits;
   a.count = w.count;

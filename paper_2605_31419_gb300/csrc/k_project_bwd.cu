@@ -6,6 +6,8 @@
 //   * edge functions E_i = s_i lambda_{i+2} with s_i = perimeter / |e_i| (Eq. 2-3 normalised
 //     by phi(s), the inradius): the same plane term plus the chain through the edge lengths;
 //   * o_F = (o_i + o_j + o_k) / 3 (Sec. 3.1): each vertex opacity gets a third;
+//   * with TS_FLAG_NORMALS, the face normal of the normal map (Eq. 12) through the cross product
+//     of the camera-space edge vectors;
 //   * the pinhole (Eq. 1) to camera space, R^T to world space, and the left-perturbation pose
 //     Jacobian [I, -[v_C]x] (Eq. 7): dL/dtau += [g_C ; v_C x g_C].
 //
@@ -33,6 +35,7 @@ struct PBArgs {
   long long M, VM;
   const uint32_t* count;
   float* grad;
+  const float4* nrm;  // camera-space face normals (TS_FLAG_NORMALS), else null
   const TsDevHeader* hdr;
   float* dst[7];  // gpx, gpy, gpz, gcr, gcg, gcb, gop
   float* part;
@@ -130,14 +133,43 @@ __device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) 
     gu[j1] += cx; gv[j1] += cy;
     gu[j] -= cx; gv[j] -= cy;
   }
+  // normal map (Eq. 12): dL/dn_F from words 23, 30, 31 through n = s u / |u|, u = e1 x e2 with
+  // e1 = v1 - v0, e2 = v2 - v0 in camera space and s = +-1 the camera-facing turn of the forward:
+  // dL/du = s (g - n (n . g)) / |u|, dL/de1 = e2 x dL/du, dL/de2 = dL/du x e1
+  float ng[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  if (a.nrm) {
+    const float gn[3] = {G[23], a.grad[slot * TS_GRAD_WORDS + 30], a.grad[slot * TS_GRAD_WORDS + 31]};
+    if (gn[0] != 0.f || gn[1] != 0.f || gn[2] != 0.f) {
+      const float4 nn = a.nrm[(long long)v * a.M + m];
+      const float e1[3] = {xc[1] - xc[0], yc[1] - yc[0], zc[1] - zc[0]};
+      const float e2[3] = {xc[2] - xc[0], yc[2] - yc[0], zc[2] - zc[0]};
+      const float uu[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+      const float il2 = rsqrtf(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+      const float sg = (nn.x * uu[0] + nn.y * uu[1] + nn.z * uu[2]) < 0.f ? -1.f : 1.f;
+      const float n[3] = {sg * uu[0] * il2, sg * uu[1] * il2, sg * uu[2] * il2};
+      const float ndg = n[0] * gn[0] + n[1] * gn[1] + n[2] * gn[2];
+      float du[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) du[r] = sg * il2 * (gn[r] - n[r] * ndg);
+      const float d1[3] = {e2[1] * du[2] - e2[2] * du[1], e2[2] * du[0] - e2[0] * du[2], e2[0] * du[1] - e2[1] * du[0]};
+      const float d2[3] = {du[1] * e1[2] - du[2] * e1[1], du[2] * e1[0] - du[0] * e1[2], du[0] * e1[1] - du[1] * e1[0]};
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        ng[1][r] = d1[r];
+        ng[2][r] = d2[r];
+        ng[0][r] = -(d1[r] + d2[r]);
+      }
+    }
+  }
   float out[9];
   float tau[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float iz = 1.0f / zc[k];
-    const float gx = gu[k] * vw.fx * iz;
-    const float gy = gv[k] * vw.fy * iz;
-    const float gz = -(gx * xc[k] + gy * yc[k]) * iz + G[G_Z + k];  // pinhole + interpolated depth
+    const float gxp = gu[k] * vw.fx * iz;
+    const float gyp = gv[k] * vw.fy * iz;
+    const float gz = -(gxp * xc[k] + gyp * yc[k]) * iz + G[G_Z + k] + ng[k][2];  // pinhole + depth + normal
+    const float gx = gxp + ng[k][0], gy = gyp + ng[k][1];
     out[3 * k + 0] = P.R[0] * gx + P.R[3] * gy + P.R[6] * gz;  // R^T g_C
     out[3 * k + 1] = P.R[1] * gx + P.R[4] * gy + P.R[7] * gz;
     out[3 * k + 2] = P.R[2] * gx + P.R[5] * gy + P.R[8] * gz;
@@ -316,6 +348,7 @@ cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_m
   a.VM = (long long)p->V * p->M;
   a.count = w.count;
   a.grad = w.grad;
+  a.nrm = w.nrm;
   a.hdr = w.hdr;
   a.dst[0] = g->gpx; a.dst[1] = g->gpy; a.dst[2] = g->gpz;
   a.dst[3] = g->gcr; a.dst[4] = g->gcg; a.dst[5] = g->gcb;

@@ -51,6 +51,9 @@ struct RenderArgs {
   int S;
   unsigned int* counter;
   uint16_t* cmask;
+  const float4* nrm;   // per (view, face) camera-space normal (TS_FLAG_NORMALS), else null
+  float* normal;       // normal map output (may be null)
+  const float* dN;     // gradient w.r.t. the normal map (may be null)
   TsDevHeader* hdr;
 };
 
@@ -106,13 +109,14 @@ __device__ __forceinline__ TileGeom<TW, TH> tile_geom(const RenderArgs& a, long 
 }
 
 // Warp 0 issues the bulk copies of stage `st` (records [st*S, st*S + cnt) of the tile's list)
-// into buffer `b`.
+// into buffer `b`; with NRM also each record's 16-byte normal (after both record buffers).
+template <bool NRM>
 __device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, uint64_t* bar, int b, int st,
-                                            uint32_t start, int n, const float4* vbase) {
+                                            uint32_t start, int n, const float4* vbase, const float4* nbase) {
   const int lane = threadIdx.x & 31;
   const int S = a.S;
   const int cnt = min(S, n - st * S);
-  if (lane == 0) ts_mbar_arrive_expect_tx(&bar[b], (uint32_t)cnt * 128u);
+  if (lane == 0) ts_mbar_arrive_expect_tx(&bar[b], (uint32_t)cnt * (NRM ? 144u : 128u));
   __syncwarp();
   for (int j = lane; j < cnt; j += 32) {
     uint32_t id = __ldg(a.ids + start + (uint32_t)(st * S + j));
@@ -121,6 +125,7 @@ __device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, 
       id = 0;
     }
     ts_bulk_g2s(smrec + ((size_t)b * S + j) * 8, vbase + (size_t)id * 8, 128u, &bar[b]);
+    if (NRM) ts_bulk_g2s(smrec + (size_t)2 * S * 8 + (size_t)b * S + j, nbase + id, 16u, &bar[b]);
   }
 }
 
@@ -182,7 +187,7 @@ __device__ __forceinline__ bool wait_stage(const RenderArgs& a, RenderSmem& sm, 
 }
 
 // Forward of one tile; seq counts the stages this CTA has waited for so far (mbarrier phases).
-template <int TW, int TH>
+template <int TW, int TH, bool NRM>
 __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
                                          int& seq) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
@@ -190,6 +195,7 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
   const uint2 rg = a.ranges[tile];
   const int n = (int)(rg.y - rg.x);
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+  float N0 = 0.f, N1 = 0.f, N2 = 0.f;
   int nl = 0;
   bool done = !g.inimg;
   unsigned contrib = 0;
@@ -198,17 +204,19 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
     const int S = a.S;
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
-    if (warp == 0) issue_stage(a, smrec, sm.bar, seq & 1, 0, rg.x, n, vbase);
+    const float4* nbase = NRM ? a.nrm + (size_t)g.view * (size_t)a.M : nullptr;
+    if (warp == 0) issue_stage<NRM>(a, smrec, sm.bar, seq & 1, 0, rg.x, n, vbase, nbase);
     for (int st = 0; st < nst; ++st) {
       const int b = seq & 1;
       const int cnt = min(S, n - st * S);
       if (!wait_stage(a, sm, seq)) { ok = false; break; }
       ++seq;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
+      const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
       stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
       for (int j = threadIdx.x; j < cnt; j += TW * TH) sm.cm[b][j] = 0u;
       __syncthreads();
-      if (warp == 0 && st + 1 < nst) issue_stage(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase);
+      if (warp == 0 && st + 1 < nst) issue_stage<NRM>(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase, nbase);
       for (int q = 0; q * 32 < cnt; ++q) {
         const int jq = q * 32 + lane;
         unsigned bits = __ballot_sync(FULL, jq < cnt && ((sm.smask[b][min(jq, cnt - 1)] >> warp) & 1u));
@@ -234,6 +242,12 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
                   C1 += w * (l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1]);
                   C2 += w * (l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2]);
                   D += w * (l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2]);
+                  if (NRM) {
+                    const float4 nn = nb[j];
+                    N0 += w * nn.x;
+                    N1 += w * nn.y;
+                    N2 += w * nn.z;
+                  }
                   T = Tn;
                   nl = st * S + j + 1;
                   ++contrib;
@@ -270,19 +284,26 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
     }
     if (a.depth) a.depth[o] = D;
     if (a.alpha) a.alpha[o] = 1.f - T;
+    if (NRM && a.normal) {
+      float* q = a.normal + 3 * g.vw.pix_off + pi;
+      q[0] = N0;
+      q[HW] = N1;
+      q[2 * HW] = N2;
+    }
     a.tfin[o] = T;
     a.nlast[o] = nl;
   }
   return ok;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool NRM>
 __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
                                          int& seq) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint2 rg = a.ranges[tile];
   float T = 0.f, Sacc = 0.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
+  float gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
   int nl = 0;
   if (g.inimg) {
     const long long HW = (long long)g.vw.W * g.vw.H;
@@ -296,6 +317,12 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
     gC2 = dc[2 * HW];
     gD = a.dD ? a.dD[o] : 0.f;
     gA = a.dA ? a.dA[o] : 0.f;
+    if (NRM && a.dN) {
+      const float* dn = a.dN + 3 * g.vw.pix_off + pi;
+      gN0 = dn[0];
+      gN1 = dn[HW];
+      gN2 = dn[2 * HW];
+    }
     Sacc = T * (gC0 * a.bg0 + gC1 * a.bg1 + gC2 * a.bg2);
   }
   if (threadIdx.x == 0) sm.nmax = 0;
@@ -314,7 +341,8 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
     const int S = a.S;
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
-    if (warp == 0) issue_stage(a, smrec, sm.bar, seq & 1, nst - 1, rg.x, n, vbase);
+    const float4* nbase = NRM ? a.nrm + (size_t)g.view * (size_t)a.M : nullptr;
+    if (warp == 0) issue_stage<NRM>(a, smrec, sm.bar, seq & 1, nst - 1, rg.x, n, vbase, nbase);
     const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
     const int q = lane & 3;
     const int widx = (hi16 ? 12 : 0) + (hi8 ? 6 : 0) + (hi4 ? 3 : 0) + q;
@@ -325,11 +353,12 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
       if (!wait_stage(a, sm, seq)) { ok = false; break; }
       ++seq;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
+      const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
       // the forward's record of which warps blended each face (positions below the tile's
       // largest list position after a contribution were all written by the forward)
       for (int j = threadIdx.x; j < cnt; j += TW * TH) sm.smask[b][j] = a.cmask[rg.x + st * S + j];
       __syncthreads();
-      if (warp == 0 && k + 1 < nst) issue_stage(a, smrec, sm.bar, b ^ 1, st - 1, rg.x, n, vbase);
+      if (warp == 0 && k + 1 < nst) issue_stage<NRM>(a, smrec, sm.bar, b ^ 1, st - 1, rg.x, n, vbase, nbase);
       // this warp visits only the stage's faces it blended in the forward (back to front)
       for (int qq = (cnt - 1) >> 5; qq >= 0; --qq) {
         const int jq = qq * 32 + lane;
@@ -352,9 +381,11 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             }
           }
           if (!__any_sync(FULL, cb)) continue;
-          float v[24];
+          // per-face sums: words 0..22 (and with normals dL/dn_F in words 23, 30, 31)
+          constexpr int NVAL = NRM ? 32 : 24;
+          float v[NVAL];
 #pragma unroll
-          for (int i = 0; i < 24; ++i) v[i] = 0.f;
+          for (int i = 0; i < NVAL; ++i) v[i] = 0.f;
           if (cb) {
             const float oma = 1.f - al;  // >= 1 - alpha_max
             const float ro = ts_rcp_approx(oma);
@@ -365,7 +396,12 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             const float c1 = l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1];
             const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
             const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
-            const float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
+            float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
+            float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (NRM) {
+              nn = nb[j];
+              val += gN0 * nn.x + gN1 * nn.y + gN2 * nn.z;
+            }
             const float dal = val * Tn - Sacc * ro;
             Sacc += val * al * Tn;
             T = Tn;
@@ -376,6 +412,11 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             v[G_C + 6] = w2 * l0; v[G_C + 7] = w2 * l1; v[G_C + 8] = w2 * l2;
             v[G_Z + 0] = wz * l0; v[G_Z + 1] = wz * l1; v[G_Z + 2] = wz * l2;
             v[G_CNT] = 1.f;
+            if constexpr (NRM) {
+              v[23] = gN0 * w;
+              v[30] = gN1 * w;
+              v[31] = gN2 * w;
+            }
             const float oF = r[R_OF];
             if (!(oF * I > a.alpha_max)) {
               v[G_O] = dal * I;
@@ -388,6 +429,28 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
               v[G_E + 6] = e.arg == 2 ? d0 : 0.f; v[G_E + 7] = e.arg == 2 ? d1 : 0.f; v[G_E + 8] = e.arg == 2 ? d2 : 0.f;
             }
             ++contrib;
+          }
+          if constexpr (NRM) {
+            // reduce-scatter 32 -> 16 -> 8 -> 4 -> 2 -> 1: lane L ends with the sum of value L
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+              const bool hi = lane & o;
+#pragma unroll
+              for (int i = 0; i < o; ++i) {
+                const float send = hi ? v[i] : v[i + o];
+                const float keep = hi ? v[i + o] : v[i];
+                v[i] = keep + __shfl_xor_sync(FULL, send, o);
+              }
+            }
+            if (v[0] != 0.f) {
+              const uint32_t slot = __float_as_uint(r[R_SLOT]);
+              if ((long long)slot < a.VM) {
+                atomicAdd(a.grad + (size_t)slot * TS_GRAD_WORDS + lane, v[0]);
+              } else {
+                atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
+              }
+            }
+            continue;
           }
           // reduce-scatter: 24 -> 12 -> 6 -> 3 values per lane, then a butterfly over 4 lanes
 #pragma unroll
@@ -447,66 +510,73 @@ __device__ __forceinline__ long long next_tile(const RenderArgs& a, RenderSmem& 
   return sm.next_tile < a.n_tiles ? (long long)sm.next_tile : -1;
 }
 
-template <int TW, int TH, bool PERSIST>
+template <int TW, int TH, bool PERSIST, bool NRM>
 __global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ RenderSmem sm;
   init_bars(sm);
   int seq = 0;
   if (!PERSIST) {
-    fwd_tile<TW, TH>(a, blockIdx.x, smrec, sm, seq);
+    fwd_tile<TW, TH, NRM>(a, blockIdx.x, smrec, sm, seq);
     return;
   }
   for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    if (!fwd_tile<TW, TH>(a, t, smrec, sm, seq)) return;
+    if (!fwd_tile<TW, TH, NRM>(a, t, smrec, sm, seq)) return;
 }
 
-template <int TW, int TH, bool PERSIST>
+template <int TW, int TH, bool PERSIST, bool NRM>
 __global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ RenderSmem sm;
   init_bars(sm);
   int seq = 0;
   if (!PERSIST) {
-    bwd_tile<TW, TH>(a, blockIdx.x, smrec, sm, seq);
+    bwd_tile<TW, TH, NRM>(a, blockIdx.x, smrec, sm, seq);
     return;
   }
   for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    if (!bwd_tile<TW, TH>(a, t, smrec, sm, seq)) return;
+    if (!bwd_tile<TW, TH, NRM>(a, t, smrec, sm, seq)) return;
 }
 
-template <int TW, int TH>
+// Dynamic shared memory: two stage buffers of S 128-byte records, then (with normals) two of S
+// 16-byte normals.
+template <int TW, int TH, bool NRM>
 cudaError_t launch_pair(bool fwd, bool persist, const RenderArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)2 * a.S * 128;
+  const size_t smem = (size_t)2 * a.S * (NRM ? 144 : 128);
   if (a.n_tiles == 0) return cudaSuccess;
   if (!persist) {
-    if (fwd) k_render_fwd<TW, TH, false><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
-    else k_render_bwd<TW, TH, false><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
+    if (fwd) k_render_fwd<TW, TH, false, NRM><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
+    else k_render_bwd<TW, TH, false, NRM><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
     return cudaGetLastError();
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<TW, TH, true>, TW * TH, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<TW, TH, true>, TW * TH, smem);
+  if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<TW, TH, true, NRM>, TW * TH, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<TW, TH, true, NRM>, TW * TH, smem);
   const long long grid = std::max(1LL, std::min<long long>(a.n_tiles, (long long)sms * std::max(per_sm, 1)));
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  if (fwd) k_render_fwd<TW, TH, true><<<(unsigned)grid, TW * TH, smem, s>>>(a);
-  else k_render_bwd<TW, TH, true><<<(unsigned)grid, TW * TH, smem, s>>>(a);
+  if (fwd) k_render_fwd<TW, TH, true, NRM><<<(unsigned)grid, TW * TH, smem, s>>>(a);
+  else k_render_bwd<TW, TH, true, NRM><<<(unsigned)grid, TW * TH, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t dispatch(bool fwd, const TsPlanImpl* p, const RenderArgs& a, cudaStream_t s) {
+template <bool NRM>
+cudaError_t dispatch_tiles(bool fwd, const TsPlanImpl* p, const RenderArgs& a, cudaStream_t s) {
   const int tw = p->prm.tile_w, th = p->prm.tile_h;
   const bool persist = (p->prm.flags & TS_FLAG_PERSISTENT) != 0;
-  if (tw == 16 && th == 8) return launch_pair<16, 8>(fwd, persist, a, s);
-  if (tw == 16 && th == 16) return launch_pair<16, 16>(fwd, persist, a, s);
-  if (tw == 8 && th == 8) return launch_pair<8, 8>(fwd, persist, a, s);
-  if (tw == 32 && th == 8) return launch_pair<32, 8>(fwd, persist, a, s);
-  if (tw == 16 && th == 32) return launch_pair<16, 32>(fwd, persist, a, s);
-  if (tw == 32 && th == 16) return launch_pair<32, 16>(fwd, persist, a, s);
+  if (tw == 16 && th == 8) return launch_pair<16, 8, NRM>(fwd, persist, a, s);
+  if (tw == 16 && th == 16) return launch_pair<16, 16, NRM>(fwd, persist, a, s);
+  if (tw == 8 && th == 8) return launch_pair<8, 8, NRM>(fwd, persist, a, s);
+  if (tw == 32 && th == 8) return launch_pair<32, 8, NRM>(fwd, persist, a, s);
+  if (tw == 16 && th == 32) return launch_pair<16, 32, NRM>(fwd, persist, a, s);
+  if (tw == 32 && th == 16) return launch_pair<32, 16, NRM>(fwd, persist, a, s);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch(bool fwd, const TsPlanImpl* p, const RenderArgs& a, cudaStream_t s) {
+  return p->normals ? dispatch_tiles<true>(fwd, p, a, s) : dispatch_tiles<false>(fwd, p, a, s);
 }
 
 RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
@@ -535,25 +605,30 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.hdr = w.hdr;
   a.counter = &w.hdr->tile_counter;
   a.cmask = w.cmask;
+  a.nrm = w.nrm;
+  a.normal = nullptr;
+  a.dN = nullptr;
   return a;
 }
 
 }  // namespace
 
 cudaError_t ts_launch_render_fwd(const TsPlanImpl* p, const TsWs& w, float* color, float* depth, float* alpha,
-                                 cudaStream_t s) {
+                                 float* normal, cudaStream_t s) {
   RenderArgs a = base_args(p, w);
   a.color = color;
   a.depth = depth;
   a.alpha = alpha;
+  a.normal = normal;
   return dispatch(true, p, a, s);
 }
 
 cudaError_t ts_launch_render_bwd(const TsPlanImpl* p, const TsWs& w, const float* dC, const float* dD,
-                                 const float* dA, cudaStream_t s) {
+                                 const float* dA, const float* dN, cudaStream_t s) {
   RenderArgs a = base_args(p, w);
   a.dC = dC;
   a.dD = dD;
   a.dA = dA;
+  a.dN = dN;
   return dispatch(false, p, a, s);
 }

@@ -66,7 +66,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   if (prm->tris_per_stage != 32 && prm->tris_per_stage != 64 && prm->tris_per_stage != 128) return TS_ERR_INVALID_ARG;
   if (!(prm->sigma > 0.0f) || !(prm->alpha_max > 0.0f && prm->alpha_max < 1.0f) || !(prm->alpha_min >= 0.0f) ||
       !(prm->T_min >= 0.0f && prm->T_min < 1.0f) || !(prm->z_near > 0.0f) || !(prm->r_min >= 0.0f) ||
-      (prm->flags & ~TS_FLAG_PERSISTENT) != 0)
+      (prm->flags & ~(TS_FLAG_PERSISTENT | TS_FLAG_NORMALS)) != 0)
     return TS_ERR_INVALID_ARG;
   if (pair_capacity < 0) return TS_ERR_INVALID_ARG;
   memset(plan, 0, sizeof(ts_plan));
@@ -107,6 +107,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   for (int v = 0; v < n_views; ++v) max_hw = std::max<int64_t>(max_hw, (int64_t)p->views[v].W * p->views[v].H);
   p->n_loss_blocks = (max_hw + 2047) / 2048;
   p->n_pho_blocks = ts_pho_blocks(p->views, n_views);
+  p->normals = (prm->flags & TS_FLAG_NORMALS) != 0;
   // layout
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -135,6 +136,8 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_cmask = take((size_t)cap * 2);
   p->o_pho = take((size_t)n_views * p->n_pho_blocks * 3 * 4);
   p->o_equi = take((size_t)ts_equi_blocks(n_faces) * 4);
+  p->o_nrm = take(p->normals ? (size_t)VM * 16 : 0);
+  p->o_nloss = take((size_t)n_views * p->n_loss_blocks * 4);
   p->total = o;
   p->magic = TS_PLAN_MAGIC;
   return TS_OK;
@@ -211,25 +214,39 @@ ts_status ts_bin(const ts_plan* plan, void* ws, ts_stream stream) {
   return cuda_status(ts_launch_bin(p, ts_ws(p, ws), s));
 }
 
-ts_status ts_render_fwd(const ts_plan* plan, void* ws, float* color, float* depth, float* alpha, ts_stream stream) {
+ts_status ts_render_fwd_n(const ts_plan* plan, void* ws, float* color, float* depth, float* alpha, float* normal,
+                          ts_stream stream) {
   const TsPlanImpl* p = impl(plan);
   if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return TS_ERR_INVALID_ARG;
   if (color && ((void*)color == (void*)depth || (void*)color == (void*)alpha)) return TS_ERR_INVALID_ARG;
+  if (normal && (!p->normals || (void*)normal == (void*)color || (void*)normal == (void*)depth ||
+                 (void*)normal == (void*)alpha))
+    return TS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   StageTimer t(p, TS_STAGE_FWD, s);
-  return cuda_status(ts_launch_render_fwd(p, ts_ws(p, ws), color, depth, alpha, s));
+  return cuda_status(ts_launch_render_fwd(p, ts_ws(p, ws), color, depth, alpha, normal, s));
+}
+
+ts_status ts_render_fwd(const ts_plan* plan, void* ws, float* color, float* depth, float* alpha, ts_stream stream) {
+  return ts_render_fwd_n(plan, ws, color, depth, alpha, nullptr, stream);
 }
 
 ts_status ts_render_bwd(const ts_plan* plan, void* ws, const float* dC, const float* dD, const float* dA,
                         const ts_map_grad* grad, ts_stream stream) {
+  return ts_render_bwd_n(plan, ws, dC, dD, dA, nullptr, grad, stream);
+}
+
+ts_status ts_render_bwd_n(const ts_plan* plan, void* ws, const float* dC, const float* dD, const float* dA,
+                          const float* dN, const ts_map_grad* grad, ts_stream stream) {
   const TsPlanImpl* p = impl(plan);
   if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) || !dC) return TS_ERR_INVALID_ARG;
+  if (dN && !p->normals) return TS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   TsWs w = ts_ws(p, ws);
   cudaError_t e;
   {
     StageTimer t(p, TS_STAGE_BWD_RASTER, s);
-    e = ts_launch_render_bwd(p, w, dC, dD, dA, s);
+    e = ts_launch_render_bwd(p, w, dC, dD, dA, dN, s);
   }
   if (e != cudaSuccess) return TS_ERR_CUDA;
   StageTimer t(p, TS_STAGE_BWD_PROJECT, s);
@@ -267,6 +284,15 @@ ts_status ts_pho_loss(const ts_plan* plan, void* ws, const float* color, const f
   StageTimer t(p, TS_STAGE_LOSS, s);
   return cuda_status(ts_launch_pho_loss(p, ts_ws(p, ws), color, depth, tgt_color, tgt_depth, lambda_ssim, lambda_dep,
                                         loss, dC, dD, s));
+}
+
+ts_status ts_normal_loss(const ts_plan* plan, void* ws, const float* normal, const float* tgt_normal, float weight,
+                         float* loss, float* dN, ts_stream stream) {
+  const TsPlanImpl* p = impl(plan);
+  if (!p || !ws || !normal || !tgt_normal || !loss || !dN || !std::isfinite(weight)) return TS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  StageTimer t(p, TS_STAGE_LOSS, s);
+  return cuda_status(ts_launch_normal_loss(p, ts_ws(p, ws), normal, tgt_normal, weight, loss, dN, s));
 }
 
 ts_status ts_equilateral(const ts_plan* plan, const ts_map* map, void* ws, size_t ws_bytes, float weight, float* loss,

@@ -85,9 +85,11 @@ struct TsPlanImpl {
   int64_t n_tiles, n_pix;
   int32_t tile_bits, sort_passes;
   int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks, n_pho_blocks;
+  bool normals;  // TS_FLAG_NORMALS
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
-      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, o_equi, total;
+      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, o_equi, o_nrm, o_nloss,
+      total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
   TsView views[TS_MAX_VIEWS];
@@ -117,6 +119,8 @@ struct TsWs {
   float* loss;
   float* pho;  // per (view, 32 x 32 tile): L1, SSIM and depth partial sums of the photometric loss
   float* equi;  // per block of 256 faces: partial sums of the equilateral regulariser
+  float4* nrm;  // per (view, face): camera-space unit normal (TS_FLAG_NORMALS), else null
+  float* nloss;  // per (view, 2048-pixel block): partial sums of the normal loss
   uint16_t* cmask;  // per sorted pair: the warps of its tile that blended the face in the forward
 };
 
@@ -146,6 +150,8 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.loss = (float*)(b + p->o_loss);
   w.pho = (float*)(b + p->o_pho);
   w.equi = (float*)(b + p->o_equi);
+  w.nrm = p->normals ? (float4*)(b + p->o_nrm) : nullptr;
+  w.nloss = (float*)(b + p->o_nloss);
   w.cmask = (uint16_t*)(b + p->o_cmask);
   return w;
 }
@@ -157,10 +163,12 @@ cudaError_t ts_launch_setup(const TsPlanImpl* p, const TsWs& w, const ts_map* ma
                             cudaStream_t s);
 cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* map, cudaStream_t s);
 cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s);
+cudaError_t ts_launch_normal_loss(const TsPlanImpl* p, const TsWs& w, const float* normal, const float* tgt,
+                                  float weight, float* loss, float* dN, cudaStream_t s);
 cudaError_t ts_launch_render_fwd(const TsPlanImpl* p, const TsWs& w, float* color, float* depth, float* alpha,
-                                 cudaStream_t s);
+                                 float* normal, cudaStream_t s);
 cudaError_t ts_launch_render_bwd(const TsPlanImpl* p, const TsWs& w, const float* dC, const float* dD,
-                                 const float* dA, cudaStream_t s);
+                                 const float* dA, const float* dN, cudaStream_t s);
 cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_map_grad* g, cudaStream_t s);
 cudaError_t ts_launch_pose_reduce(const TsPlanImpl* p, const TsWs& w, float* dtau, cudaStream_t s);
 inline TsImageTable ts_image_table(const TsPlanImpl* p) {

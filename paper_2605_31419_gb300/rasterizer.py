@@ -75,6 +75,11 @@ class Rasterizer:
         self.loss_v = torch.empty(self.V, dtype=torch.float32, device=self.device)
         self.dC = torch.empty_like(self.color)
         self.dD = torch.empty_like(self.depth)
+        # the normal map of Eq. 12 and its loss gradient, with TS_FLAG_NORMALS
+        self.normals = bool(self.params.flags & B.TS_FLAG_NORMALS)
+        self.normal = torch.empty_like(self.color) if self.normals else None
+        self.dN = torch.empty_like(self.color) if self.normals else None
+        self.nloss_v = torch.empty(self.V, dtype=torch.float32, device=self.device) if self.normals else None
         self._map: Optional[Map] = None
         self._poses: Optional[torch.Tensor] = None
         self.generation = 0
@@ -91,9 +96,14 @@ class Rasterizer:
     def bin(self, stream=None):
         B.ts_bin(self.plan, self.ws, stream)
 
-    def render_fwd(self, stream=None, color=None, depth=None, alpha=None):
-        B.ts_render_fwd(self.plan, self.ws, self.color if color is None else color,
-                        self.depth if depth is None else depth, self.alpha if alpha is None else alpha, stream)
+    def render_fwd(self, stream=None, color=None, depth=None, alpha=None, normal=None):
+        c = self.color if color is None else color
+        d = self.depth if depth is None else depth
+        a = self.alpha if alpha is None else alpha
+        if self.normals:
+            B.ts_render_fwd_n(self.plan, self.ws, c, d, a, self.normal if normal is None else normal, stream)
+        else:
+            B.ts_render_fwd(self.plan, self.ws, c, d, a, stream)
 
     def forward(self, m: Map, poses: torch.Tensor, stream=None):
         """Project, bin and composite all views; returns (color [3P], depth [P], alpha [P]) views of
@@ -103,10 +113,14 @@ class Rasterizer:
         self.render_fwd(stream)
         return self.color, self.depth, self.alpha
 
-    def backward(self, dC, dD=None, dA=None, grad: Optional[Map] = None, stream=None):
-        """Adds dL/d(map) into ``grad`` (a Map of gradient tensors) and prepares the pose partials."""
+    def backward(self, dC, dD=None, dA=None, grad: Optional[Map] = None, stream=None, dN=None):
+        """Adds dL/d(map) into ``grad`` (a Map of gradient tensors) and prepares the pose partials.
+        dN: gradient w.r.t. the normal map (plans with TS_FLAG_NORMALS)."""
         g = B.make_grad(grad.pos, grad.col, grad.opa) if grad is not None else None
-        B.ts_render_bwd(self.plan, self.ws, dC, dD, dA, g, stream)
+        if dN is not None:
+            B.ts_render_bwd_n(self.plan, self.ws, dC, dD, dA, dN, g, stream)
+        else:
+            B.ts_render_bwd(self.plan, self.ws, dC, dD, dA, g, stream)
 
     def pose_grad(self, out=None, stream=None):
         out = self.dtau if out is None else out
@@ -124,6 +138,14 @@ class Rasterizer:
         B.ts_pho_loss(self.plan, self.ws, self.color, self.depth, tgt_color, tgt_depth, lambda_ssim, lambda_dep,
                       self.loss_v, self.dC, self.dD, stream)
         return self.loss_v, self.dC, self.dD
+
+    def normal_loss(self, tgt_normal, weight: float = 0.05, stream=None):
+        """Eq. 12 on the last forward's normal map against sensor normals tgt_normal [3P] (zero =
+        no normal): per-view loss [V] and its gradient (scaled by ``weight``, lambda_norm)."""
+        if not self.normals:
+            raise ValueError("the plan was made without TS_FLAG_NORMALS")
+        B.ts_normal_loss(self.plan, self.ws, self.normal, tgt_normal, weight, self.nloss_v, self.dN, stream)
+        return self.nloss_v, self.dN
 
     def equilateral(self, m: Map, weight: float = 1.2, grad: Optional[Map] = None, out=None, stream=None):
         """Eq. 14 on the map's faces: returns E (device [1]); adds weight * dE/dpos into grad.pos."""

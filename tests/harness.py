@@ -20,8 +20,9 @@ def params_pair(**kw):
     return p, o
 
 
-def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, lambda_dep=0.05, pair_capacity=0):
-    """Forward (and backward of the L1 loss, or of the given image gradients) on the GPU."""
+def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, dN=None, lambda_dep=0.05, pair_capacity=0):
+    """Forward (and backward of the L1 loss, or of the given image gradients) on the GPU.  With
+    TS_FLAG_NORMALS in p.flags the normal map is returned and dN (if given) joins the backward."""
     import torch
     import paper_2605_31419_gb300 as ts
     rast = ts.Rasterizer(scene.cams, scene.n_faces, p, pair_capacity=pair_capacity)
@@ -33,6 +34,8 @@ def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, lambda_dep=0.
     out["T_final"] = rast.debug("T_final").cpu().numpy().astype(np.float64)
     out["n_last"] = rast.debug("n_last").cpu().numpy()
     out["counters"] = rast.counters(raise_on_error=False)
+    if rast.normals:
+        out["normal"] = rast.normal.cpu().numpy().astype(np.float64)
     if backward:
         dev = lambda a: None if a is None else torch.as_tensor(np.asarray(a), dtype=torch.float32, device="cuda")  # noqa
         if scene.tgt_color:
@@ -47,7 +50,7 @@ def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, lambda_dep=0.
             # differ by ~1e-5 around C = Cbar it may flip, so parity of the backward uses one dC)
             gC, gD, gA = dev(dC), dev(dD), dev(dA)
         g = m.zeros_like()
-        rast.backward(gC, gD, gA, g)
+        rast.backward(gC, gD, gA, g, dN=dev(dN))
         dtau = rast.pose_grad()
         torch.cuda.synchronize()
         out["dpos"] = g.pos.cpu().numpy().T.astype(np.float64)
@@ -59,7 +62,7 @@ def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, lambda_dep=0.
     return out
 
 
-def oracle_run(o: Oracle, scene, po: Params, *, backward=True, dC=None, dD=None, dA=None, lambda_dep=0.05):
+def oracle_run(o: Oracle, scene, po: Params, *, backward=True, dC=None, dD=None, dA=None, dN=None, lambda_dep=0.05):
     sa = SceneArrays.of(scene)
     f = o.forward(sa, po)
     out = dict(f)
@@ -69,7 +72,7 @@ def oracle_run(o: Oracle, scene, po: Params, *, backward=True, dC=None, dD=None,
             lo = o.l1_loss(sa, f["color"], f["depth"], tc, td, lambda_dep)
             dC, dD = lo["dC"], lo["dD"]
             out["loss_v"] = lo["loss_v"]
-        out.update(o.backward(sa, po, dC, dD, dA))
+        out.update(o.backward(sa, po, dC, dD, dA, dN))
         out["dC_used"], out["dD_used"] = dC, dD
     return out
 
