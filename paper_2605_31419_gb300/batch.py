@@ -27,17 +27,31 @@ STAGE_SIZES = (32, 64, 128)
 class MultiViewStep:
     """Forward, loss and backward of all views of ``cams`` on ``m`` in one batched pass.
 
-    The loss is E_pho + lambda_dep E_dep (Eq. 8, 13): (1 - lambda_ssim) L1 + lambda_ssim D-SSIM on
-    colour, L1 on depth; lambda_ssim = 0 uses the plain L1 kernel."""
+    The loss is the mapping loss E_map of Eq. 15, term by term:
+      * E_pho + lambda_dep E_dep (Eq. 8, 13): (1 - lambda_ssim) L1 + lambda_ssim D-SSIM on colour
+        (lambda_ssim = 0 uses the plain L1 kernel), L1 on depth;
+      * lambda_norm E_norm (Eq. 12) when sensor normals ``tgt_normal`` ([3P] packed like colour,
+        zero where there is none) are given: the plan then renders the normal map
+        (TS_FLAG_NORMALS) and its gradient joins the backward;
+      * lambda_equi E_equi (Eq. 14) on the map's faces when lambda_equi > 0 (needs ``grad``).
+    Map gradients accumulate into ``grad``; per-view values are in ``losses()``."""
 
     def __init__(self, m: Map, cams, poses: torch.Tensor, tgt_color: torch.Tensor, tgt_depth: torch.Tensor,
                  params: Optional[B.TsRasterParams] = None, grad: Optional[Map] = None, lambda_dep: float = 0.05,
-                 pair_capacity: int = 0, want_pose: bool = True, lambda_ssim: float = 0.0):
+                 pair_capacity: int = 0, want_pose: bool = True, lambda_ssim: float = 0.0,
+                 tgt_normal: Optional[torch.Tensor] = None, lambda_norm: float = 0.05, lambda_equi: float = 0.0):
         self.map, self.poses = m, poses
-        self.tc, self.td = tgt_color, tgt_depth
+        self.tc, self.td, self.tn = tgt_color, tgt_depth, tgt_normal
+        if tgt_normal is not None:
+            params = B.TsRasterParams.from_buffer_copy(params) if params is not None else B.ts_default_params()
+            params.flags |= B.TS_FLAG_NORMALS
         self.rast = Rasterizer(cams, m.n_faces, params, pair_capacity=pair_capacity)
         self.grad = grad
         self.lambda_dep, self.lambda_ssim = float(lambda_dep), float(lambda_ssim)
+        self.lambda_norm, self.lambda_equi = float(lambda_norm), float(lambda_equi)
+        if self.lambda_equi > 0 and grad is None:
+            raise ValueError("the equilateral term needs map gradient buffers")
+        self.equi = torch.zeros(1, dtype=torch.float32, device=self.rast.ws.device)
         self.want_pose = want_pose
         self.graph: Optional[torch.cuda.CUDAGraph] = None
 
@@ -50,9 +64,24 @@ class MultiViewStep:
             r.pho_loss(self.tc, self.td, self.lambda_ssim, self.lambda_dep)
         else:
             r.l1_loss(self.tc, self.td, self.lambda_dep)
-        r.backward(r.dC, r.dD, None, self.grad)
+        dN = None
+        if self.tn is not None:
+            _, dN = r.normal_loss(self.tn, self.lambda_norm)
+        r.backward(r.dC, r.dD, None, self.grad, dN=dN)
+        if self.lambda_equi > 0:
+            r.equilateral(self.map, self.lambda_equi, self.grad, out=self.equi)
         if self.want_pose:
             r.pose_grad()
+
+    def losses(self) -> dict:
+        """Per-view E_pho + lambda_dep E_dep, per-view E_norm (if normals), and E_equi (if on)."""
+        r = self.rast
+        out = {"pho_dep": r.loss_v}
+        if self.tn is not None:
+            out["norm"] = r.nloss_v
+        if self.lambda_equi > 0:
+            out["equi"] = self.equi
+        return out
 
     def capture(self):
         s = torch.cuda.Stream()

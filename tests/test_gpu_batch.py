@@ -76,3 +76,44 @@ def test_autotune_picks_a_valid_shape(tmp_path, monkeypatch):
     assert best["ms"] == min(r["ms"] for r in res)
     again, res2 = ts.autotune(m, sc.cams, ts.poses_tensor(sc.poses), tc, td)
     assert again == best and res2 is None  # served from the cache
+
+
+def test_mapping_loss_step_composes_the_terms():
+    """MultiViewStep with all terms of E_map (Eq. 15: D-SSIM photometric, depth, normal against
+    sensor normals, equilateral) equals the same kernels called one by one."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    from ts_synth.scenes import sensor_normals
+    sc = _window()
+    m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa)
+    poses = ts.poses_tensor(sc.poses)
+    dev = lambda a: torch.as_tensor(np.asarray(a, np.float32), device="cuda")  # noqa: E731
+    tc = dev(np.concatenate([t.reshape(-1) for t in sc.tgt_color]))
+    td = dev(np.concatenate([t.reshape(-1) for t in sc.tgt_depth]))
+    tn = dev(sensor_normals(7, sc.cams))
+    g_full = m.zeros_like()
+    full = ts.MultiViewStep(m, sc.cams, poses, tc, td, None, g_full, lambda_ssim=0.2, tgt_normal=tn,
+                            lambda_norm=0.05, lambda_equi=1.2)
+    full.run(1)
+    g_man = m.zeros_like()
+    r = ts.Rasterizer(sc.cams, m.n_faces, ts.ts_default_params(flags=ts.TS_FLAG_NORMALS))
+    r.forward(m, poses)
+    r.pho_loss(tc, td, 0.2, 0.05)
+    _, dN = r.normal_loss(tn, 0.05)
+    r.backward(r.dC, r.dD, None, g_man, dN=dN)
+    e = r.equilateral(m, 1.2, g_man)
+    r.pose_grad()
+    torch.cuda.synchronize()
+    L = full.losses()
+    assert np.array_equal(L["pho_dep"].cpu().numpy(), r.loss_v.cpu().numpy())
+    assert np.array_equal(L["norm"].cpu().numpy(), r.nloss_v.cpu().numpy())
+    assert np.array_equal(L["equi"].cpu().numpy(), e.cpu().numpy())
+    assert np.all(L["norm"].cpu().numpy() > 0) and float(L["equi"].item()) > 0
+    for name in ("pos", "col", "opa"):
+        assert_grad(getattr(g_full, name).cpu().numpy(), getattr(g_man, name).cpu().numpy(), f"d{name}", rtol=1e-4)
+    assert np.allclose(full.rast.dtau.cpu().numpy(), r.dtau.cpu().numpy(), rtol=1e-4, atol=1e-6)
+    # the normal and equilateral terms move the position gradient
+    g_pho = m.zeros_like()
+    ts.MultiViewStep(m, sc.cams, poses, tc, td, None, g_pho, lambda_ssim=0.2).run(1)
+    torch.cuda.synchronize()
+    assert np.abs(g_pho.pos.cpu().numpy() - g_full.pos.cpu().numpy()).max() > 1e-3 * np.abs(g_full.pos.cpu().numpy()).max()

@@ -174,6 +174,22 @@ def loss_images(seed: int, cams: np.ndarray, shift: int = 2, noise: float = 0.05
     f = lambda xs: np.concatenate(xs).astype(np.float32)  # noqa: E731
     return f(Cs), f(Ds), f(tCs), f(tDs)
 
+
+def sensor_normals(seed: int, cams: np.ndarray, invalid: float = 0.1) -> np.ndarray:
+    """Packed per-view sensor normal maps [3][H][W] (float32, flat): unit vectors drawn uniformly on
+    the hemisphere facing the camera (negative z), with an ``invalid`` fraction of pixels set to
+    the zero vector (no normal)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in cams:
+        HW = int(c[4]) * int(c[5])
+        n = rng.normal(size=(3, HW))
+        n /= np.linalg.norm(n, axis=0)
+        n[2] = -np.abs(n[2])
+        n[:, rng.random(HW) < invalid] = 0.0
+        out.append(n.ravel())
+    return np.concatenate(out).astype(np.float32)
+
 # --------------------------------------------------------------------------
 # workloads
 # --------------------------------------------------------------------------
