@@ -146,6 +146,7 @@ class Oracle:
         L.oracle_l1_loss.restype = d
         L.oracle_pho_loss.argtypes = [vp, vp, vp, vp, vp, d, d, vp, vp, vp, vp, vp]
         L.oracle_pho_loss.restype = d
+        L.oracle_face_stats.argtypes = [vp, vp, vp, vp]
         L.oracle_equilateral.argtypes = [vp, vp]
         L.oracle_equilateral.restype = d
         L.oracle_window.argtypes = [vp, d, d, d, vp]
@@ -188,6 +189,15 @@ class Oracle:
         self.lib.oracle_forward(C.byref(sc), C.byref(p), _ptr(color), _ptr(depth), _ptr(alpha), _ptr(T), _ptr(n_last),
                                 _ptr(normal))
         return dict(color=color, depth=depth, alpha=alpha, T_final=T, n_last=n_last, normal=normal, pix_off=off)
+
+    def face_stats(self, sa: SceneArrays, prm: Params):
+        """Per (view, face): pixel coverage of the forward walk and projected area (Sec. 3.4)."""
+        VM = len(sa.cams) * sa.n_faces
+        cov = np.zeros(VM, np.uint32)
+        area = np.zeros(VM)
+        sc, p = sa.c(), prm.c()
+        self.lib.oracle_face_stats(C.byref(sc), C.byref(p), _ptr(cov), _ptr(area))
+        return dict(coverage=cov, area=area)
 
     def pixel_trace(self, sa: SceneArrays, prm: Params, view: int, x: int, y: int, cap: int = 4096):
         faces = np.empty(cap, np.int32)

@@ -66,6 +66,9 @@
 //      (triangles are two-sided, so the winding carries no orientation);
 //   R22 Eq. 12 sums 1 - N . Nbar over the pixels with a sensor normal (Nbar != 0), divided by
 //      HW like the depth term of R11; N is used as rendered (not renormalised);
+//   R23 Sec. 3.4's map statistics: a face's pixel coverage in a view counts the pixels at which
+//      it was blended (its alpha passed alpha_min before termination); its projected area is
+//      that of the projected triangle; a face is visible in a view when its coverage is > 0;
 //   R14 in FP32 mode the projection follows one fixed operation order with
 //      no fused multiply-add (build with -ffp-contract=off), so that culling,
 //      pixel boxes, tiles and depth keys are bit-identical to any other
@@ -689,6 +692,64 @@ int oracle_forward(const or_scene* sc, const or_params* p, double* color, double
         if (n_last) n_last[w.pix_off + pi] = (int32_t)nl;
         if (normal) for (int ch = 0; ch < 3; ++ch) normal[3 * w.pix_off + ch * HW + pi] = N[ch];
       }
+    }
+  }
+  return 0;
+}
+
+// Mapping-support statistics per (view, face) (Sec. 3.4, R23): coverage [V*M] = pixels at which
+// the face was blended in the forward walk; area [V*M] = projected area |D2| / 2 in pixels^2 of a
+// face that passed culling (0 otherwise), D2 = (u1 - u0)(v2 - v0) - (u2 - u0)(v1 - v0) in the
+// projection's precision (R14).  Either output may be NULL.
+int oracle_face_stats(const or_scene* sc, const or_params* p, uint32_t* coverage, double* area) {
+  Ctx c = make_ctx(sc, p);
+  Bins b = make_bins(c);
+  const int64_t M = sc->n_faces;
+  if (area)
+    for (int v = 0; v < sc->n_views; ++v)
+      for (int64_t m = 0; m < M; ++m) {
+        const Proj& pr = b.proj[(size_t)v * M + m];
+        double a = 0;
+        if (pr.visible) {
+          if (p->fp64) {
+            a = 0.5 * std::fabs((pr.u[1] - pr.u[0]) * (pr.v[2] - pr.v[0]) - (pr.u[2] - pr.u[0]) * (pr.v[1] - pr.v[0]));
+          } else {
+            const float u0 = (float)pr.u[0], u1 = (float)pr.u[1], u2 = (float)pr.u[2];
+            const float v0 = (float)pr.v[0], v1 = (float)pr.v[1], v2 = (float)pr.v[2];
+            float du1 = u1 - u0, dv1 = v1 - v0, du2 = u2 - u0, dv2 = v2 - v0;
+            float a1 = du1 * dv2, a2 = du2 * dv1;
+            float d2 = a1 - a2;
+#if ORACLE_MUTANT == 19
+            a = (double)std::fabs(d2);  // twice the area
+#else
+            a = 0.5 * (double)std::fabs(d2);
+#endif
+          }
+        }
+        area[(size_t)v * M + m] = a;
+      }
+  if (coverage) {
+    std::memset(coverage, 0, sizeof(uint32_t) * (size_t)sc->n_views * M);
+    for (int v = 0; v < sc->n_views; ++v) {
+      const View& w = c.views[v];
+      std::vector<Contrib> list;
+      for (int y = 0; y < w.H; ++y)
+        for (int x = 0; x < w.W; ++x) {
+          int64_t nl;
+          walk_pixel(c, b, v, x, y, &list, &nl);
+          for (const Contrib& k : list) coverage[(size_t)v * M + k.face] += 1;
+#if ORACLE_MUTANT == 20
+          {  // also counts faces whose window is positive but whose alpha was skipped
+            double px, py;
+            pixel_centre(x, y, &px, &py);
+            const int64_t tile = w.tile_off + (int64_t)(y / c.p.tile_h) * w.TX + (x / c.p.tile_w);
+            for (int64_t i = b.start[tile]; i < b.end[tile]; ++i) {
+              const Term t = eval_term(c, v, b.ids[i], b.proj[(size_t)v * M + b.ids[i]], px, py);
+              if (t.ratio > 0 && t.alpha < c.p.alpha_min) coverage[(size_t)v * M + b.ids[i]] += 1;
+            }
+          }
+#endif
+        }
     }
   }
   return 0;

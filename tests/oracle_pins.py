@@ -512,6 +512,45 @@ def pin_normal_loss(o: Oracle):
 
 
 # ---------------------------------------------------------------------------------------------
+# Map statistics (Sec. 3.4, R23): coverage by brute force, projected area in closed form
+# ---------------------------------------------------------------------------------------------
+def pin_face_stats(o: Oracle):
+    # one face of low opacity: its rim pixels have alpha < alpha_min and must not count
+    verts = [[-0.6, -0.5, 2.0], [0.7, -0.4, 2.0], [0.0, 0.6, 2.0]]
+    opas = [0.01, 0.012, 0.011]
+    sc = _single_face_scene(verts, [[0.5] * 3] * 3, opas, cam=(20.0, 20.0, 16.0, 16.0, 32, 32))
+    sa = SceneArrays.of(sc)
+    prm = Params()
+    st = o.face_stats(sa, prm)
+    pr = o.project(sa, prm)
+    uvz = pr["uvz"][0]
+    tri = [uvz[0], uvz[3], uvz[1], uvz[4], uvz[2], uvz[5]]
+    P = np.asarray(tri).reshape(3, 2)
+    lens = [np.hypot(*(P[(i + 1) % 3] - P[i])) for i in range(3)]
+    area2 = (P[1, 0] - P[0, 0]) * (P[2, 1] - P[0, 1]) - (P[2, 0] - P[0, 0]) * (P[1, 1] - P[0, 1])
+    r = abs(area2) / sum(lens)
+    oF = sa.opa.sum() / 3
+    inside = counted = 0
+    for y in range(32):
+        for x in range(32):
+            d = _dist_edges(tri, x + 0.5, y + 0.5)
+            if d.min() > 0:
+                inside += 1
+                if min(prm.alpha_max, oF * (d.min() / r) ** prm.sigma) >= prm.alpha_min:
+                    counted += 1
+    assert 0 < counted < inside
+    assert int(st["coverage"][0]) == counted
+    # projected area: a fronto-parallel face at depth z scales its world area by (f / z)^2
+    world = 0.5 * abs(np.cross(np.subtract(verts[1], verts[0]), np.subtract(verts[2], verts[0]))[2])
+    assert abs(st["area"][0] - world * (20.0 / 2.0) ** 2) < 1e-4 * st["area"][0]
+    # a culled face (behind the camera) has no area and no coverage
+    behind = _single_face_scene([[0, 0, -1], [1, 0, -1], [0, 1, -1]], [[0.5] * 3] * 3, [1, 1, 1],
+                                cam=(20.0, 20.0, 16.0, 16.0, 32, 32))
+    st2 = o.face_stats(SceneArrays.of(behind), prm)
+    assert st2["area"][0] == 0 and st2["coverage"][0] == 0
+
+
+# ---------------------------------------------------------------------------------------------
 # Equilateral regulariser (Eq. 14, R19): closed forms, invariances, finite differences
 # ---------------------------------------------------------------------------------------------
 def _soup(tris, seed=0):
@@ -637,5 +676,6 @@ def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
 ALL_PINS = [pin_window_closed_form, pin_barycentric, pin_projection, pin_single_triangle, pin_coverage_bruteforce,
             pin_fronto_parallel_depth, pin_transmittance_product, pin_termination_stack, pin_binning_bruteforce,
             pin_sort_ties, pin_l1_loss, pin_ssim_scipy, pin_ssim_closed_forms, pin_pho_fd,
-            pin_normal_closed_forms, pin_normal_loss, pin_equilateral_closed_forms, pin_equilateral_invariance_and_fd,
+            pin_normal_closed_forms, pin_normal_loss, pin_face_stats, pin_equilateral_closed_forms,
+            pin_equilateral_invariance_and_fd,
             pin_se3_exp, pin_fd_gradients]

@@ -9,14 +9,15 @@ off-by-one tile box, a wrong loss normalisation; in the D-SSIM term of Eq. 8 the
 constant used for the contrast term, a dropped factor 2 in d(x^2)/dx, and edge clamping instead
 of zero padding; and in the equilateral regulariser (Eq. 14) an angle measured between edges that
 leave different vertices; and for the rendered normal map (Eq. 12) a normal left as the winding
-gives it and a normal in world instead of camera space.
+gives it and a normal in world instead of camera space; and in the map statistics (Sec. 3.4) twice
+the projected area and a coverage that also counts skipped contributions.
 """
 import pytest
 
 import oracle_pins as P
 from oracle.oracle import Oracle
 
-MUTANTS = list(range(1, 19))
+MUTANTS = list(range(1, 21))
 
 
 @pytest.mark.parametrize("k", MUTANTS)
