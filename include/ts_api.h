@@ -89,6 +89,10 @@ typedef struct {
  * and the raster kernels stage it beside the face's record. */
 #define TS_FLAG_NORMALS 2
 
+/* ts_raster_params.flags: the forward also counts, per (view, face), the pixels at which it
+ * blended the face (4 bytes per (view, face) in the workspace), for ts_face_stats. */
+#define TS_FLAG_STATS 4
+
 /* The map (Sec. 3.1): N vertices with position, colour, opacity as structure-of-arrays float32
  * device buffers, and M faces.  faces = NULL selects triangle-soup mode (face m uses vertices
  * 3m, 3m+1, 3m+2; N = 3M); otherwise faces is device int32 [M][3].  The buffers must stay valid
@@ -191,6 +195,26 @@ ts_status ts_render_bwd(const ts_plan* plan, void* ws, const float* dC, const fl
  * normal and through alpha and T.  dN != NULL needs a plan with TS_FLAG_NORMALS. */
 ts_status ts_render_bwd_n(const ts_plan* plan, void* ws, const float* dC, const float* dD, const float* dA,
                           const float* dN, const ts_map_grad* grad, ts_stream stream);
+
+/* Map statistics of the last ts_project / ts_render_fwd (Sec. 3.4: densification by pixel
+ * coverage above theta_blur * H * W, pruning by projected area above epsilon_a, keyframing by
+ * triangle co-visibility), per (view, face) in view-major order [n_views][n_faces]:
+ *   coverage:  device uint32, pixels at which the forward blended the face (alpha >= alpha_min,
+ *              before termination); needs TS_FLAG_STATS;
+ *   area:      device float, projected area |D2| / 2 in pixels^2 of a face that passed culling,
+ *              else 0 (D2 formed from the record's vertices in the projection's operation order);
+ *   visible:   device uint32 [n_views][ceil(n_faces / 32)], bit m of view v set when the face's
+ *              coverage is > 0; needs TS_FLAG_STATS;
+ *   n_visible: device uint32 [n_views], the number of visible faces; needs TS_FLAG_STATS.
+ * Any output may be NULL.  Asking for a TS_FLAG_STATS output without the flag returns
+ * TS_ERR_INVALID_ARG.  Integer outputs are exact; all are deterministic. */
+ts_status ts_face_stats(const ts_plan* plan, void* ws, uint32_t* coverage, float* area, uint32_t* visible,
+                        uint32_t* n_visible, ts_stream stream);
+
+/* Triangle co-visibility between views (Sec. 3.4 keyframing): iou[i][j] = |S_i and S_j| /
+ * |S_i or S_j| of the visible-face sets written by ts_face_stats (device uint32
+ * [n_views][ceil(n_faces / 32)]); 0 when both are empty.  iou: device float [n_views][n_views]. */
+ts_status ts_covisibility(const ts_plan* plan, const uint32_t* visible, float* iou, ts_stream stream);
 
 /* Normal loss of Eq. 12 per view: loss_v = sum over pixels with a sensor normal (tgt_normal not
  * the zero vector) of (1 - N . Nbar) / (HW), N as rendered (not renormalised); dN = weight *

@@ -22,6 +22,7 @@ STATUS = {0: "TS_OK", 1: "TS_ERR_INVALID_ARG", 2: "TS_ERR_CUDA", 3: "TS_ERR_CAPA
 STAGES = ["project", "bin", "fwd", "bwd_raster", "bwd_project", "pose", "loss"]
 TS_FLAG_PERSISTENT = 1  # ts_raster_params.flags bits of include/ts_api.h
 TS_FLAG_NORMALS = 2
+TS_FLAG_STATS = 4
 DEBUG = dict(keys=0, ids=1, ranges=2, rect=3, zbits=4, count=5, T_final=6, n_last=7, records=8)
 
 
@@ -87,6 +88,8 @@ SIGNATURES = {
     "ts_render_fwd": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp]),
     "ts_render_fwd_n": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, _vp]),
     "ts_render_bwd_n": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.POINTER(TsMapGrad), _vp]),
+    "ts_face_stats": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "ts_covisibility": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
     "ts_normal_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, C.c_float, _vp, _vp, _vp]),
     "ts_render_bwd": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, C.POINTER(TsMapGrad), _vp]),
     "ts_pose_grad": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
@@ -245,6 +248,15 @@ def ts_render_bwd_n(plan, ws, dC, dD, dA, dN, grad: Optional[TsMapGrad], stream=
     g = grad if grad is not None else TsMapGrad()
     _check(lib().ts_render_bwd_n(C.byref(plan), _ptr(ws), _ptr(dC), _ptr(dD), _ptr(dA), _ptr(dN), C.byref(g),
                                  _stream(stream)), "ts_render_bwd_n")
+
+
+def ts_face_stats(plan, ws, coverage=None, area=None, visible=None, n_visible=None, stream=None):
+    _check(lib().ts_face_stats(C.byref(plan), _ptr(ws), _ptr(coverage), _ptr(area), _ptr(visible), _ptr(n_visible),
+                               _stream(stream)), "ts_face_stats")
+
+
+def ts_covisibility(plan, visible, iou, stream=None):
+    _check(lib().ts_covisibility(C.byref(plan), _ptr(visible), _ptr(iou), _stream(stream)), "ts_covisibility")
 
 
 def ts_normal_loss(plan, ws, normal, tgt_normal, weight, loss, dN, stream=None):

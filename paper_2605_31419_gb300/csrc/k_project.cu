@@ -46,6 +46,7 @@ struct ProjArgs {
   int tile_w, tile_h;
   float4* frec;
   float4* nrm;  // camera-space unit normals (TS_FLAG_NORMALS), else null
+  uint32_t* cov;  // per (view, face) forward pixel coverage (TS_FLAG_STATS), else null
   float* grad;
   short4* rect;
   uint32_t* zbits;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
       const int tx0 = x0 / a.tile_w, tx1 = x1 / a.tile_w, ty0 = y0 / a.tile_h, ty1 = y1 / a.tile_h;
       a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
       a.count[idx] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+      if (a.cov) a.cov[idx] = 0u;
       if (a.nrm) {
         // unit normal (v1 - v0) x (v2 - v0), turned towards the camera.  The edge vectors are
         // taken in world space, where nearby float32 positions subtract almost exactly, and the
@@ -207,6 +209,7 @@ cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* 
   a.grad = w.grad;
   a.frec = w.frec;
   a.nrm = w.nrm;
+  a.cov = w.cov;
   a.rect = w.rect;
   a.zbits = w.zbits;
   a.count = w.count;

@@ -54,6 +54,7 @@ struct RenderArgs {
   const float4* nrm;   // per (view, face) camera-space normal (TS_FLAG_NORMALS), else null
   float* normal;       // normal map output (may be null)
   const float* dN;     // gradient w.r.t. the normal map (may be null)
+  uint32_t* cov;       // per (view, face) pixels blended by the forward (TS_FLAG_STATS), else null
   TsDevHeader* hdr;
 };
 
@@ -64,6 +65,7 @@ struct RenderSmem {
   uint64_t bar[2];
   uint32_t smask[2][128];
   uint32_t cm[2][128];  // forward: warps of the tile that blended each staged face
+  uint32_t cv[2][128];  // forward, TS_FLAG_STATS: pixels of the tile that blended each staged face
   int view;
   int nmax;
   int next_tile;
@@ -214,7 +216,10 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
       stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
-      for (int j = threadIdx.x; j < cnt; j += TW * TH) sm.cm[b][j] = 0u;
+      for (int j = threadIdx.x; j < cnt; j += TW * TH) {
+        sm.cm[b][j] = 0u;
+        sm.cv[b][j] = 0u;
+      }
       __syncthreads();
       if (warp == 0 && st + 1 < nst) issue_stage<NRM>(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase, nbase);
       for (int q = 0; q * 32 < cnt; ++q) {
@@ -257,11 +262,22 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
             }
           }
           // the backward revisits exactly the (warp, face) pairs that blended somewhere
-          if (__any_sync(FULL, blended) && lane == 0) atomicOr(&sm.cm[b][j], 1u << warp);
+          const unsigned bl = __ballot_sync(FULL, blended);
+          if (bl && lane == 0) {
+            atomicOr(&sm.cm[b][j], 1u << warp);
+            if (a.cov) atomicAdd(&sm.cv[b][j], (unsigned)__popc(bl));
+          }
         }
       }
       const int alive = __syncthreads_count(!done);
-      for (int j = threadIdx.x; j < cnt; j += TW * TH) a.cmask[rg.x + st * S + j] = (uint16_t)sm.cm[b][j];
+      for (int j = threadIdx.x; j < cnt; j += TW * TH) {
+        a.cmask[rg.x + st * S + j] = (uint16_t)sm.cm[b][j];
+        if (a.cov && sm.cv[b][j]) {  // face m of the record's slot m * V + view
+          const uint32_t slot = __float_as_uint(rb[j * TS_REC_WORDS + R_SLOT]);
+          const long long m = (long long)(slot / (uint32_t)a.V);
+          if (m < a.M) atomicAdd(a.cov + (long long)g.view * a.M + m, sm.cv[b][j]);
+        }
+      }
       if (alive == 0) {
         if (st + 1 < nst) {  // a prefetched stage is in flight: consume its phase before leaving
           if (!wait_stage(a, sm, seq)) { ok = false; break; }
@@ -606,6 +622,7 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.counter = &w.hdr->tile_counter;
   a.cmask = w.cmask;
   a.nrm = w.nrm;
+  a.cov = w.cov;
   a.normal = nullptr;
   a.dN = nullptr;
   return a;

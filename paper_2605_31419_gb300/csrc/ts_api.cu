@@ -66,7 +66,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   if (prm->tris_per_stage != 32 && prm->tris_per_stage != 64 && prm->tris_per_stage != 128) return TS_ERR_INVALID_ARG;
   if (!(prm->sigma > 0.0f) || !(prm->alpha_max > 0.0f && prm->alpha_max < 1.0f) || !(prm->alpha_min >= 0.0f) ||
       !(prm->T_min >= 0.0f && prm->T_min < 1.0f) || !(prm->z_near > 0.0f) || !(prm->r_min >= 0.0f) ||
-      (prm->flags & ~(TS_FLAG_PERSISTENT | TS_FLAG_NORMALS)) != 0)
+      (prm->flags & ~(TS_FLAG_PERSISTENT | TS_FLAG_NORMALS | TS_FLAG_STATS)) != 0)
     return TS_ERR_INVALID_ARG;
   if (pair_capacity < 0) return TS_ERR_INVALID_ARG;
   memset(plan, 0, sizeof(ts_plan));
@@ -108,6 +108,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->n_loss_blocks = (max_hw + 2047) / 2048;
   p->n_pho_blocks = ts_pho_blocks(p->views, n_views);
   p->normals = (prm->flags & TS_FLAG_NORMALS) != 0;
+  p->stats = (prm->flags & TS_FLAG_STATS) != 0;
   // layout
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -138,6 +139,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_equi = take((size_t)ts_equi_blocks(n_faces) * 4);
   p->o_nrm = take(p->normals ? (size_t)VM * 16 : 0);
   p->o_nloss = take((size_t)n_views * p->n_loss_blocks * 4);
+  p->o_cov = take(p->stats ? (size_t)VM * 4 : 0);
   p->total = o;
   p->magic = TS_PLAN_MAGIC;
   return TS_OK;
@@ -284,6 +286,20 @@ ts_status ts_pho_loss(const ts_plan* plan, void* ws, const float* color, const f
   StageTimer t(p, TS_STAGE_LOSS, s);
   return cuda_status(ts_launch_pho_loss(p, ts_ws(p, ws), color, depth, tgt_color, tgt_depth, lambda_ssim, lambda_dep,
                                         loss, dC, dD, s));
+}
+
+ts_status ts_face_stats(const ts_plan* plan, void* ws, uint32_t* coverage, float* area, uint32_t* visible,
+                        uint32_t* n_visible, ts_stream stream) {
+  const TsPlanImpl* p = impl(plan);
+  if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return TS_ERR_INVALID_ARG;
+  if ((coverage || visible || n_visible) && !p->stats) return TS_ERR_INVALID_ARG;
+  return cuda_status(ts_launch_face_stats(p, ts_ws(p, ws), coverage, area, visible, n_visible, (cudaStream_t)stream));
+}
+
+ts_status ts_covisibility(const ts_plan* plan, const uint32_t* visible, float* iou, ts_stream stream) {
+  const TsPlanImpl* p = impl(plan);
+  if (!p || !visible || !iou) return TS_ERR_INVALID_ARG;
+  return cuda_status(ts_launch_covisibility(p, visible, iou, (cudaStream_t)stream));
 }
 
 ts_status ts_normal_loss(const ts_plan* plan, void* ws, const float* normal, const float* tgt_normal, float weight,

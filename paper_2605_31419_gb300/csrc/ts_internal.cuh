@@ -86,10 +86,11 @@ struct TsPlanImpl {
   int32_t tile_bits, sort_passes;
   int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks, n_pho_blocks;
   bool normals;  // TS_FLAG_NORMALS
+  bool stats;    // TS_FLAG_STATS
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
       o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, o_equi, o_nrm, o_nloss,
-      total;
+      o_cov, total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
   TsView views[TS_MAX_VIEWS];
@@ -121,6 +122,7 @@ struct TsWs {
   float* equi;  // per block of 256 faces: partial sums of the equilateral regulariser
   float4* nrm;  // per (view, face): camera-space unit normal (TS_FLAG_NORMALS), else null
   float* nloss;  // per (view, 2048-pixel block): partial sums of the normal loss
+  uint32_t* cov;  // per (view, face): pixels blended by the forward (TS_FLAG_STATS), else null
   uint16_t* cmask;  // per sorted pair: the warps of its tile that blended the face in the forward
 };
 
@@ -152,6 +154,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.equi = (float*)(b + p->o_equi);
   w.nrm = p->normals ? (float4*)(b + p->o_nrm) : nullptr;
   w.nloss = (float*)(b + p->o_nloss);
+  w.cov = p->stats ? (uint32_t*)(b + p->o_cov) : nullptr;
   w.cmask = (uint16_t*)(b + p->o_cmask);
   return w;
 }
@@ -163,6 +166,9 @@ cudaError_t ts_launch_setup(const TsPlanImpl* p, const TsWs& w, const ts_map* ma
                             cudaStream_t s);
 cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* map, cudaStream_t s);
 cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s);
+cudaError_t ts_launch_face_stats(const TsPlanImpl* p, const TsWs& w, uint32_t* coverage, float* area,
+                                 uint32_t* visible, uint32_t* n_visible, cudaStream_t s);
+cudaError_t ts_launch_covisibility(const TsPlanImpl* p, const uint32_t* visible, float* iou, cudaStream_t s);
 cudaError_t ts_launch_normal_loss(const TsPlanImpl* p, const TsWs& w, const float* normal, const float* tgt,
                                   float weight, float* loss, float* dN, cudaStream_t s);
 cudaError_t ts_launch_render_fwd(const TsPlanImpl* p, const TsWs& w, float* color, float* depth, float* alpha,

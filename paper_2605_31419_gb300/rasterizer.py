@@ -139,6 +139,28 @@ class Rasterizer:
                       self.loss_v, self.dC, self.dD, stream)
         return self.loss_v, self.dC, self.dD
 
+    def face_stats(self, stream=None) -> dict:
+        """Map statistics of the last forward (Sec. 3.4), per (view, face) [V, M]: projected area
+        (pixels^2), and with TS_FLAG_STATS the pixel coverage, the visible-face bitsets
+        [V, ceil(M/32)] (int32 views of uint32 words) and their counts [V]."""
+        V, M = self.V, self.n_faces
+        dev = self.ws.device
+        out = {"area": torch.empty(V, M, dtype=torch.float32, device=dev)}
+        stats = bool(self.params.flags & B.TS_FLAG_STATS)
+        if stats:
+            out["coverage"] = torch.empty(V, M, dtype=torch.int32, device=dev)
+            out["visible"] = torch.empty(V, (M + 31) // 32, dtype=torch.int32, device=dev)
+            out["n_visible"] = torch.empty(V, dtype=torch.int32, device=dev)
+        B.ts_face_stats(self.plan, self.ws, out.get("coverage"), out["area"], out.get("visible"),
+                        out.get("n_visible"), stream)
+        return out
+
+    def covisibility(self, visible, stream=None) -> torch.Tensor:
+        """IoU [V, V] of the views' visible-face sets (bitsets from face_stats)."""
+        iou = torch.empty(self.V, self.V, dtype=torch.float32, device=self.ws.device)
+        B.ts_covisibility(self.plan, visible, iou, stream)
+        return iou
+
     def normal_loss(self, tgt_normal, weight: float = 0.05, stream=None):
         """Eq. 12 on the last forward's normal map against sensor normals tgt_normal [3P] (zero =
         no normal): per-view loss [V] and its gradient (scaled by ``weight``, lambda_norm)."""

@@ -62,7 +62,7 @@ def test_plan_layout_and_workspace(ts):
 
 @pytest.mark.parametrize("bad", [
     dict(tile_w=12), dict(tile_h=5), dict(tris_per_stage=48), dict(sigma=0.0), dict(alpha_max=1.0),
-    dict(T_min=1.0), dict(z_near=0.0), dict(flags=4)])
+    dict(T_min=1.0), dict(z_near=0.0), dict(flags=8)])
 def test_plan_rejects_bad_params(ts, bad):
     with pytest.raises(ts.TsError) as e:
         ts.ts_plan_init(np.array([[150, 150, 80, 60, 160, 120]]), 10, ts.ts_default_params(**bad))
@@ -98,6 +98,10 @@ def test_device_calls_reject_null_arguments(ts):
     assert L.ts_render_bwd_n(C.byref(plan), C.c_void_p(256), C.c_void_p(512), None, None, C.c_void_p(1024),
                              None, None) == 1
     assert L.ts_normal_loss(C.byref(plan), C.c_void_p(256), None, None, C.c_float(0.05), None, None, None) == 1
+    # coverage, visibility and counts need TS_FLAG_STATS; co-visibility needs its buffers
+    assert L.ts_face_stats(C.byref(plan), C.c_void_p(256), C.c_void_p(512), None, None, None, None) == 1
+    assert L.ts_face_stats(C.byref(plan), C.c_void_p(256), None, None, None, C.c_void_p(512), None) == 1
+    assert L.ts_covisibility(C.byref(plan), None, None, None) == 1
     # equilateral regulariser: null map or loss, a non-finite weight
     assert L.ts_equilateral(C.byref(plan), None, C.c_void_p(256), 1 << 30, C.c_float(1.0), C.c_void_p(256),
                             None, None) == 1
