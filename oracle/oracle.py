@@ -45,7 +45,7 @@ class _Params(C.Structure):
     _fields_ = [("sigma", C.c_double), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
                 ("T_min", C.c_double), ("z_near", C.c_double), ("r_min", C.c_double),
                 ("bg", C.c_double * 3), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("fp64", C.c_int32), ("n_threads", C.c_int32)]
+                ("fp64", C.c_int32), ("n_threads", C.c_int32), ("min_opacity", C.c_int32)]
 
 
 class _Scene(C.Structure):
@@ -68,6 +68,7 @@ class Params:
     tile_h: int = 16
     fp64: bool = False
     n_threads: int = 0
+    min_opacity: bool = False
 
     def c(self) -> _Params:
         p = _Params()
@@ -77,6 +78,7 @@ class Params:
         p.tile_w, p.tile_h = int(self.tile_w), int(self.tile_h)
         p.fp64 = 1 if self.fp64 else 0
         p.n_threads = int(self.n_threads)
+        p.min_opacity = 1 if self.min_opacity else 0
         return p
 
 

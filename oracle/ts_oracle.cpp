@@ -69,6 +69,8 @@
 //   R23 Sec. 3.4's map statistics: a face's pixel coverage in a view counts the pixels at which
 //      it was blended (its alpha passed alpha_min before termination); its projected area is
 //      that of the projected triangle; a face is visible in a view when its coverage is > 0;
+//   R24 the Mesh Splatting variant (Sec. 3.1 contrasts it) takes o_F = min of the three vertex
+//      opacities; its derivative goes to the first vertex (in face order) attaining the minimum;
 //   R14 in FP32 mode the projection follows one fixed operation order with
 //      no fused multiply-add (build with -ffp-contract=off), so that culling,
 //      pixel boxes, tiles and depth keys are bit-identical to any other
@@ -98,6 +100,7 @@ typedef struct {
   int32_t tile_w, tile_h;
   int32_t fp64;       // 0: projection in FP32 with the fixed op order (R14); 1: FP64 throughout
   int32_t n_threads;  // OpenMP threads (<= 0: library default)
+  int32_t min_opacity;  // 1: o_F = min of the vertex opacities (Mesh Splatting variant, R24)
 } or_params;
 
 typedef struct {
@@ -241,9 +244,14 @@ Proj project_f32(const Ctx& c, int view, int64_t m) {
   per = per + len[2];
   float r = std::fabs(area2) / per;
   if (!(r >= (float)c.p.r_min)) return pr;
-  float oF = o[0] + o[1];
-  oF = oF + o[2];
-  oF = oF / 3.0f;
+  float oF;
+  if (c.p.min_opacity) {
+    oF = std::min(o[0], std::min(o[1], o[2]));
+  } else {
+    oF = o[0] + o[1];
+    oF = oF + o[2];
+    oF = oF / 3.0f;
+  }
   if (oF < (float)c.p.alpha_min) return pr;
   float umin = std::min(u[0], std::min(u[1], u[2])), umax = std::max(u[0], std::max(u[1], u[2]));
   float vmin = std::min(v[0], std::min(v[1], v[2])), vmax = std::max(v[0], std::max(v[1], v[2]));
@@ -291,7 +299,7 @@ Proj project_f64(const Ctx& c, int view, int64_t m) {
     per += std::hypot(pr.u[j] - pr.u[i], pr.v[j] - pr.v[i]);
   }
   if (!(std::fabs(area2) / per >= c.p.r_min)) return pr;
-  double oF = (o[0] + o[1] + o[2]) / 3.0;
+  double oF = c.p.min_opacity ? std::min(o[0], std::min(o[1], o[2])) : (o[0] + o[1] + o[2]) / 3.0;
   if (oF < c.p.alpha_min) return pr;
   double umin = std::min({pr.u[0], pr.u[1], pr.u[2]}), umax = std::max({pr.u[0], pr.u[1], pr.u[2]});
   double vmin = std::min({pr.v[0], pr.v[1], pr.v[2]}), vmax = std::max({pr.v[0], pr.v[1], pr.v[2]});
@@ -369,12 +377,11 @@ S window_and_bary(const S qx[3], const S qy[3], double px, double py, double sig
   return I;
 }
 
-inline double face_opacity(double o0, double o1, double o2) {
+inline double face_opacity(double o0, double o1, double o2, bool min_variant) {
 #if ORACLE_MUTANT == 1
-  return std::min(o0, std::min(o1, o2));
-#else
-  return (o0 + o1 + o2) / 3.0;
+  min_variant = true;
 #endif
+  return min_variant ? std::min(o0, std::min(o1, o2)) : (o0 + o1 + o2) / 3.0;
 }
 
 // Per (pixel, face) quantities used by the compositing.
@@ -408,7 +415,7 @@ Term eval_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px, dou
   Term t;
   double o[3];
   for (int k = 0; k < 3; ++k) o[k] = sc->opa[vidx(sc, m, k)];
-  const double oF = face_opacity(o[0], o[1], o[2]);
+  const double oF = face_opacity(o[0], o[1], o[2], c.p.min_opacity != 0);
   t.I = I;
   t.ratio = ratio;
   t.clamped = oF * I > c.p.alpha_max;
@@ -588,9 +595,18 @@ DualTerm dual_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px,
   double ratio;
   Dual I = window_and_bary<Dual>(qx, qy, px, py, c.p.sigma, lam, &ratio);
 #if ORACLE_MUTANT == 1
-  Dual oF = min_(op[0], min_(op[1], op[2]));
+  const bool min_variant = true;
 #else
-  Dual oF = (op[0] + op[1] + op[2]) / Dual(3.0);
+  const bool min_variant = c.p.min_opacity != 0;
+#endif
+  // the minimum passes its derivative to the first vertex that attains it (R24)
+  Dual oF = min_variant ? min_(op[0], min_(op[1], op[2])) : (op[0] + op[1] + op[2]) / Dual(3.0);
+#if ORACLE_MUTANT == 21
+  if (min_variant) {  // the minimum's value with the mean's derivative
+    const double mv = oF.v;
+    oF = (op[0] + op[1] + op[2]) / Dual(3.0);
+    oF.v = mv;
+  }
 #endif
   DualTerm t;
   Dual a = oF * I;

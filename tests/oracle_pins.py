@@ -512,6 +512,43 @@ def pin_normal_loss(o: Oracle):
 
 
 # ---------------------------------------------------------------------------------------------
+# Min-opacity variant (Mesh Splatting, R24): alpha scales by min(o) / mean(o); FD of dopa
+# ---------------------------------------------------------------------------------------------
+def pin_min_opacity_variant(o: Oracle):
+    verts = [[-0.6, -0.5, 2.0], [0.7, -0.4, 2.3], [0.0, 0.6, 1.8]]
+    opas = [0.5, 0.2, 0.35]
+    sc = _single_face_scene(verts, [[0.5] * 3] * 3, opas, cam=(20.0, 20.0, 16.0, 16.0, 32, 32))
+    sa = SceneArrays.of(sc)
+    a_mean = o.forward(sa, Params(alpha_min=0.0))["alpha"]
+    a_min = o.forward(sa, Params(alpha_min=0.0, min_opacity=True))["alpha"]
+    cov = a_mean > 0
+    assert cov.sum() > 20
+    ratio = sa.opa.min() / sa.opa.mean()
+    assert np.abs(a_min[cov] - ratio * a_mean[cov]).max() < 1e-12
+    # finite differences of the opacity gradient: only the minimal vertex receives one
+    sc = tiny_scene(23, n_faces=5)
+    base = SceneArrays.of(sc)
+    prm = Params(alpha_min=0.0, T_min=0.0, fp64=True, min_opacity=True, sigma=1.0)
+    P = int(base.pix_offsets()[-1])
+    rng = np.random.default_rng(123)
+    wC, wD, wA = rng.normal(size=3 * P), rng.normal(size=P), rng.normal(size=P)
+    an = o.backward(base, prm, wC, wD, wA)
+    opa3 = base.opa.reshape(-1, 3)
+    is_min = np.zeros_like(opa3, bool)
+    is_min[np.arange(len(opa3)), np.argmin(opa3, axis=1)] = True
+    assert np.all(an["dopa"].reshape(-1, 3)[~is_min] == 0)
+    h = 1e-6
+    scale = np.abs(an["dopa"]).max() + 1e-12
+    for i in range(len(base.opa)):
+        xp, xm = base.opa.copy(), base.opa.copy()
+        xp[i] += h
+        xm[i] -= h
+        f = lambda x: _linear_functional(SceneArrays.of(sc, opa=x), prm, o, wC, wD, wA, np.zeros(3 * P))  # noqa
+        fd = (f(xp) - f(xm)) / (2 * h)
+        assert abs(fd - an["dopa"][i]) <= 2e-5 * scale + 1e-4 * abs(fd), (i, fd, an["dopa"][i])
+
+
+# ---------------------------------------------------------------------------------------------
 # Map statistics (Sec. 3.4, R23): coverage by brute force, projected area in closed form
 # ---------------------------------------------------------------------------------------------
 def pin_face_stats(o: Oracle):
@@ -676,6 +713,7 @@ def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
 ALL_PINS = [pin_window_closed_form, pin_barycentric, pin_projection, pin_single_triangle, pin_coverage_bruteforce,
             pin_fronto_parallel_depth, pin_transmittance_product, pin_termination_stack, pin_binning_bruteforce,
             pin_sort_ties, pin_l1_loss, pin_ssim_scipy, pin_ssim_closed_forms, pin_pho_fd,
-            pin_normal_closed_forms, pin_normal_loss, pin_face_stats, pin_equilateral_closed_forms,
+            pin_normal_closed_forms, pin_normal_loss, pin_min_opacity_variant, pin_face_stats,
+            pin_equilateral_closed_forms,
             pin_equilateral_invariance_and_fd,
             pin_se3_exp, pin_fd_gradients]

@@ -10,14 +10,15 @@ constant used for the contrast term, a dropped factor 2 in d(x^2)/dx, and edge c
 of zero padding; and in the equilateral regulariser (Eq. 14) an angle measured between edges that
 leave different vertices; and for the rendered normal map (Eq. 12) a normal left as the winding
 gives it and a normal in world instead of camera space; and in the map statistics (Sec. 3.4) twice
-the projected area and a coverage that also counts skipped contributions.
+the projected area and a coverage that also counts skipped contributions; and for the min-opacity
+variant the mean's derivative under the minimum's value.
 """
 import pytest
 
 import oracle_pins as P
 from oracle.oracle import Oracle
 
-MUTANTS = list(range(1, 21))
+MUTANTS = list(range(1, 22))
 
 
 @pytest.mark.parametrize("k", MUTANTS)
