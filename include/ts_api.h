@@ -93,6 +93,11 @@ typedef struct {
  * blended the face (4 bytes per (view, face) in the workspace), for ts_face_stats. */
 #define TS_FLAG_STATS 4
 
+/* ts_raster_params.flags: the Mesh Splatting face opacity o_F = min(o_i, o_j, o_k) instead of the
+ * paper's mean (Sec. 3.1); dL/do_F then goes to the first vertex, in face order, that attains the
+ * minimum. */
+#define TS_FLAG_MIN_OPACITY 8
+
 /* The map (Sec. 3.1): N vertices with position, colour, opacity as structure-of-arrays float32
  * device buffers, and M faces.  faces = NULL selects triangle-soup mode (face m uses vertices
  * 3m, 3m+1, 3m+2; N = 3M); otherwise faces is device int32 [M][3].  The buffers must stay valid

@@ -23,6 +23,7 @@ STAGES = ["project", "bin", "fwd", "bwd_raster", "bwd_project", "pose", "loss"]
 TS_FLAG_PERSISTENT = 1  # ts_raster_params.flags bits of include/ts_api.h
 TS_FLAG_NORMALS = 2
 TS_FLAG_STATS = 4
+TS_FLAG_MIN_OPACITY = 8
 DEBUG = dict(keys=0, ids=1, ranges=2, rect=3, zbits=4, count=5, T_final=6, n_last=7, records=8)
 
 

@@ -43,6 +43,7 @@ struct ProjArgs {
   long long VM;
   int V;
   float z_near, r_min, alpha_min;
+  bool min_opacity;
   int tile_w, tile_h;
   float4* frec;
   float4* nrm;  // camera-space unit normals (TS_FLAG_NORMALS), else null
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
       per = __fadd_rn(__fadd_rn(len[0], len[1]), len[2]);
       const float r = __fdiv_rn(fabsf(area2), per);
       if (!(r >= a.r_min)) vis = false;
-      oF = __fdiv_rn(__fadd_rn(__fadd_rn(o[0], o[1]), o[2]), 3.0f);
+      oF = a.min_opacity ? fminf(o[0], fminf(o[1], o[2])) : __fdiv_rn(__fadd_rn(__fadd_rn(o[0], o[1]), o[2]), 3.0f);
       if (oF < a.alpha_min) vis = false;
     }
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
@@ -203,6 +204,7 @@ cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* 
   a.z_near = p->prm.z_near;
   a.r_min = p->prm.r_min;
   a.alpha_min = p->prm.alpha_min;
+  a.min_opacity = p->min_opacity;
   a.tile_w = p->prm.tile_w;
   a.tile_h = p->prm.tile_h;
   a.V = p->V;

@@ -38,6 +38,7 @@ struct PBArgs {
   const float4* nrm;  // camera-space face normals (TS_FLAG_NORMALS), else null
   const TsDevHeader* hdr;
   float* dst[7];  // gpx, gpy, gpz, gcr, gcg, gcb, gop
+  bool min_opacity;  // o_F = min of the vertex opacities: dL/do_F to the first minimal vertex
   float* part;
   int nblocks;
 };
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
   const int c = lane / 3, k = lane - 3 * (lane / 3);
   const bool owner = lane < 21;
   const int word = c < 3 ? G_DPOS + 3 * k + c : (c < 6 ? G_C + 3 * (c - 3) + k : G_O);
-  const float scale = c == 6 ? (1.0f / 3.0f) : 1.0f;
+  const float mean_scale = c == 6 ? (1.0f / 3.0f) : 1.0f;
   float* dst = owner ? a.dst[c] : nullptr;
   const bool indexed = h->faces != nullptr;
   const long long stride = (long long)gridDim.x * PG_WARPS * PG_F;
@@ -292,6 +293,14 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
 #pragma unroll
     for (int f = 0; f < PG_F; ++f) {
       if (m0 + f < a.M && dst) {
+        float scale = mean_scale;
+        if (c == 6 && a.min_opacity) {  // the first vertex, in face order, attaining the minimum
+          const long long m = m0 + f;
+          const float o0 = __ldg(h->op + face_vertex(h, m, 0)), o1 = __ldg(h->op + face_vertex(h, m, 1));
+          const float o2 = __ldg(h->op + face_vertex(h, m, 2));
+          const int km = (o0 <= o1 && o0 <= o2) ? 0 : (o1 <= o2 ? 1 : 2);
+          scale = k == km ? 1.0f : 0.0f;
+        }
         if (indexed) atomicAdd(dst + j[f], s[f] * scale);
         else dst[j[f]] = old[f] + s[f] * scale;
       }
@@ -353,6 +362,7 @@ cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_m
   a.dst[0] = g->gpx; a.dst[1] = g->gpy; a.dst[2] = g->gpz;
   a.dst[3] = g->gcr; a.dst[4] = g->gcg; a.dst[5] = g->gcb;
   a.dst[6] = g->gop;
+  a.min_opacity = p->min_opacity;
   a.part = w.pose;
   a.nblocks = (int)p->n_pose_blocks;
   const long long chunks = (a.VM + 31) / 32;

@@ -66,7 +66,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   if (prm->tris_per_stage != 32 && prm->tris_per_stage != 64 && prm->tris_per_stage != 128) return TS_ERR_INVALID_ARG;
   if (!(prm->sigma > 0.0f) || !(prm->alpha_max > 0.0f && prm->alpha_max < 1.0f) || !(prm->alpha_min >= 0.0f) ||
       !(prm->T_min >= 0.0f && prm->T_min < 1.0f) || !(prm->z_near > 0.0f) || !(prm->r_min >= 0.0f) ||
-      (prm->flags & ~(TS_FLAG_PERSISTENT | TS_FLAG_NORMALS | TS_FLAG_STATS)) != 0)
+      (prm->flags & ~(TS_FLAG_PERSISTENT | TS_FLAG_NORMALS | TS_FLAG_STATS | TS_FLAG_MIN_OPACITY)) != 0)
     return TS_ERR_INVALID_ARG;
   if (pair_capacity < 0) return TS_ERR_INVALID_ARG;
   memset(plan, 0, sizeof(ts_plan));
@@ -109,6 +109,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->n_pho_blocks = ts_pho_blocks(p->views, n_views);
   p->normals = (prm->flags & TS_FLAG_NORMALS) != 0;
   p->stats = (prm->flags & TS_FLAG_STATS) != 0;
+  p->min_opacity = (prm->flags & TS_FLAG_MIN_OPACITY) != 0;
   // layout
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };

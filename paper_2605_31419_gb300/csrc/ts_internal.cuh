@@ -87,6 +87,7 @@ struct TsPlanImpl {
   int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks, n_pho_blocks;
   bool normals;  // TS_FLAG_NORMALS
   bool stats;    // TS_FLAG_STATS
+  bool min_opacity;  // TS_FLAG_MIN_OPACITY
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
       o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, o_equi, o_nrm, o_nloss,

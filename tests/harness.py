@@ -16,7 +16,8 @@ def params_pair(**kw):
     import paper_2605_31419_gb300 as ts
     p = ts.ts_default_params(**kw)
     o = Params(sigma=p.sigma, alpha_min=p.alpha_min, alpha_max=p.alpha_max, T_min=p.T_min, z_near=p.z_near,
-               r_min=p.r_min, bg=tuple(p.bg), tile_w=p.tile_w, tile_h=p.tile_h)
+               r_min=p.r_min, bg=tuple(p.bg), tile_w=p.tile_w, tile_h=p.tile_h,
+               min_opacity=bool(p.flags & ts.TS_FLAG_MIN_OPACITY))
     return p, o
 
 

@@ -62,7 +62,7 @@ def test_plan_layout_and_workspace(ts):
 
 @pytest.mark.parametrize("bad", [
     dict(tile_w=12), dict(tile_h=5), dict(tris_per_stage=48), dict(sigma=0.0), dict(alpha_max=1.0),
-    dict(T_min=1.0), dict(z_near=0.0), dict(flags=8)])
+    dict(T_min=1.0), dict(z_near=0.0), dict(flags=1 << 20)])
 def test_plan_rejects_bad_params(ts, bad):
     with pytest.raises(ts.TsError) as e:
         ts.ts_plan_init(np.array([[150, 150, 80, 60, 160, 120]]), 10, ts.ts_default_params(**bad))

@@ -1,0 +1,41 @@
+"""Raster variants switched by ts_raster_params.flags, on the GPU against the oracle through the C
+ABI, at the tolerances of tests/test_gpu_parity.py (images 1e-5 + 1e-4 |y|, bins bit-exact,
+gradients 1e-3 relative; the pose gradient condition-aware)."""
+import numpy as np
+import pytest
+
+from harness import assert_grad, assert_images, assert_pose_grad, gpu_run, oracle_run, params_pair
+from oracle.oracle import SceneArrays
+from ts_synth.scenes import random_triangles_scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _scenes():
+    from test_gpu_parity import _indexed, _ragged_room
+    return {"c1": lambda: random_triangles_scene(seed=1), "ragged_room": _ragged_room, "indexed": _indexed}
+
+
+@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed"])
+def test_min_opacity_variant(oracle, name):
+    import paper_2605_31419_gb300 as ts
+    sc = _scenes()[name]()
+    p, po = params_pair(flags=ts.TS_FLAG_MIN_OPACITY)
+    assert po.min_opacity
+    P = int(SceneArrays.of(sc).pix_offsets()[-1])
+    rng = np.random.default_rng(29)
+    dC = rng.normal(size=3 * P).astype(np.float32) * 1e-3
+    dD = rng.normal(size=P).astype(np.float32) * 1e-3
+    g = gpu_run(sc, p, dC=dC, dD=dD)
+    r = oracle_run(oracle, sc, po, dC=dC, dD=dD)
+    assert np.array_equal(g["n_last"], r["n_last"])
+    for k in ("color", "depth", "alpha"):
+        assert_images(g[k], r[k], k)
+    assert_grad(g["dpos"], r["dpos"], "dpos")
+    assert_grad(g["dcol"], r["dcol"], "dcol")
+    assert_grad(g["dopa"], r["dopa"], "dopa")
+    assert_pose_grad(g["dtau"], r["dtau"], r["dtau_abs"])
+    # only one vertex of each soup face receives an opacity gradient
+    if sc.faces is None:
+        nz = (np.abs(g["dopa"].reshape(-1, 3)) > 0).sum(1)
+        assert nz.max() <= 1
