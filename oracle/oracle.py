@@ -51,7 +51,7 @@ class _Params(C.Structure):
 class _Scene(C.Structure):
     _fields_ = [("pos", C.c_void_p), ("col", C.c_void_p), ("opa", C.c_void_p), ("faces", C.c_void_p),
                 ("n_vertices", C.c_int64), ("n_faces", C.c_int64), ("cams", C.c_void_p),
-                ("poses", C.c_void_p), ("n_views", C.c_int32)]
+                ("poses", C.c_void_p), ("n_views", C.c_int32), ("sigma_face", C.c_void_p)]
 
 
 @dataclass
@@ -91,15 +91,17 @@ class SceneArrays:
     faces: Optional[np.ndarray]
     cams: np.ndarray
     poses: np.ndarray
+    sigma: Optional[np.ndarray] = None
     keep: list = field(default_factory=list)
 
     @staticmethod
-    def of(scene, pos=None, col=None, opa=None, poses=None) -> "SceneArrays":
+    def of(scene, pos=None, col=None, opa=None, poses=None, sigma=None) -> "SceneArrays":
         f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
         faces = None if scene.faces is None else np.ascontiguousarray(scene.faces, dtype=np.int32)
+        sig = sigma if sigma is not None else getattr(scene, "sigma", None)
         return SceneArrays(f64(scene.pos if pos is None else pos), f64(scene.col if col is None else col),
                            f64(scene.opa if opa is None else opa), faces, f64(scene.cams),
-                           f64(scene.poses if poses is None else poses))
+                           f64(scene.poses if poses is None else poses), None if sig is None else f64(sig))
 
     def c(self) -> _Scene:
         s = _Scene()
@@ -109,6 +111,7 @@ class SceneArrays:
         s.n_faces = len(self.faces) if self.faces is not None else len(self.pos) // 3
         s.cams, s.poses = self.cams.ctypes.data, self.poses.ctypes.data
         s.n_views = len(self.cams)
+        s.sigma_face = None if self.sigma is None else self.sigma.ctypes.data
         return s
 
     @property
@@ -141,7 +144,7 @@ class Oracle:
         L.oracle_pixel_trace.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, i32, vp]
         L.oracle_pixel_trace.restype = i32
         L.oracle_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
-        L.oracle_backward_ex.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_backward_ex.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_normal_loss.argtypes = [vp, vp, vp, d, vp, vp]
         L.oracle_normal_loss.restype = d
         L.oracle_l1_loss.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, vp]
@@ -218,12 +221,13 @@ class Oracle:
         dopa = np.zeros(N)
         dtau = np.zeros((len(sa.cams), 6))
         dtau_abs = np.zeros((len(sa.cams), 6))
+        dsigma = np.zeros(sa.n_faces) if sa.sigma is not None else None
         f = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
         dC, dD, dA, dN = f(dC), f(dD), f(dA), f(dN)
         sc, p = sa.c(), prm.c()
         self.lib.oracle_backward_ex(C.byref(sc), C.byref(p), _ptr(dC), _ptr(dD), _ptr(dA), _ptr(dN), _ptr(dpos),
-                                    _ptr(dcol), _ptr(dopa), _ptr(dtau), _ptr(dtau_abs))
-        return dict(dpos=dpos, dcol=dcol, dopa=dopa, dtau=dtau, dtau_abs=dtau_abs)
+                                    _ptr(dcol), _ptr(dopa), _ptr(dtau), _ptr(dtau_abs), _ptr(dsigma))
+        return dict(dpos=dpos, dcol=dcol, dopa=dopa, dtau=dtau, dtau_abs=dtau_abs, dsigma=dsigma)
 
     def l1_loss(self, sa: SceneArrays, color, depth, tgt_color, tgt_depth, lambda_dep: float = 0.05):
         f = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731

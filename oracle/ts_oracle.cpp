@@ -71,6 +71,9 @@
 //      that of the projected triangle; a face is visible in a view when its coverage is > 0;
 //   R24 the Mesh Splatting variant (Sec. 3.1 contrasts it) takes o_F = min of the three vertex
 //      opacities; its derivative goes to the first vertex (in face order) attaining the minimum;
+//   R25 the learnable-sigma variant (Triangle Splatting, which Eq. 3 follows) gives each face its
+//      own exponent sigma_F in I = ReLU(phi / phi(s))^sigma_F, differentiated like the other
+//      face parameters; dI/dsigma_F = I ln(phi / phi(s));
 //   R14 in FP32 mode the projection follows one fixed operation order with
 //      no fused multiply-add (build with -ffp-contract=off), so that culling,
 //      pixel boxes, tiles and depth keys are bit-identical to any other
@@ -112,6 +115,7 @@ typedef struct {
   const double* cams;    // [V][6] fx, fy, cx, cy, W, H
   const double* poses;   // [V][12] row-major R, then t: v_C = R v_W + t
   int32_t n_views;
+  const double* sigma_face;  // [M] per-face window exponent (learnable-sigma variant, R25), or NULL
 } or_scene;
 
 }  // extern "C"
@@ -119,7 +123,7 @@ typedef struct {
 namespace {
 
 // ---------------------------------------------------------------- dual numbers
-constexpr int NT = 27;  // 3 vertices x (x, y, z, r, g, b, o) + 6 pose (rho, theta)
+constexpr int NT = 28;  // 3 vertices x (x, y, z, r, g, b, o) + 6 pose (rho, theta) + the face's sigma
 
 struct Dual {
   double v;
@@ -142,6 +146,18 @@ inline Dual pow_(const Dual& a, double e) {
   Dual r(std::pow(a.v, e));
   const double k = e * std::pow(a.v, e - 1.0);
   for (int i = 0; i < NT; ++i) r.d[i] = a.d[i] * k;
+  return r;
+}
+// a^e with a dual exponent: d(a^e) = e a^(e-1) da + a^e ln(a) de
+inline Dual pow_(const Dual& a, const Dual& e) {
+  Dual r(std::pow(a.v, e.v));
+  const double ka = e.v * std::pow(a.v, e.v - 1.0);
+#if ORACLE_MUTANT == 22
+  const double ke = r.v;  // the logarithm dropped
+#else
+  const double ke = r.v * std::log(a.v);
+#endif
+  for (int i = 0; i < NT; ++i) r.d[i] = a.d[i] * ka + e.d[i] * ke;
   return r;
 }
 inline double val(const Dual& a) { return a.v; }
@@ -339,7 +355,7 @@ Proj project(const Ctx& c, int view, int64_t m) {
 // (qx, qy) and its screen-space barycentrics lam.  Returns I; ratio gets
 // phi(p) / phi(s).
 template <class S>
-S window_and_bary(const S qx[3], const S qy[3], double px, double py, double sigma, S lam[3], double* ratio_out) {
+S window_and_bary(const S qx[3], const S qy[3], double px, double py, const S& sigma, S lam[3], double* ratio_out) {
   S nx[3], ny[3], d[3], len[3];
   for (int i = 0; i < 3; ++i) {
     const int j = (i + 1) % 3, k = (i + 2) % 3;
@@ -411,7 +427,8 @@ void face_normal(const S vc[3][3], S n[3]) {
 Term eval_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px, double py) {
   const or_scene* sc = c.sc;
   double lam[3], ratio;
-  double I = window_and_bary<double>(pr.u, pr.v, px, py, c.p.sigma, lam, &ratio);
+  const double sig = sc->sigma_face ? sc->sigma_face[m] : c.p.sigma;
+  double I = window_and_bary<double>(pr.u, pr.v, px, py, sig, lam, &ratio);
   Term t;
   double o[3];
   for (int k = 0; k < 3; ++k) o[k] = sc->opa[vidx(sc, m, k)];
@@ -593,7 +610,9 @@ DualTerm dual_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px,
   }
   Dual lam[3];
   double ratio;
-  Dual I = window_and_bary<Dual>(qx, qy, px, py, c.p.sigma, lam, &ratio);
+  Dual sig(sc->sigma_face ? sc->sigma_face[m] : c.p.sigma);
+  if (sc->sigma_face) sig.d[27] = 1.0;
+  Dual I = window_and_bary<Dual>(qx, qy, px, py, sig, lam, &ratio);
 #if ORACLE_MUTANT == 1
   const bool min_variant = true;
 #else
@@ -794,7 +813,8 @@ int oracle_pixel_trace(const or_scene* sc, const or_params* p, int view, int x, 
 // values of the per-(pixel, face) pose terms: the scale against which the cancelling sum dtau is
 // compared.
 int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC, const double* dD, const double* dA,
-                       const double* dN, double* dpos, double* dcol, double* dopa, double* dtau, double* dtau_abs) {
+                       const double* dN, double* dpos, double* dcol, double* dopa, double* dtau, double* dtau_abs,
+                       double* dsigma) {
   Ctx c = make_ctx(sc, p);
   Bins b = make_bins(c);
   const int nt = threads_of(p);
@@ -863,6 +883,10 @@ int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC,
               dopa[vi] += g[7 * kk + 6];
             }
           }
+          if (dsigma && sc->sigma_face) {
+#pragma omp atomic
+            dsigma[q.face] += g[27];
+          }
           for (int i = 0; i < 6; ++i) {
             tau_acc[i] += g[21 + i];
             tau_abs[i] += std::fabs(g[21 + i]);
@@ -878,7 +902,7 @@ int oracle_backward_ex(const or_scene* sc, const or_params* p, const double* dC,
 
 int oracle_backward(const or_scene* sc, const or_params* p, const double* dC, const double* dD, const double* dA,
                     double* dpos, double* dcol, double* dopa, double* dtau) {
-  return oracle_backward_ex(sc, p, dC, dD, dA, nullptr, dpos, dcol, dopa, dtau, nullptr);
+  return oracle_backward_ex(sc, p, dC, dD, dA, nullptr, dpos, dcol, dopa, dtau, nullptr, nullptr);
 }
 
 // L1 colour + depth loss (R11).  Returns the total over views; loss_v [V];

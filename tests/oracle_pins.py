@@ -549,6 +549,45 @@ def pin_min_opacity_variant(o: Oracle):
 
 
 # ---------------------------------------------------------------------------------------------
+# Learnable per-face sigma (R25): reduces to the global exponent; finite differences in sigma_F
+# ---------------------------------------------------------------------------------------------
+def pin_face_sigma_variant(o: Oracle):
+    sc = tiny_scene(24, n_faces=5)
+    M = sc.n_faces
+    prm = Params(alpha_min=0.0, T_min=0.0, fp64=True, sigma=0.5)
+    ref = o.forward(SceneArrays.of(sc), prm)
+    same = o.forward(SceneArrays.of(sc, sigma=np.full(M, 0.5)), prm)
+    for k in ("color", "depth", "alpha", "normal"):
+        assert np.array_equal(ref[k], same[k]), k
+    sig = np.random.default_rng(25).uniform(0.6, 1.5, size=M)
+    base = SceneArrays.of(sc, sigma=sig)
+    P = int(base.pix_offsets()[-1])
+    rng = np.random.default_rng(125)
+    wC, wD, wA, wN = rng.normal(size=3 * P), rng.normal(size=P), rng.normal(size=P), rng.normal(size=3 * P)
+    an = o.backward(base, prm, wC, wD, wA, wN)
+    h = 1e-6
+
+    def J(**kw):
+        return _linear_functional(SceneArrays.of(sc, sigma=kw.pop("sigma", sig), **kw), prm, o, wC, wD, wA, wN)
+
+    scale = np.abs(an["dsigma"]).max()
+    assert scale > 0
+    for i in range(M):
+        sp, sm = sig.copy(), sig.copy()
+        sp[i] += h
+        sm[i] -= h
+        fd = (J(sigma=sp) - J(sigma=sm)) / (2 * h)
+        assert abs(fd - an["dsigma"][i]) <= 2e-5 * scale + 1e-4 * abs(fd), (i, fd, an["dsigma"][i])
+    scale = np.abs(an["dpos"]).max()
+    for idx in list(np.ndindex(base.pos.shape))[::4]:
+        xp, xm = base.pos.copy(), base.pos.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (J(pos=xp) - J(pos=xm)) / (2 * h)
+        assert abs(fd - an["dpos"][idx]) <= 2e-5 * scale + 1e-4 * abs(fd), (idx, fd, an["dpos"][idx])
+
+
+# ---------------------------------------------------------------------------------------------
 # Map statistics (Sec. 3.4, R23): coverage by brute force, projected area in closed form
 # ---------------------------------------------------------------------------------------------
 def pin_face_stats(o: Oracle):
@@ -713,7 +752,8 @@ def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
 ALL_PINS = [pin_window_closed_form, pin_barycentric, pin_projection, pin_single_triangle, pin_coverage_bruteforce,
             pin_fronto_parallel_depth, pin_transmittance_product, pin_termination_stack, pin_binning_bruteforce,
             pin_sort_ties, pin_l1_loss, pin_ssim_scipy, pin_ssim_closed_forms, pin_pho_fd,
-            pin_normal_closed_forms, pin_normal_loss, pin_min_opacity_variant, pin_face_stats,
+            pin_normal_closed_forms, pin_normal_loss, pin_min_opacity_variant, pin_face_sigma_variant,
+            pin_face_stats,
             pin_equilateral_closed_forms,
             pin_equilateral_invariance_and_fd,
             pin_se3_exp, pin_fd_gradients]

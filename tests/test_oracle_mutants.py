@@ -11,14 +11,15 @@ of zero padding; and in the equilateral regulariser (Eq. 14) an angle measured b
 leave different vertices; and for the rendered normal map (Eq. 12) a normal left as the winding
 gives it and a normal in world instead of camera space; and in the map statistics (Sec. 3.4) twice
 the projected area and a coverage that also counts skipped contributions; and for the min-opacity
-variant the mean's derivative under the minimum's value.
+variant the mean's derivative under the minimum's value; and for the learnable-sigma variant a
+derivative in sigma without the logarithm.
 """
 import pytest
 
 import oracle_pins as P
 from oracle.oracle import Oracle
 
-MUTANTS = list(range(1, 22))
+MUTANTS = list(range(1, 23))
 
 
 @pytest.mark.parametrize("k", MUTANTS)

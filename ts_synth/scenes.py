@@ -32,6 +32,7 @@ class Scene:
     poses: np.ndarray
     tgt_color: List[np.ndarray] = field(default_factory=list)
     tgt_depth: List[np.ndarray] = field(default_factory=list)
+    sigma: Optional[np.ndarray] = None  # per-face window exponents (learnable-sigma variant), [M]
 
     @property
     def n_faces(self) -> int:
