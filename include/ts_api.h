@@ -98,6 +98,11 @@ typedef struct {
  * minimum. */
 #define TS_FLAG_MIN_OPACITY 8
 
+/* ts_raster_params.flags: each face has its own window exponent sigma_F (ts_map.sigma) in
+ * I = ReLU(phi / phi(s))^sigma_F, as in Triangle Splatting, and ts_render_bwd returns dL/dsigma_F
+ * (ts_map_grad.gsigma); the global sigma is then unused. */
+#define TS_FLAG_FACE_SIGMA 16
+
 /* The map (Sec. 3.1): N vertices with position, colour, opacity as structure-of-arrays float32
  * device buffers, and M faces.  faces = NULL selects triangle-soup mode (face m uses vertices
  * 3m, 3m+1, 3m+2; N = 3M); otherwise faces is device int32 [M][3].  The buffers must stay valid
@@ -108,6 +113,7 @@ typedef struct {
   const float *op;
   const int32_t* faces;
   int64_t n_vertices, n_faces;
+  const float* sigma;  /* [n_faces] window exponents, read with TS_FLAG_FACE_SIGMA (else may be NULL) */
 } ts_map;
 
 /* Gradient buffers (device float32, same layout as ts_map).  ts_render_bwd ADDS into them, so
@@ -117,6 +123,7 @@ typedef struct {
   float *gpx, *gpy, *gpz;
   float *gcr, *gcg, *gcb;
   float *gop;
+  float *gsigma;  /* [n_faces] dL/dsigma_F with TS_FLAG_FACE_SIGMA (may be NULL) */
 } ts_map_grad;
 
 /* Host-side plan: the views, the map size, the parameters and the workspace layout.  Filled by

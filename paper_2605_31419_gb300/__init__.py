@@ -10,7 +10,7 @@ from .binding import (  # noqa: F401
     ts_render_fwd, ts_render_bwd, ts_render_fwd_n, ts_render_bwd_n, ts_pose_grad,
     ts_l1_loss, ts_l1_loss_noalloc, ts_pho_loss, ts_normal_loss, ts_equilateral, ts_pose_apply, ts_pose_adam,
     ts_sync_status, ts_face_stats, ts_covisibility, TS_FLAG_PERSISTENT, TS_FLAG_NORMALS, TS_FLAG_STATS,
-    TS_FLAG_MIN_OPACITY,
+    TS_FLAG_MIN_OPACITY, TS_FLAG_FACE_SIGMA,
     ts_plan_layout,
     ts_debug_copy, ts_debug_timeout_probe, ts_set_stage_events, ts_status_string,
 )

@@ -24,6 +24,7 @@ TS_FLAG_PERSISTENT = 1  # ts_raster_params.flags bits of include/ts_api.h
 TS_FLAG_NORMALS = 2
 TS_FLAG_STATS = 4
 TS_FLAG_MIN_OPACITY = 8
+TS_FLAG_FACE_SIGMA = 16
 DEBUG = dict(keys=0, ids=1, ranges=2, rect=3, zbits=4, count=5, T_final=6, n_last=7, records=8)
 
 
@@ -56,12 +57,12 @@ class TsRasterParams(C.Structure):
 class TsMap(C.Structure):
     _fields_ = [("px", C.c_void_p), ("py", C.c_void_p), ("pz", C.c_void_p), ("cr", C.c_void_p), ("cg", C.c_void_p),
                 ("cb", C.c_void_p), ("op", C.c_void_p), ("faces", C.c_void_p), ("n_vertices", C.c_int64),
-                ("n_faces", C.c_int64)]
+                ("n_faces", C.c_int64), ("sigma", C.c_void_p)]
 
 
 class TsMapGrad(C.Structure):
     _fields_ = [("gpx", C.c_void_p), ("gpy", C.c_void_p), ("gpz", C.c_void_p), ("gcr", C.c_void_p),
-                ("gcg", C.c_void_p), ("gcb", C.c_void_p), ("gop", C.c_void_p)]
+                ("gcg", C.c_void_p), ("gcb", C.c_void_p), ("gop", C.c_void_p), ("gsigma", C.c_void_p)]
 
 
 class TsPlan(C.Structure):
@@ -197,19 +198,21 @@ def ts_status_string(s: int) -> str:
 
 
 # ----------------------------------------------------------------------------- device calls
-def make_map(pos, col, opa, faces=None) -> TsMap:
+def make_map(pos, col, opa, faces=None, sigma=None) -> TsMap:
     """TsMap over structure-of-arrays tensors: pos [3, N], col [3, N], opa [N] (float32, CUDA,
-    contiguous), faces int32 [M, 3] or None (soup)."""
+    contiguous), faces int32 [M, 3] or None (soup), sigma [M] per-face exponents or None."""
     n = pos.shape[1]
     m = faces.shape[0] if faces is not None else n // 3
     s = pos.stride(0) * pos.element_size()
     sc = col.stride(0) * col.element_size()
     b, c = pos.data_ptr(), col.data_ptr()
-    return TsMap(b, b + s, b + 2 * s, c, c + sc, c + 2 * sc, opa.data_ptr(), _ptr(faces), n, m)
+    return TsMap(b, b + s, b + 2 * s, c, c + sc, c + 2 * sc, opa.data_ptr(), _ptr(faces), n, m, _ptr(sigma))
 
 
-def make_grad(gpos=None, gcol=None, gopa=None) -> TsMapGrad:
+def make_grad(gpos=None, gcol=None, gopa=None, gsigma=None) -> TsMapGrad:
     g = TsMapGrad()
+    if gsigma is not None:
+        g.gsigma = gsigma.data_ptr()
     if gpos is not None:
         s = gpos.stride(0) * gpos.element_size()
         g.gpx, g.gpy, g.gpz = gpos.data_ptr(), gpos.data_ptr() + s, gpos.data_ptr() + 2 * s

@@ -46,7 +46,9 @@ struct ProjArgs {
   bool min_opacity;
   int tile_w, tile_h;
   float4* frec;
-  float4* nrm;  // camera-space unit normals (TS_FLAG_NORMALS), else null
+  float4* aux;  // camera-space unit normal (TS_FLAG_NORMALS) and sigma_F in .w (TS_FLAG_FACE_SIGMA)
+  bool normals;
+  const float* sigma;  // per-face window exponents (TS_FLAG_FACE_SIGMA), else null
   uint32_t* cov;  // per (view, face) forward pixel coverage (TS_FLAG_STATS), else null
   float* grad;
   short4* rect;
@@ -150,7 +152,8 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
       a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
       a.count[idx] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
       if (a.cov) a.cov[idx] = 0u;
-      if (a.nrm) {
+      float4 ax = make_float4(0.f, 0.f, 0.f, a.sigma ? __ldg(a.sigma + m) : 0.f);
+      if (a.normals) {
         // unit normal (v1 - v0) x (v2 - v0), turned towards the camera.  The edge vectors are
         // taken in world space, where nearby float32 positions subtract almost exactly, and the
         // unit normal is then rotated by R: camera-space edges would be differences of
@@ -170,8 +173,11 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
         const float facing =
             nc[0] * (xv[0] + xv[1] + xv[2]) + nc[1] * (yv[0] + yv[1] + yv[2]) + nc[2] * (z[0] + z[1] + z[2]);
         const float sg = facing > 0.f ? -1.f : 1.f;
-        a.nrm[idx] = make_float4(sg * nc[0], sg * nc[1], sg * nc[2], 0.f);
+        ax.x = sg * nc[0];
+        ax.y = sg * nc[1];
+        ax.z = sg * nc[2];
       }
+      if (a.aux) a.aux[idx] = ax;
     } else {
       a.rect[idx] = make_short4(-1, -1, -1, -1);
       a.count[idx] = 0u;
@@ -210,7 +216,9 @@ cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* 
   a.V = p->V;
   a.grad = w.grad;
   a.frec = w.frec;
-  a.nrm = w.nrm;
+  a.aux = w.aux;
+  a.normals = p->normals;
+  a.sigma = p->face_sigma ? map->sigma : nullptr;
   a.cov = w.cov;
   a.rect = w.rect;
   a.zbits = w.zbits;

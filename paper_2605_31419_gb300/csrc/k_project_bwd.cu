@@ -7,7 +7,8 @@
 //     by phi(s), the inradius): the same plane term plus the chain through the edge lengths;
 //   * o_F = (o_i + o_j + o_k) / 3 (Sec. 3.1): each vertex opacity gets a third;
 //   * with TS_FLAG_NORMALS, the face normal of the normal map (Eq. 12) through the cross product
-//     of the camera-space edge vectors;
+//     of the camera-space edge vectors; with TS_FLAG_FACE_SIGMA, dL/dsigma_F (a sum the raster
+//     backward already formed) is moved to word 23 and summed over views by the gather;
 //   * the pinhole (Eq. 1) to camera space, R^T to world space, and the left-perturbation pose
 //     Jacobian [I, -[v_C]x] (Eq. 7): dL/dtau += [g_C ; v_C x g_C].
 //
@@ -35,7 +36,9 @@ struct PBArgs {
   long long M, VM;
   const uint32_t* count;
   float* grad;
-  const float4* nrm;  // camera-space face normals (TS_FLAG_NORMALS), else null
+  const float4* aux;  // per (view, face) normal and sigma_F (TS_FLAG_NORMALS / TS_FLAG_FACE_SIGMA)
+  bool normals, face_sigma;
+  float* dst_sigma;  // dL/dsigma_F per face (TS_FLAG_FACE_SIGMA), may be null
   const TsDevHeader* hdr;
   float* dst[7];  // gpx, gpy, gpz, gcr, gcg, gcb, gop
   bool min_opacity;  // o_F = min of the vertex opacities: dL/do_F to the first minimal vertex
@@ -59,6 +62,7 @@ __device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) 
     const float4 q = gp[i];
     G[4 * i] = q.x; G[4 * i + 1] = q.y; G[4 * i + 2] = q.z; G[4 * i + 3] = q.w;
   }
+  const float gsig = a.face_sigma ? gp[6].x : 0.f;  // word 24, before the pose terms overwrite it
   const TsView vw = a.views[v];
   const ts_pose P = a.poses[v];
   // The projection, edge vectors, lengths and area are recomputed in the forward record's fixed
@@ -138,10 +142,10 @@ __device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) 
   // e1 = v1 - v0, e2 = v2 - v0 in camera space and s = +-1 the camera-facing turn of the forward:
   // dL/du = s (g - n (n . g)) / |u|, dL/de1 = e2 x dL/du, dL/de2 = dL/du x e1
   float ng[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  if (a.nrm) {
+  if (a.normals) {
     const float gn[3] = {G[23], a.grad[slot * TS_GRAD_WORDS + 30], a.grad[slot * TS_GRAD_WORDS + 31]};
     if (gn[0] != 0.f || gn[1] != 0.f || gn[2] != 0.f) {
-      const float4 nn = a.nrm[(long long)v * a.M + m];
+      const float4 nn = a.aux[(long long)v * a.M + m];
       const float e1[3] = {xc[1] - xc[0], yc[1] - yc[0], zc[1] - zc[0]};
       const float e2[3] = {xc[2] - xc[0], yc[2] - yc[0], zc[2] - zc[0]};
       const float uu[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -187,6 +191,7 @@ __device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) 
   gp[6] = make_float4(tau[0], tau[1], tau[2], tau[3]);
   gs[28] = tau[4];
   gs[29] = tau[5];
+  if (a.face_sigma) gs[23] = gsig;  // (the normal's word 23 is consumed above)
 }
 
 constexpr int PA_T = 256;
@@ -233,12 +238,14 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
   float* my = pv + (size_t)warp * a.V * 8;
   for (int i = lane; i < a.V * 8; i += 32) my[i] = 0.f;
   __syncwarp();
-  // lanes 0..20 each own one output word: array c (gpx..gop), vertex k
+  // lanes 0..20 each own one output word: array c (gpx..gop), vertex k; with per-face sigma,
+  // lane 21 owns the face's dL/dsigma_F (word 23 after the chain pass)
   const int c = lane / 3, k = lane - 3 * (lane / 3);
-  const bool owner = lane < 21;
-  const int word = c < 3 ? G_DPOS + 3 * k + c : (c < 6 ? G_C + 3 * (c - 3) + k : G_O);
+  const bool face_word = lane == 21;
+  const bool owner = lane < 21 || (face_word && a.face_sigma);
+  const int word = c < 3 ? G_DPOS + 3 * k + c : (c < 6 ? G_C + 3 * (c - 3) + k : (c == 6 ? G_O : 23));
   const float mean_scale = c == 6 ? (1.0f / 3.0f) : 1.0f;
-  float* dst = owner ? a.dst[c] : nullptr;
+  float* dst = owner ? (face_word ? a.dst_sigma : a.dst[c]) : nullptr;
   const bool indexed = h->faces != nullptr;
   const long long stride = (long long)gridDim.x * PG_WARPS * PG_F;
   for (long long m0 = ((long long)blockIdx.x * PG_WARPS + warp) * PG_F; m0 < a.M; m0 += stride) {
@@ -247,8 +254,8 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
 #pragma unroll
     for (int f = 0; f < PG_F; ++f) {
       const long long m = m0 + f;
-      j[f] = (m < a.M && owner) ? face_vertex(h, m, k) : 0;
-      old[f] = (m < a.M && dst && !indexed) ? dst[j[f]] : 0.f;  // issued early
+      j[f] = (m < a.M && owner) ? (face_word ? m : face_vertex(h, m, k)) : 0;
+      old[f] = (m < a.M && dst && (!indexed || face_word)) ? dst[j[f]] : 0.f;  // issued early
       s[f] = 0.f;
     }
     for (int r = 0; r * 32 < a.V; ++r) {
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
           const int km = (o0 <= o1 && o0 <= o2) ? 0 : (o1 <= o2 ? 1 : 2);
           scale = k == km ? 1.0f : 0.0f;
         }
-        if (indexed) atomicAdd(dst + j[f], s[f] * scale);
+        if (indexed && !face_word) atomicAdd(dst + j[f], s[f] * scale);
         else dst[j[f]] = old[f] + s[f] * scale;
       }
     }
@@ -357,7 +364,10 @@ cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_m
   a.VM = (long long)p->V * p->M;
   a.count = w.count;
   a.grad = w.grad;
-  a.nrm = w.nrm;
+  a.aux = w.aux;
+  a.normals = p->normals;
+  a.face_sigma = p->face_sigma;
+  a.dst_sigma = p->face_sigma ? g->gsigma : nullptr;
   a.hdr = w.hdr;
   a.dst[0] = g->gpx; a.dst[1] = g->gpy; a.dst[2] = g->gpz;
   a.dst[3] = g->gcr; a.dst[4] = g->gcg; a.dst[5] = g->gcb;

@@ -51,7 +51,9 @@ struct RenderArgs {
   int S;
   unsigned int* counter;
   uint16_t* cmask;
-  const float4* nrm;   // per (view, face) camera-space normal (TS_FLAG_NORMALS), else null
+  const float4* aux;   // per (view, face): camera-space normal and, in .w, sigma_F; else null
+  bool normals;        // TS_FLAG_NORMALS: composite the normal map
+  bool face_sigma;     // TS_FLAG_FACE_SIGMA: each face's own window exponent
   float* normal;       // normal map output (may be null)
   const float* dN;     // gradient w.r.t. the normal map (may be null)
   uint32_t* cov;       // per (view, face) pixels blended by the forward (TS_FLAG_STATS), else null
@@ -111,14 +113,15 @@ __device__ __forceinline__ TileGeom<TW, TH> tile_geom(const RenderArgs& a, long 
 }
 
 // Warp 0 issues the bulk copies of stage `st` (records [st*S, st*S + cnt) of the tile's list)
-// into buffer `b`; with NRM also each record's 16-byte normal (after both record buffers).
-template <bool NRM>
+// into buffer `b`; with AUX also each record's 16-byte side entry (normal, sigma_F), after both
+// record buffers.
+template <bool AUX>
 __device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, uint64_t* bar, int b, int st,
                                             uint32_t start, int n, const float4* vbase, const float4* nbase) {
   const int lane = threadIdx.x & 31;
   const int S = a.S;
   const int cnt = min(S, n - st * S);
-  if (lane == 0) ts_mbar_arrive_expect_tx(&bar[b], (uint32_t)cnt * (NRM ? 144u : 128u));
+  if (lane == 0) ts_mbar_arrive_expect_tx(&bar[b], (uint32_t)cnt * (AUX ? 144u : 128u));
   __syncwarp();
   for (int j = lane; j < cnt; j += 32) {
     uint32_t id = __ldg(a.ids + start + (uint32_t)(st * S + j));
@@ -127,7 +130,7 @@ __device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, 
       id = 0;
     }
     ts_bulk_g2s(smrec + ((size_t)b * S + j) * 8, vbase + (size_t)id * 8, 128u, &bar[b]);
-    if (NRM) ts_bulk_g2s(smrec + (size_t)2 * S * 8 + (size_t)b * S + j, nbase + id, 16u, &bar[b]);
+    if (AUX) ts_bulk_g2s(smrec + (size_t)2 * S * 8 + (size_t)b * S + j, nbase + id, 16u, &bar[b]);
   }
 }
 
@@ -189,7 +192,7 @@ __device__ __forceinline__ bool wait_stage(const RenderArgs& a, RenderSmem& sm, 
 }
 
 // Forward of one tile; seq counts the stages this CTA has waited for so far (mbarrier phases).
-template <int TW, int TH, bool NRM>
+template <int TW, int TH, bool AUX>
 __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
                                          int& seq) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
@@ -206,8 +209,8 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
     const int S = a.S;
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
-    const float4* nbase = NRM ? a.nrm + (size_t)g.view * (size_t)a.M : nullptr;
-    if (warp == 0) issue_stage<NRM>(a, smrec, sm.bar, seq & 1, 0, rg.x, n, vbase, nbase);
+    const float4* nbase = AUX ? a.aux + (size_t)g.view * (size_t)a.M : nullptr;
+    if (warp == 0) issue_stage<AUX>(a, smrec, sm.bar, seq & 1, 0, rg.x, n, vbase, nbase);
     for (int st = 0; st < nst; ++st) {
       const int b = seq & 1;
       const int cnt = min(S, n - st * S);
@@ -221,7 +224,7 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
         sm.cv[b][j] = 0u;
       }
       __syncthreads();
-      if (warp == 0 && st + 1 < nst) issue_stage<NRM>(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase, nbase);
+      if (warp == 0 && st + 1 < nst) issue_stage<AUX>(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase, nbase);
       for (int q = 0; q * 32 < cnt; ++q) {
         const int jq = q * 32 + lane;
         unsigned bits = __ballot_sync(FULL, jq < cnt && ((sm.smask[b][min(jq, cnt - 1)] >> warp) & 1u));
@@ -233,7 +236,8 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
             const float* r = rb + j * TS_REC_WORDS;
             const TsPix e = ts_eval_edges(r, g.px, g.py);
             if (e.m > 0.f) {
-              const float I = ts_window(e.m, a.sigma);
+              const float sig = (AUX && a.face_sigma) ? nb[j].w : a.sigma;
+              const float I = ts_window(e.m, sig);
               const float al = fminf(r[R_OF] * I, a.alpha_max);
               if (al >= a.alpha_min) {
                 const float Tn = T * (1.f - al);
@@ -247,7 +251,7 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
                   C1 += w * (l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1]);
                   C2 += w * (l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2]);
                   D += w * (l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2]);
-                  if (NRM) {
+                  if (AUX && a.normals) {
                     const float4 nn = nb[j];
                     N0 += w * nn.x;
                     N1 += w * nn.y;
@@ -300,7 +304,7 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
     }
     if (a.depth) a.depth[o] = D;
     if (a.alpha) a.alpha[o] = 1.f - T;
-    if (NRM && a.normal) {
+    if (AUX && a.normal) {
       float* q = a.normal + 3 * g.vw.pix_off + pi;
       q[0] = N0;
       q[HW] = N1;
@@ -312,7 +316,7 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
   return ok;
 }
 
-template <int TW, int TH, bool NRM>
+template <int TW, int TH, bool AUX>
 __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
                                          int& seq) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
@@ -333,7 +337,7 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
     gC2 = dc[2 * HW];
     gD = a.dD ? a.dD[o] : 0.f;
     gA = a.dA ? a.dA[o] : 0.f;
-    if (NRM && a.dN) {
+    if (AUX && a.dN) {
       const float* dn = a.dN + 3 * g.vw.pix_off + pi;
       gN0 = dn[0];
       gN1 = dn[HW];
@@ -357,8 +361,8 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
     const int S = a.S;
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
-    const float4* nbase = NRM ? a.nrm + (size_t)g.view * (size_t)a.M : nullptr;
-    if (warp == 0) issue_stage<NRM>(a, smrec, sm.bar, seq & 1, nst - 1, rg.x, n, vbase, nbase);
+    const float4* nbase = AUX ? a.aux + (size_t)g.view * (size_t)a.M : nullptr;
+    if (warp == 0) issue_stage<AUX>(a, smrec, sm.bar, seq & 1, nst - 1, rg.x, n, vbase, nbase);
     const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
     const int q = lane & 3;
     const int widx = (hi16 ? 12 : 0) + (hi8 ? 6 : 0) + (hi4 ? 3 : 0) + q;
@@ -374,7 +378,7 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
       // largest list position after a contribution were all written by the forward)
       for (int j = threadIdx.x; j < cnt; j += TW * TH) sm.smask[b][j] = a.cmask[rg.x + st * S + j];
       __syncthreads();
-      if (warp == 0 && k + 1 < nst) issue_stage<NRM>(a, smrec, sm.bar, b ^ 1, st - 1, rg.x, n, vbase, nbase);
+      if (warp == 0 && k + 1 < nst) issue_stage<AUX>(a, smrec, sm.bar, b ^ 1, st - 1, rg.x, n, vbase, nbase);
       // this warp visits only the stage's faces it blended in the forward (back to front)
       for (int qq = (cnt - 1) >> 5; qq >= 0; --qq) {
         const int jq = qq * 32 + lane;
@@ -388,17 +392,19 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
           bool cb = false;
           TsPix e;
           float I = 0.f, al = 0.f;
+          const float sig = (AUX && a.face_sigma) ? nb[j].w : a.sigma;
           if (pos < nl) {
             e = ts_eval_edges(r, g.px, g.py);
             if (e.m > 0.f) {
-              I = ts_window(e.m, a.sigma);
+              I = ts_window(e.m, sig);
               al = fminf(r[R_OF] * I, a.alpha_max);
               cb = al >= a.alpha_min;
             }
           }
           if (!__any_sync(FULL, cb)) continue;
-          // per-face sums: words 0..22 (and with normals dL/dn_F in words 23, 30, 31)
-          constexpr int NVAL = NRM ? 32 : 24;
+          // per-face sums: words 0..22, and with the side array dL/dn_F in words 23, 30, 31 and
+          // dL/dsigma_F in word 24 (the chain pass moves it to 23 before it writes the pose terms)
+          constexpr int NVAL = AUX ? 32 : 24;
           float v[NVAL];
 #pragma unroll
           for (int i = 0; i < NVAL; ++i) v[i] = 0.f;
@@ -414,7 +420,7 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
             float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
             float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (NRM) {
+            if (AUX && a.normals) {
               nn = nb[j];
               val += gN0 * nn.x + gN1 * nn.y + gN2 * nn.z;
             }
@@ -428,7 +434,7 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             v[G_C + 6] = w2 * l0; v[G_C + 7] = w2 * l1; v[G_C + 8] = w2 * l2;
             v[G_Z + 0] = wz * l0; v[G_Z + 1] = wz * l1; v[G_Z + 2] = wz * l2;
             v[G_CNT] = 1.f;
-            if constexpr (NRM) {
+            if constexpr (AUX) {
               v[23] = gN0 * w;
               v[30] = gN1 * w;
               v[31] = gN2 * w;
@@ -438,7 +444,10 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
               v[G_O] = dal * I;
               const float dI = dal * oF;
               // I >= alpha_min / o_F here, far from zero
-              const float dm = (a.sigma == 0.5f) ? dI * 0.5f * ts_rcp_approx(I) : dI * a.sigma * I / e.m;
+              const float dm = (sig == 0.5f) ? dI * 0.5f * ts_rcp_approx(I) : dI * sig * I / e.m;
+              if constexpr (AUX) {  // dL/dsigma_F = dL/dalpha o_F I ln(ratio)
+                if (a.face_sigma) v[24] = dI * I * logf(e.m);
+              }
               const float d0 = dm * l0, d1 = dm * l1, d2 = dm * l2;
               v[G_E + 0] = e.arg == 0 ? d0 : 0.f; v[G_E + 1] = e.arg == 0 ? d1 : 0.f; v[G_E + 2] = e.arg == 0 ? d2 : 0.f;
               v[G_E + 3] = e.arg == 1 ? d0 : 0.f; v[G_E + 4] = e.arg == 1 ? d1 : 0.f; v[G_E + 5] = e.arg == 1 ? d2 : 0.f;
@@ -446,7 +455,7 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             }
             ++contrib;
           }
-          if constexpr (NRM) {
+          if constexpr (AUX) {
             // reduce-scatter 32 -> 16 -> 8 -> 4 -> 2 -> 1: lane L ends with the sum of value L
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) {
@@ -526,73 +535,73 @@ __device__ __forceinline__ long long next_tile(const RenderArgs& a, RenderSmem& 
   return sm.next_tile < a.n_tiles ? (long long)sm.next_tile : -1;
 }
 
-template <int TW, int TH, bool PERSIST, bool NRM>
+template <int TW, int TH, bool PERSIST, bool AUX>
 __global__ void __launch_bounds__(TW * TH) k_render_fwd(RenderArgs a) {
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ RenderSmem sm;
   init_bars(sm);
   int seq = 0;
   if (!PERSIST) {
-    fwd_tile<TW, TH, NRM>(a, blockIdx.x, smrec, sm, seq);
+    fwd_tile<TW, TH, AUX>(a, blockIdx.x, smrec, sm, seq);
     return;
   }
   for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    if (!fwd_tile<TW, TH, NRM>(a, t, smrec, sm, seq)) return;
+    if (!fwd_tile<TW, TH, AUX>(a, t, smrec, sm, seq)) return;
 }
 
-template <int TW, int TH, bool PERSIST, bool NRM>
+template <int TW, int TH, bool PERSIST, bool AUX>
 __global__ void __launch_bounds__(TW * TH) k_render_bwd(RenderArgs a) {
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ RenderSmem sm;
   init_bars(sm);
   int seq = 0;
   if (!PERSIST) {
-    bwd_tile<TW, TH, NRM>(a, blockIdx.x, smrec, sm, seq);
+    bwd_tile<TW, TH, AUX>(a, blockIdx.x, smrec, sm, seq);
     return;
   }
   for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    if (!bwd_tile<TW, TH, NRM>(a, t, smrec, sm, seq)) return;
+    if (!bwd_tile<TW, TH, AUX>(a, t, smrec, sm, seq)) return;
 }
 
-// Dynamic shared memory: two stage buffers of S 128-byte records, then (with normals) two of S
-// 16-byte normals.
-template <int TW, int TH, bool NRM>
+// Dynamic shared memory: two stage buffers of S 128-byte records, then (with the side array) two
+// of S 16-byte side entries.
+template <int TW, int TH, bool AUX>
 cudaError_t launch_pair(bool fwd, bool persist, const RenderArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)2 * a.S * (NRM ? 144 : 128);
+  const size_t smem = (size_t)2 * a.S * (AUX ? 144 : 128);
   if (a.n_tiles == 0) return cudaSuccess;
   if (!persist) {
-    if (fwd) k_render_fwd<TW, TH, false, NRM><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
-    else k_render_bwd<TW, TH, false, NRM><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
+    if (fwd) k_render_fwd<TW, TH, false, AUX><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
+    else k_render_bwd<TW, TH, false, AUX><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
     return cudaGetLastError();
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<TW, TH, true, NRM>, TW * TH, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<TW, TH, true, NRM>, TW * TH, smem);
+  if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<TW, TH, true, AUX>, TW * TH, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<TW, TH, true, AUX>, TW * TH, smem);
   const long long grid = std::max(1LL, std::min<long long>(a.n_tiles, (long long)sms * std::max(per_sm, 1)));
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  if (fwd) k_render_fwd<TW, TH, true, NRM><<<(unsigned)grid, TW * TH, smem, s>>>(a);
-  else k_render_bwd<TW, TH, true, NRM><<<(unsigned)grid, TW * TH, smem, s>>>(a);
+  if (fwd) k_render_fwd<TW, TH, true, AUX><<<(unsigned)grid, TW * TH, smem, s>>>(a);
+  else k_render_bwd<TW, TH, true, AUX><<<(unsigned)grid, TW * TH, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool NRM>
+template <bool AUX>
 cudaError_t dispatch_tiles(bool fwd, const TsPlanImpl* p, const RenderArgs& a, cudaStream_t s) {
   const int tw = p->prm.tile_w, th = p->prm.tile_h;
   const bool persist = (p->prm.flags & TS_FLAG_PERSISTENT) != 0;
-  if (tw == 16 && th == 8) return launch_pair<16, 8, NRM>(fwd, persist, a, s);
-  if (tw == 16 && th == 16) return launch_pair<16, 16, NRM>(fwd, persist, a, s);
-  if (tw == 8 && th == 8) return launch_pair<8, 8, NRM>(fwd, persist, a, s);
-  if (tw == 32 && th == 8) return launch_pair<32, 8, NRM>(fwd, persist, a, s);
-  if (tw == 16 && th == 32) return launch_pair<16, 32, NRM>(fwd, persist, a, s);
-  if (tw == 32 && th == 16) return launch_pair<32, 16, NRM>(fwd, persist, a, s);
+  if (tw == 16 && th == 8) return launch_pair<16, 8, AUX>(fwd, persist, a, s);
+  if (tw == 16 && th == 16) return launch_pair<16, 16, AUX>(fwd, persist, a, s);
+  if (tw == 8 && th == 8) return launch_pair<8, 8, AUX>(fwd, persist, a, s);
+  if (tw == 32 && th == 8) return launch_pair<32, 8, AUX>(fwd, persist, a, s);
+  if (tw == 16 && th == 32) return launch_pair<16, 32, AUX>(fwd, persist, a, s);
+  if (tw == 32 && th == 16) return launch_pair<32, 16, AUX>(fwd, persist, a, s);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t dispatch(bool fwd, const TsPlanImpl* p, const RenderArgs& a, cudaStream_t s) {
-  return p->normals ? dispatch_tiles<true>(fwd, p, a, s) : dispatch_tiles<false>(fwd, p, a, s);
+  return (p->normals || p->face_sigma) ? dispatch_tiles<true>(fwd, p, a, s) : dispatch_tiles<false>(fwd, p, a, s);
 }
 
 RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
@@ -621,7 +630,9 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.hdr = w.hdr;
   a.counter = &w.hdr->tile_counter;
   a.cmask = w.cmask;
-  a.nrm = w.nrm;
+  a.aux = w.aux;
+  a.normals = p->normals;
+  a.face_sigma = p->face_sigma;
   a.cov = w.cov;
   a.normal = nullptr;
   a.dN = nullptr;

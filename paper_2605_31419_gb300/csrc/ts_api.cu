@@ -66,7 +66,8 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   if (prm->tris_per_stage != 32 && prm->tris_per_stage != 64 && prm->tris_per_stage != 128) return TS_ERR_INVALID_ARG;
   if (!(prm->sigma > 0.0f) || !(prm->alpha_max > 0.0f && prm->alpha_max < 1.0f) || !(prm->alpha_min >= 0.0f) ||
       !(prm->T_min >= 0.0f && prm->T_min < 1.0f) || !(prm->z_near > 0.0f) || !(prm->r_min >= 0.0f) ||
-      (prm->flags & ~(TS_FLAG_PERSISTENT | TS_FLAG_NORMALS | TS_FLAG_STATS | TS_FLAG_MIN_OPACITY)) != 0)
+      (prm->flags & ~(TS_FLAG_PERSISTENT | TS_FLAG_NORMALS | TS_FLAG_STATS | TS_FLAG_MIN_OPACITY |
+                       TS_FLAG_FACE_SIGMA)) != 0)
     return TS_ERR_INVALID_ARG;
   if (pair_capacity < 0) return TS_ERR_INVALID_ARG;
   memset(plan, 0, sizeof(ts_plan));
@@ -110,6 +111,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->normals = (prm->flags & TS_FLAG_NORMALS) != 0;
   p->stats = (prm->flags & TS_FLAG_STATS) != 0;
   p->min_opacity = (prm->flags & TS_FLAG_MIN_OPACITY) != 0;
+  p->face_sigma = (prm->flags & TS_FLAG_FACE_SIGMA) != 0;
   // layout
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -138,7 +140,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_cmask = take((size_t)cap * 2);
   p->o_pho = take((size_t)n_views * p->n_pho_blocks * 3 * 4);
   p->o_equi = take((size_t)ts_equi_blocks(n_faces) * 4);
-  p->o_nrm = take(p->normals ? (size_t)VM * 16 : 0);
+  p->o_aux = take((p->normals || p->face_sigma) ? (size_t)VM * 16 : 0);
   p->o_nloss = take((size_t)n_views * p->n_loss_blocks * 4);
   p->o_cov = take(p->stats ? (size_t)VM * 4 : 0);
   p->total = o;
@@ -200,6 +202,7 @@ ts_status ts_project(const ts_plan* plan, const ts_map* map, const ts_pose* pose
     if (!map->px || !map->py || !map->pz || !map->cr || !map->cg || !map->cb || !map->op) return TS_ERR_INVALID_ARG;
     if (!map->faces && map->n_vertices != 3 * map->n_faces) return TS_ERR_INVALID_ARG;
     if (map->faces && map->n_vertices < 1) return TS_ERR_INVALID_ARG;
+    if (p->face_sigma && !map->sigma) return TS_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
   TsWs w = ts_ws(p, ws);

@@ -88,9 +88,10 @@ struct TsPlanImpl {
   bool normals;  // TS_FLAG_NORMALS
   bool stats;    // TS_FLAG_STATS
   bool min_opacity;  // TS_FLAG_MIN_OPACITY
+  bool face_sigma;   // TS_FLAG_FACE_SIGMA
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
-      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, o_equi, o_nrm, o_nloss,
+      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, o_equi, o_aux, o_nloss,
       o_cov, total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
@@ -121,7 +122,8 @@ struct TsWs {
   float* loss;
   float* pho;  // per (view, 32 x 32 tile): L1, SSIM and depth partial sums of the photometric loss
   float* equi;  // per block of 256 faces: partial sums of the equilateral regulariser
-  float4* nrm;  // per (view, face): camera-space unit normal (TS_FLAG_NORMALS), else null
+  float4* aux;  // per (view, face): camera-space unit normal (TS_FLAG_NORMALS) and the face's sigma
+               // (TS_FLAG_FACE_SIGMA) in .w; null without either flag
   float* nloss;  // per (view, 2048-pixel block): partial sums of the normal loss
   uint32_t* cov;  // per (view, face): pixels blended by the forward (TS_FLAG_STATS), else null
   uint16_t* cmask;  // per sorted pair: the warps of its tile that blended the face in the forward
@@ -153,7 +155,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.loss = (float*)(b + p->o_loss);
   w.pho = (float*)(b + p->o_pho);
   w.equi = (float*)(b + p->o_equi);
-  w.nrm = p->normals ? (float4*)(b + p->o_nrm) : nullptr;
+  w.aux = (p->normals || p->face_sigma) ? (float4*)(b + p->o_aux) : nullptr;
   w.nloss = (float*)(b + p->o_nloss);
   w.cov = p->stats ? (uint32_t*)(b + p->o_cov) : nullptr;
   w.cmask = (uint16_t*)(b + p->o_cmask);

@@ -19,31 +19,35 @@ from . import binding as B
 @dataclass
 class Map:
     """Vertices as SoA float32 CUDA tensors: pos [3, N], col [3, N], opa [N]; faces int32 [M, 3] or
-    None for triangle-soup mode (face m = vertices 3m, 3m+1, 3m+2)."""
+    None for triangle-soup mode (face m = vertices 3m, 3m+1, 3m+2); sigma [M] per-face window
+    exponents for plans with TS_FLAG_FACE_SIGMA (in a gradient Map: dL/dsigma)."""
     pos: torch.Tensor
     col: torch.Tensor
     opa: torch.Tensor
     faces: Optional[torch.Tensor] = None
+    sigma: Optional[torch.Tensor] = None
 
     @property
     def n_faces(self) -> int:
         return self.faces.shape[0] if self.faces is not None else self.pos.shape[1] // 3
 
     @staticmethod
-    def from_numpy(pos, col, opa, faces=None, device="cuda") -> "Map":
+    def from_numpy(pos, col, opa, faces=None, device="cuda", sigma=None) -> "Map":
         t = lambda a: torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.float32).T)).to(device)  # noqa: E731
         f = None if faces is None else torch.from_numpy(np.ascontiguousarray(faces, np.int32)).to(device)
-        return Map(t(pos), t(col), torch.from_numpy(np.ascontiguousarray(opa, np.float32)).to(device), f)
+        sg = None if sigma is None else torch.from_numpy(np.ascontiguousarray(sigma, np.float32)).to(device)
+        return Map(t(pos), t(col), torch.from_numpy(np.ascontiguousarray(opa, np.float32)).to(device), f, sg)
 
     def ts(self) -> B.TsMap:
         for name in ("pos", "col", "opa"):
             t = getattr(self, name)
             if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
                 raise ValueError(f"Map.{name} must be a contiguous float32 CUDA tensor")
-        return B.make_map(self.pos, self.col, self.opa, self.faces)
+        return B.make_map(self.pos, self.col, self.opa, self.faces, self.sigma)
 
     def zeros_like(self) -> "Map":
-        return Map(torch.zeros_like(self.pos), torch.zeros_like(self.col), torch.zeros_like(self.opa), self.faces)
+        return Map(torch.zeros_like(self.pos), torch.zeros_like(self.col), torch.zeros_like(self.opa), self.faces,
+                   None if self.sigma is None else torch.zeros_like(self.sigma))
 
 
 def poses_tensor(poses, device="cuda") -> torch.Tensor:
@@ -116,7 +120,7 @@ class Rasterizer:
     def backward(self, dC, dD=None, dA=None, grad: Optional[Map] = None, stream=None, dN=None):
         """Adds dL/d(map) into ``grad`` (a Map of gradient tensors) and prepares the pose partials.
         dN: gradient w.r.t. the normal map (plans with TS_FLAG_NORMALS)."""
-        g = B.make_grad(grad.pos, grad.col, grad.opa) if grad is not None else None
+        g = B.make_grad(grad.pos, grad.col, grad.opa, grad.sigma) if grad is not None else None
         if dN is not None:
             B.ts_render_bwd_n(self.plan, self.ws, dC, dD, dA, dN, g, stream)
         else:

@@ -27,7 +27,7 @@ def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, dN=None, lamb
     import torch
     import paper_2605_31419_gb300 as ts
     rast = ts.Rasterizer(scene.cams, scene.n_faces, p, pair_capacity=pair_capacity)
-    m = ts.Map.from_numpy(scene.pos, scene.col, scene.opa, scene.faces)
+    m = ts.Map.from_numpy(scene.pos, scene.col, scene.opa, scene.faces, sigma=getattr(scene, "sigma", None))
     poses = ts.poses_tensor(scene.poses)
     C, D, A = rast.forward(m, poses)
     out = dict(color=C.cpu().numpy().astype(np.float64), depth=D.cpu().numpy().astype(np.float64),
@@ -58,6 +58,8 @@ def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, dN=None, lamb
         out["dcol"] = g.col.cpu().numpy().T.astype(np.float64)
         out["dopa"] = g.opa.cpu().numpy().astype(np.float64)
         out["dtau"] = dtau.cpu().numpy().astype(np.float64)
+        if g.sigma is not None:
+            out["dsigma"] = g.sigma.cpu().numpy().astype(np.float64)
         out["counters"] = rast.counters(raise_on_error=False)
     out["rast"] = rast
     return out
