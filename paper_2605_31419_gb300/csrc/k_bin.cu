@@ -3,8 +3,8 @@
 //  1. exclusive scan of the tiles each (view, face) touches (two-level, 4096 items per block);
 //  2. emission of one 64-bit key (global tile id << 32 | float bits of the depth key) and a
 //     face-id value per touched tile, in (view, face) order;
-//  3. a stable LSD radix sort over the key bits in use (32 depth bits + ceil(log2 tiles) tile
-//     bits, 8 bits per pass): per-block digit histograms, a scan of the digit-major histogram,
+//  3. a stable LSD radix sort over the key bits in use (31 depth bits -- a positive depth's sign
+//     bit is 0 -- and ceil(log2 tiles) tile bits, 8 bits per pass): per-block digit histograms, a scan of the digit-major histogram,
 //     and a scatter whose in-block ranks come from warp-level match masks, so that equal keys
 //     keep emission order (ascending face id);
 //  4. per-tile [start, end) ranges.
@@ -14,6 +14,14 @@
 #include "ts_internal.cuh"
 
 namespace {
+
+// Digit of a (tile << 32 | depth bits) key for an LSD pass starting at bit `shift` of the key with
+// bit 31 removed: visible faces have positive depth, so that bit is always 0 and 31 + ceil(log2
+// tiles) bits order the keys exactly as all 64 do.
+__device__ __forceinline__ uint32_t key_digit(unsigned long long key, int shift) {
+  const unsigned long long packed = ((key >> 32) << 31) | (key & 0x7fffffffull);
+  return (uint32_t)(packed >> shift) & 255u;
+}
 
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_PER = TS_SCAN_ITEMS / SCAN_T;  // 4
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(TS_SORT_THREADS) k_radix_upsweep(SortArgs a) {
   for (int j = 0; j < TS_SORT_ITEMS / TS_SORT_THREADS; ++j) {
     const long long i = base + (long long)j * TS_SORT_THREADS + threadIdx.x;
     const bool ok = i < n;
-    const uint32_t d = ok ? (uint32_t)(a.keys_in[i] >> a.shift) & 255u : 256u + lane;
+    const uint32_t d = ok ? key_digit(a.keys_in[i], a.shift) : 256u + lane;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(TS_SORT_THREADS) k_radix_downsweep(SortArgs a)
     const bool ok = i < n;
     key[r] = ok ? a.keys_in[i] : 0ull;
     val[r] = ok ? a.vals_in[i] : 0u;
-    const uint32_t d = ok ? (uint32_t)(key[r] >> a.shift) & 255u : 256u + lane;
+    const uint32_t d = ok ? key_digit(key[r], a.shift) : 256u + lane;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = ok ? wc[warp][d] : 0u;
     __syncwarp();
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(TS_SORT_THREADS) k_radix_downsweep(SortArgs a)
 #pragma unroll
   for (int r = 0; r < SORT_ROUNDS; ++r) {
     if (rank[r] == 0xffffffffu) continue;
-    const uint32_t d = (uint32_t)(key[r] >> a.shift) & 255u;
+    const uint32_t d = key_digit(key[r], a.shift);
     const long long dst = (long long)gbase[d] + wc[warp][d] + rank[r];
     if (dst < n) {
       a.keys_out[dst] = key[r];

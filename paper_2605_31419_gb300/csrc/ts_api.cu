@@ -100,7 +100,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   int tb = 0;
   while (((int64_t)1 << tb) < toff) ++tb;
   p->tile_bits = tb;
-  p->sort_passes = (32 + tb + 7) / 8;
+  p->sort_passes = (31 + tb + 7) / 8;  // depth bit 31 is always 0 for visible faces (positive depth)
   p->n_scan_blocks = std::max<int64_t>(1, (VM + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
   p->n_sort_blocks_cap = (cap + TS_SORT_ITEMS - 1) / TS_SORT_ITEMS;
   p->n_pose_blocks = std::max(1, ts_pose_blocks(n_faces));

@@ -80,15 +80,18 @@ def test_tracking_converges_with_graph_replay(oracle, lambda_ssim):
     err1 = ts.pose_error(trk.poses.cpu().numpy(), np.tile(gt, (8, 1)))
     assert np.median(err1[:, 0]) < 0.5 * np.median(err0[:, 0]), (err0, err1)
     assert np.median(err1[:, 1]) < 0.5 * np.median(err0[:, 1]), (err0, err1)
-    # eager execution of the same iterations matches the graph replay (over a few iterations:
-    # Adam normalises each step, so last-bit differences of the atomic gradient sums can flip
-    # individual steps and the two trajectories drift apart by ~1 mm over 100 iterations)
+    # a graph replay computes what eager execution computes: the same (deterministic) loss and the
+    # same pose gradient up to the order of its atomic sums.  (Poses are not compared: Adam's
+    # first steps are +-lr per component, so a near-zero gradient component whose last bits
+    # differ between two runs can flip its step.)
     a = ts.Tracker(m, sc.cams[0], tc, td, init, p, lambda_ssim=lambda_ssim)
-    a.run(3, use_graph=True)
+    a.run(1, use_graph=True)
     b = ts.Tracker(m, sc.cams[0], tc, td, init, p, lambda_ssim=lambda_ssim)
-    b.run(3, use_graph=False)
+    b.run(1, use_graph=False)
     torch.cuda.synchronize()
-    assert np.allclose(a.poses.cpu().numpy(), b.poses.cpu().numpy(), atol=2e-5)
+    assert np.array_equal(a.loss().cpu().numpy(), b.loss().cpu().numpy())
+    ga, gb = a.rast.dtau.cpu().numpy(), b.rast.dtau.cpu().numpy()
+    assert np.allclose(ga, gb, rtol=1e-4, atol=1e-6 * np.abs(gb).max())
 
 
 def _crop_scene():
