@@ -451,11 +451,26 @@ def main():
         d_poses, d_tc, d_td = torch.empty_like(poses), torch.empty_like(tgt_c), torch.empty_like(tgt_d)
         dm = ts.Map(d_pos, d_col, d_opa)
 
+        copy_stream = torch.cuda.Stream(device=dev)
+
         def e2e_step():
-            for d, hsrc in ((d_pos, h_pos), (d_col, h_col), (d_opa, h_opa), (d_poses, h_poses), (d_tc, h_tc),
-                            (d_td, h_td)):
+            # the map and poses feed the projection; the targets are first read by the loss, so
+            # they cross on a second stream while the projection, sort and forward blend run.
+            # Host-to-device copies share a copy engine in issue order: the map goes first.
+            for d, hsrc in ((d_pos, h_pos), (d_col, h_col), (d_opa, h_opa), (d_poses, h_poses)):
                 d.copy_(hsrc, non_blocking=True)
-            step(rast, dm, d_poses, d_tc, d_td)
+            copy_stream.wait_stream(stream)  # the previous step has finished reading the targets
+            with torch.cuda.stream(copy_stream):
+                d_tc.copy_(h_tc, non_blocking=True)
+                d_td.copy_(h_td, non_blocking=True)
+            targets_in = torch.cuda.Event()
+            targets_in.record(copy_stream)
+            grad.pos.zero_(); grad.col.zero_(); grad.opa.zero_()
+            rast.forward(dm, d_poses)
+            stream.wait_event(targets_in)
+            rast.l1_loss(d_tc, d_td, 0.05)
+            rast.backward(rast.dC, rast.dD, None, grad)
+            rast.pose_grad()
             out_pos.copy_(grad.pos, non_blocking=True)
             out_col.copy_(grad.col, non_blocking=True)
             out_opa.copy_(grad.opa, non_blocking=True)
