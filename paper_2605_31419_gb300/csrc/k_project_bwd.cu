@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
 #pragma unroll
     for (int f = 0; f < PG_F; ++f) {
       const long long m = m0 + f;
-      j[f] = (m < a.M && owner) ? (face_word ? m : face_vertex(h, m, k)) : 0;
+      j[f] = (m < a.M && dst) ? (face_word ? m : face_vertex(h, m, k)) : 0;
       old[f] = (m < a.M && dst && (!indexed || face_word)) ? dst[j[f]] : 0.f;  // issued early
       s[f] = 0.f;
     }
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
             if (bits) {
               const int v = r * 32 + __ffs(bits) - 1;
               bits &= bits - 1;
-              if (owner) vals[u] = base[(long long)v * TS_GRAD_WORDS];
+              if (dst) vals[u] = base[(long long)v * TS_GRAD_WORDS];  // only for a requested output
             }
           }
 #pragma unroll
