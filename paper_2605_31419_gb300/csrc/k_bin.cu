@@ -4,9 +4,11 @@
 //  2. emission of one 64-bit key (global tile id << 32 | float bits of the depth key) and a
 //     face-id value per touched tile, in (view, face) order;
 //  3. a stable LSD radix sort over the key bits in use (31 depth bits -- a positive depth's sign
-//     bit is 0 -- and ceil(log2 tiles) tile bits, 8 bits per pass): per-block digit histograms, a scan of the digit-major histogram,
-//     and a scatter whose in-block ranks come from warp-level match masks, so that equal keys
-//     keep emission order (ascending face id);
+//     bit is 0 -- and ceil(log2 tiles) tile bits, 8 bits per pass): per-block digit histograms,
+//     a scan of the digit-major histogram, and a scatter whose in-block ranks come from
+//     warp-level match masks, so that equal keys keep emission order (ascending face id); the
+//     block first reorders its keys by digit in shared memory so that each digit's run is
+//     written to global memory contiguously;
 //  4. per-tile [start, end) ranges.
 // Every kernel reads the pair count from the device, so nothing here synchronises the host.
 #include <algorithm>
@@ -232,9 +234,17 @@ __global__ void __launch_bounds__(TS_SORT_THREADS) k_radix_upsweep(SortArgs a) {
 constexpr int SORT_WARPS = TS_SORT_THREADS / 32;         // 8
 constexpr int SORT_ROUNDS = TS_SORT_ITEMS / TS_SORT_THREADS;  // 16: items per lane
 
+// Dynamic shared memory of the downsweep: the block's keys and values reordered by digit.
+constexpr size_t DOWNSWEEP_SMEM = (size_t)TS_SORT_ITEMS * (sizeof(unsigned long long) + sizeof(uint32_t));
+
 __global__ void __launch_bounds__(TS_SORT_THREADS) k_radix_downsweep(SortArgs a) {
+  extern __shared__ __align__(16) unsigned char sbuf[];
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(sbuf);
+  uint32_t* sval = reinterpret_cast<uint32_t*>(sbuf + (size_t)TS_SORT_ITEMS * sizeof(unsigned long long));
   __shared__ uint32_t wc[SORT_WARPS][256];
   __shared__ uint32_t gbase[256];
+  __shared__ uint32_t doff[256];       // start of each digit's run in the block's reordered keys
+  __shared__ uint32_t wsum[SORT_WARPS];
   long long n, nbs;
   sort_sizes(a, &n, &nbs);
   if (blockIdx.x >= nbs) return;
@@ -243,7 +253,8 @@ __global__ void __launch_bounds__(TS_SORT_THREADS) k_radix_downsweep(SortArgs a)
   gbase[threadIdx.x] = a.hist[(long long)threadIdx.x * nbs + blockIdx.x];
   __syncthreads();
   // each warp ranks a contiguous chunk of 512 keys in 16 rounds of 32
-  const long long wbase = (long long)blockIdx.x * TS_SORT_ITEMS + (long long)warp * (32 * SORT_ROUNDS);
+  const long long bbase = (long long)blockIdx.x * TS_SORT_ITEMS;
+  const long long wbase = bbase + (long long)warp * (32 * SORT_ROUNDS);
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long key[SORT_ROUNDS];
   uint32_t val[SORT_ROUNDS];
@@ -263,7 +274,9 @@ __global__ void __launch_bounds__(TS_SORT_THREADS) k_radix_downsweep(SortArgs a)
     rank[r] = ok ? before + __popc(peers & lt) : 0xffffffffu;
   }
   __syncthreads();
-  // digit-wise exclusive prefix over warps (in warp order = index order)
+  // digit-wise exclusive prefix over warps (in warp order = index order), and the block's count
+  // of each digit
+  uint32_t total;
   {
     const int d = threadIdx.x;
     uint32_t run = 0;
@@ -273,16 +286,44 @@ __global__ void __launch_bounds__(TS_SORT_THREADS) k_radix_downsweep(SortArgs a)
       wc[w][d] = run;
       run += c;
     }
+    total = run;
+  }
+  // exclusive scan of the digit counts over the 256 digits (thread d = digit d)
+  {
+    uint32_t x = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w)
+      if (w < warp) wpre += wsum[w];
+    doff[threadIdx.x] = wpre + x - total;
   }
   __syncthreads();
+  // reorder by digit in shared memory
 #pragma unroll
   for (int r = 0; r < SORT_ROUNDS; ++r) {
     if (rank[r] == 0xffffffffu) continue;
     const uint32_t d = key_digit(key[r], a.shift);
-    const long long dst = (long long)gbase[d] + wc[warp][d] + rank[r];
+    const uint32_t lp = doff[d] + wc[warp][d] + rank[r];
+    skey[lp] = key[r];
+    sval[lp] = val[r];
+  }
+  __syncthreads();
+  // write each digit's run to its place: consecutive threads write consecutive addresses
+  const int nb = (int)min((long long)TS_SORT_ITEMS, n - bbase);
+  for (int i = threadIdx.x; i < nb; i += TS_SORT_THREADS) {
+    const unsigned long long k = skey[i];
+    const uint32_t d = key_digit(k, a.shift);
+    const long long dst = (long long)gbase[d] + (i - (long long)doff[d]);
     if (dst < n) {
-      a.keys_out[dst] = key[r];
-      a.vals_out[dst] = val[r];
+      a.keys_out[dst] = k;
+      a.vals_out[dst] = sval[i];
     } else {
       atomicOr(a.err, TS_ERRBIT_BOUNDS);
     }
@@ -323,6 +364,11 @@ cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
   const long long hist_len = 256LL * p->n_sort_blocks_cap;
   const unsigned nbh = (unsigned)((hist_len + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
   Len lh{0, &w.hdr->n_pairs, p->cap};
+  {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DOWNSWEEP_SMEM);
+    if (e != cudaSuccess) return e;
+  }
   for (int pass = 0; pass < p->sort_passes; ++pass) {
     const int in = pass & 1;
     SortArgs sa{w.keys[in], w.vals[in], w.keys[in ^ 1], w.vals[in ^ 1], &w.hdr->n_pairs, p->cap, 8 * pass, w.hist,
@@ -331,7 +377,7 @@ cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
     k_scan_reduce<<<nbh, SCAN_T, 0, s>>>(w.hist, lh, w.hsums);
     k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.hsums, lh, nullptr, nullptr, 0);
     k_scan_apply<<<nbh, SCAN_T, 0, s>>>(w.hist, lh, w.hsums);
-    k_radix_downsweep<<<nbs, TS_SORT_THREADS, 0, s>>>(sa);
+    k_radix_downsweep<<<nbs, TS_SORT_THREADS, DOWNSWEEP_SMEM, s>>>(sa);
   }
   // 4: tile ranges over the sorted keys
   const int fb = ts_sort_final_buffer(p);
