@@ -284,6 +284,53 @@ def bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_pea
                          "work": f"{3 * pixels} pixel-channels x {FLOPS_PHO:.0f} flops"}}
 
 
+def bench_variants(ts, torch, sc, m, poses, tgt_c, tgt_d, flush, stream, params, reps=5):
+    """The bench step under each raster switch (same workload, L2 flushed, CUDA events): the normal
+    map of Eq. 12 with its gradient, the map statistics of Sec. 3.4 (forward coverage counting plus
+    ts_face_stats and ts_covisibility), the min-opacity faces and the per-face sigma variant."""
+    from ts_synth.scenes import sensor_normals
+    tn = torch.as_tensor(sensor_normals(7, sc.cams), device=m.pos.device)
+    sigma = torch.full((sc.n_faces,), 0.5, dtype=torch.float32, device=m.pos.device)
+    ms_sig = ts.Map(m.pos, m.col, m.opa, None, sigma)
+    out = {"workload": WORKLOAD.split(",")[0] + ", the bench step with one switch on"}
+    cases = (("plain", 0), ("normals", ts.TS_FLAG_NORMALS), ("stats", ts.TS_FLAG_STATS),
+             ("min_opacity", ts.TS_FLAG_MIN_OPACITY), ("face_sigma", ts.TS_FLAG_FACE_SIGMA))
+    for name, flag in cases:
+        p = ts.batch.params_of({"tile_w": params.tile_w, "tile_h": params.tile_h,
+                                "tris_per_stage": params.tris_per_stage})
+        p.flags = flag
+        r = ts.Rasterizer(sc.cams, sc.n_faces, p)
+        mm = ms_sig if flag == ts.TS_FLAG_FACE_SIGMA else m
+        g = mm.zeros_like()
+
+        def step():
+            g.pos.zero_(); g.col.zero_(); g.opa.zero_()
+            r.forward(mm, poses)
+            r.l1_loss(tgt_c, tgt_d, 0.05)
+            dN = r.normal_loss(tn, 0.05)[1] if flag == ts.TS_FLAG_NORMALS else None
+            r.backward(r.dC, r.dD, None, g, dN=dN)
+            r.pose_grad()
+            if flag == ts.TS_FLAG_STATS:
+                st = r.face_stats()
+                r.covisibility(st["visible"])
+
+        for _ in range(2):
+            step()
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[name] = {"ms_per_step": float(np.median(ms)), "mpix_s": sc.pixels() / (float(np.median(ms)) / 1e3) / 1e6}
+        del r, g
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_serving(ts, torch, dev, rates=(200, 500, 1000, 2000), seconds=2.0, n_faces=2_000_000):
     """Serving: device-resident 2M-face map; Poisson arrivals of render (one forward) and track
     (10 pose iterations) requests, resolutions uniform over 256x256, 640x480 and 1200x680,
@@ -530,6 +577,8 @@ def main():
         line["pho_loss"] = bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max)
         if not args.no_extras:
             del rast
+            torch.cuda.empty_cache()
+            line["variants"] = bench_variants(ts, torch, sc, m, poses, tgt_c, tgt_d, flush, stream, params)
             torch.cuda.empty_cache()
             line["mapping_window"] = bench_mapping_window(ts, torch, dev)
             line["tracking"] = bench_tracking(ts, torch, dev)

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "ts_internal.cuh"
 
@@ -39,6 +40,23 @@ struct StageTimer {
 };
 
 }  // namespace
+
+cudaError_t ts_smem_limit_once(int key, const void* func, int bytes) {
+  constexpr int kMaxDevices = 64, kKeys = 8;
+  static std::mutex mu;
+  static int done[kMaxDevices][kKeys];  // 0: not yet, 1: set, 2: failed
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices || key < 0 || key >= kKeys) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev][key] == 0) {
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done[dev][key] = e == cudaSuccess ? 1 : 2;
+    return e;
+  }
+  return done[dev][key] == 1 ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 extern "C" {
 

@@ -103,6 +103,28 @@ class Server:
         self.dD = torch.empty(self.max_pixels, device=self.device)
         self.dtau = torch.empty(self.max_views, 6, device=self.device)
         self.stats = dict(steps=0, pixels=0, rejected_for_memory=0)
+        self._warmup()
+
+    def _warmup(self):
+        """One render and one track step on a 16 x 16 view, so that one-time costs of the device
+        code a step runs (module loading of this library's and PyTorch's kernels, which took
+        seconds for PyTorch's index_select and index_copy_ on a fresh GB300) are paid here and
+        not by the first requests.  All server state is restored afterwards."""
+        cam = np.array([16.0, 16.0, 8.0, 8.0, 16, 16])
+        pose = np.array([1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0], np.float32)
+        tc = torch.zeros(3, 16, 16, device=self.device)
+        td = torch.zeros(16, 16, device=self.device)
+        render = Request(-1, "render", cam, pose)
+        track = Request(-2, "track", cam, pose, 0.0, tc, td)
+        track._slot = self.free_slots[0]
+        self._launch_renders([render])
+        self._launch_tracks([track])
+        torch.cuda.synchronize(self.device)
+        self.slot_pose.zero_()
+        self.slot_adam.zero_()
+        for lane in (self.render_lane, self.track_lane):
+            lane.pending.clear()
+        self.stats = dict(steps=0, pixels=0, rejected_for_memory=0)
 
     # ---------------------------------------------------------------- admission
     def _fits(self, cams: List[np.ndarray]) -> bool:
