@@ -365,7 +365,7 @@ cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
   const unsigned nbh = (unsigned)((hist_len + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
   Len lh{0, &w.hdr->n_pairs, p->cap};
   {
-    const cudaError_t e = ts_smem_limit_once(0, (const void*)k_radix_downsweep, (int)DOWNSWEEP_SMEM);
+    const cudaError_t e = ts_smem_limit((const void*)k_radix_downsweep, (int)DOWNSWEEP_SMEM);
     if (e != cudaSuccess) return e;
   }
   for (int pass = 0; pass < p->sort_passes; ++pass) {

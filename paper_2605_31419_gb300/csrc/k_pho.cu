@@ -329,7 +329,7 @@ int64_t ts_pho_blocks(const TsView* views, int V) {
 cudaError_t ts_launch_pho_loss(const TsPlanImpl* p, const TsWs& w, const float* color, const float* depth,
                                const float* tc, const float* td, float lambda, float lambda_dep, float* loss,
                                float* dC, float* dD, cudaStream_t s) {
-  cudaError_t e = ts_smem_limit_once(1, (const void*)k_pho_tile, (int)PHO_SMEM);
+  cudaError_t e = ts_smem_limit((const void*)k_pho_tile, (int)PHO_SMEM);
   if (e != cudaSuccess) return e;
   const int nblk = (int)p->n_pho_blocks;
   const TsImageTable tab = ts_image_table(p);

@@ -15,11 +15,16 @@
 //
 // Backward: per pixel, back to front from that position: recover T_n = T_{n+1} / (1 - alpha_n),
 // keep the suffix sum S of later contributions (including the background term), form
-// dL/dalpha_n = T_n v_n - S / (1 - alpha_n) with v_n = gC . c_n + gD z_n + gA, and chain into 22
-// per-face sums (barycentric-weighted gradients of the edge, colour and depth interpolants, and
-// of o_F).  A warp reduces the 24-word vector with a 27-shuffle reduce-scatter, leaving one sum
-// per lane, and issues a single 24-lane atomic add into the face's accumulator.  A warp visits
-// only the faces whose forward mask holds its bit.
+// dL/dalpha_n = T_n v_n - S / (1 - alpha_n) with v_n = gC . c_n + gD z_n + gA, and chain into 23
+// per-face sums (barycentric-weighted gradients of the edge, colour and depth interpolants, of
+// o_F, and the contribution count).  Every sum is over products of two per-pixel factors (a
+// weighted gradient times a barycentric coordinate, or a scalar times one), so a contributing
+// lane appends its 12 factors to its warp's ring in shared memory, one group of rows per face
+// visit.  When the ring is full (and at the end of the tile) lane L of the warp walks the groups,
+// summing word L's products over each group's rows, and adds the sum into the face's accumulator
+// with one atomic: the faces here cover a few pixels of a warp, and a reduction over all 32
+// lanes per visit cost more than the visit itself.  A warp visits only the faces whose forward
+// mask holds its bit.
 //
 // Launch forms: one CTA per tile, or persistent CTAs (as many as fit on the GPU) that take tiles
 // from a device counter, keeping their mbarriers across tiles.
@@ -77,12 +82,28 @@ constexpr int raster_min_blocks(int threads) {
 struct RenderSmem {
   uint64_t bar[2];
   uint32_t smask[2][128];
-  uint32_t cm[2][128];  // forward: warps of the tile that blended each staged face
-  uint32_t cv[2][128];  // forward, TS_FLAG_STATS: pixels of the tile that blended each staged face
   int view;
   int nmax;
   int next_tile;
   int fail;
+};
+
+// Forward only: per staged face, the warps of the tile that blended it and (TS_FLAG_STATS) the
+// number of its pixels that did.
+struct FwdMasks {
+  uint32_t cm[2][128];
+  uint32_t cv[2][128];
+};
+
+// Backward ring: per warp RING_CAP rows of the factors of one contributing pixel, and a header
+// (slot, end row) per face visit.  Row words: 0-2 barycentrics l_k; 3-5 w gC_c; 6 w gD; 7-9 dm
+// routed to the nearest edge (zero for the other two); 10 dL/do_F; 11 one; with the side array
+// 12-14 w gN_c and 15 dL/dsigma_F.
+constexpr int RING_CAP = 32;
+template <bool AUX>
+struct Ring {
+  static constexpr int EW = AUX ? 16 : 12;
+  static constexpr int BYTES_PER_WARP = RING_CAP * (EW * 4 + 8);
 };
 
 template <int TW, int TH>
@@ -205,7 +226,7 @@ __device__ __forceinline__ bool wait_stage(const RenderArgs& a, RenderSmem& sm, 
 // Forward of one tile; seq counts the stages this CTA has waited for so far (mbarrier phases).
 template <int TW, int TH, bool AUX>
 __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
-                                         int& seq) {
+                                         FwdMasks& fm, int& seq) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint2 rg = a.ranges[tile];
@@ -231,8 +252,8 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
       stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
       for (int j = threadIdx.x; j < cnt; j += TW * TH) {
-        sm.cm[b][j] = 0u;
-        sm.cv[b][j] = 0u;
+        fm.cm[b][j] = 0u;
+        fm.cv[b][j] = 0u;
       }
       __syncthreads();
       if (warp == 0 && st + 1 < nst) issue_stage<AUX>(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase, nbase);
@@ -279,18 +300,18 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
           // the backward revisits exactly the (warp, face) pairs that blended somewhere
           const unsigned bl = __ballot_sync(FULL, blended);
           if (bl && lane == 0) {
-            atomicOr(&sm.cm[b][j], 1u << warp);
-            if (a.cov) atomicAdd(&sm.cv[b][j], (unsigned)__popc(bl));
+            atomicOr(&fm.cm[b][j], 1u << warp);
+            if (a.cov) atomicAdd(&fm.cv[b][j], (unsigned)__popc(bl));
           }
         }
       }
       const int alive = __syncthreads_count(!done);
       for (int j = threadIdx.x; j < cnt; j += TW * TH) {
-        a.cmask[rg.x + st * S + j] = (uint16_t)sm.cm[b][j];
-        if (a.cov && sm.cv[b][j]) {  // face m of the record's slot m * V + view
+        a.cmask[rg.x + st * S + j] = (uint16_t)fm.cm[b][j];
+        if (a.cov && fm.cv[b][j]) {  // face m of the record's slot m * V + view
           const uint32_t slot = __float_as_uint(rb[j * TS_REC_WORDS + R_SLOT]);
           const long long m = (long long)(slot / (uint32_t)a.V);
-          if (m < a.M) atomicAdd(a.cov + (long long)g.view * a.M + m, sm.cv[b][j]);
+          if (m < a.M) atomicAdd(a.cov + (long long)g.view * a.M + m, fm.cv[b][j]);
         }
       }
       if (alive == 0) {
@@ -325,6 +346,60 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
     a.nlast[o] = nl;
   }
   return ok;
+}
+
+// Lane `lane`'s gradient word as a product of two ring-row words (ia x ib); false for a lane with
+// no word of its own (it multiplies one by one and adds nothing).
+template <bool AUX>
+__device__ __forceinline__ bool ring_word(int lane, int& ia, int& ib) {
+  ia = 11;
+  ib = 11;
+  if (lane < G_C) {  // G_E[i][k]: dm routed to edge i, times l_k
+    ia = 7 + lane / 3;
+    ib = lane % 3;
+  } else if (lane < G_Z) {  // G_C[c][k]: w gC_c times l_k
+    ia = 3 + (lane - G_C) / 3;
+    ib = (lane - G_C) % 3;
+  } else if (lane < G_O) {  // G_Z[k]: w gD times l_k
+    ia = 6;
+    ib = lane - G_Z;
+  } else if (lane == G_O) {
+    ia = 10;
+  } else if (lane == G_CNT) {
+  } else if (AUX && lane == 23) {
+    ia = 12;
+  } else if (AUX && lane == 24) {
+    ia = 15;
+  } else if (AUX && lane == 30) {
+    ia = 13;
+  } else if (AUX && lane == 31) {
+    ia = 14;
+  } else {
+    return false;
+  }
+  return true;
+}
+
+// Sum each group's rows of the warp's ring into the group's face accumulator (lane L: word L).
+template <bool AUX>
+__device__ __forceinline__ void ring_flush(const RenderArgs& a, const float* ring, const uint2* gh, int ng, int lane,
+                                           int ia, int ib, bool has) {
+  constexpr int EW = Ring<AUX>::EW;
+  __syncwarp();
+  int e = 0;
+  for (int g = 0; g < ng; ++g) {
+    const uint2 h = gh[g];
+    float sum = 0.f;
+    for (; e < (int)h.y; ++e) sum = fmaf(ring[e * EW + ia], ring[e * EW + ib], sum);
+    if (has && sum != 0.f) {
+      if ((long long)h.x < a.VM) {
+        atomicAdd(a.grad + (size_t)h.x * TS_GRAD_WORDS + lane, sum);
+      } else {
+        atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
+      }
+    }
+  }
+  __syncwarp();
 }
 
 template <int TW, int TH, bool AUX>
@@ -374,9 +449,15 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
     const float4* nbase = AUX ? a.aux + (size_t)g.view * (size_t)a.M : nullptr;
     if (warp == 0) issue_stage<AUX>(a, smrec, sm.bar, seq & 1, nst - 1, rg.x, n, vbase, nbase);
-    const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
-    const int q = lane & 3;
-    const int widx = (hi16 ? 12 : 0) + (hi8 ? 6 : 0) + (hi4 ? 3 : 0) + q;
+    constexpr int EW = Ring<AUX>::EW;
+    float* ring = reinterpret_cast<float*>(smrec + (size_t)2 * S * (AUX ? 9 : 8)) + warp * RING_CAP * EW;
+    uint2* gh = reinterpret_cast<uint2*>(reinterpret_cast<float*>(smrec + (size_t)2 * S * (AUX ? 9 : 8)) +
+                                         (TW * TH / 32) * RING_CAP * EW) +
+                warp * RING_CAP;
+    int ia, ib;
+    const bool has = ring_word<AUX>(lane, ia, ib);
+    const unsigned below = (1u << lane) - 1u;
+    int fill = 0, ng = 0;  // the ring's rows and groups in use (the same in every lane)
     for (int k = 0; k < nst; ++k) {
       const int st = nst - 1 - k;
       const int b = seq & 1;
@@ -412,13 +493,14 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
               cb = al >= a.alpha_min;
             }
           }
-          if (!__any_sync(FULL, cb)) continue;
-          // per-face sums: words 0..22, and with the side array dL/dn_F in words 23, 30, 31 and
-          // dL/dsigma_F in word 24 (the chain pass moves it to 23 before it writes the pose terms)
-          constexpr int NVAL = AUX ? 32 : 24;
-          float v[NVAL];
-#pragma unroll
-          for (int i = 0; i < NVAL; ++i) v[i] = 0.f;
+          const unsigned cbm = __ballot_sync(FULL, cb);
+          if (!cbm) continue;
+          const int nc = __popc(cbm);
+          if (fill + nc > RING_CAP) {
+            ring_flush<AUX>(a, ring, gh, ng, lane, ia, ib, has);
+            fill = 0;
+            ng = 0;
+          }
           if (cb) {
             const float oma = 1.f - al;  // >= 1 - alpha_max
             const float ro = ts_rcp_approx(oma);
@@ -430,100 +512,39 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
             const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
             float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
-            float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
             if (AUX && a.normals) {
-              nn = nb[j];
+              const float4 nn = nb[j];
               val += gN0 * nn.x + gN1 * nn.y + gN2 * nn.z;
             }
             const float dal = val * Tn - Sacc * ro;
             Sacc += val * al * Tn;
             T = Tn;
             const float w = al * Tn;
-            const float w0 = gC0 * w, w1 = gC1 * w, w2 = gC2 * w, wz = gD * w;
-            v[G_C + 0] = w0 * l0; v[G_C + 1] = w0 * l1; v[G_C + 2] = w0 * l2;
-            v[G_C + 3] = w1 * l0; v[G_C + 4] = w1 * l1; v[G_C + 5] = w1 * l2;
-            v[G_C + 6] = w2 * l0; v[G_C + 7] = w2 * l1; v[G_C + 8] = w2 * l2;
-            v[G_Z + 0] = wz * l0; v[G_Z + 1] = wz * l1; v[G_Z + 2] = wz * l2;
-            v[G_CNT] = 1.f;
-            if constexpr (AUX) {
-              v[23] = gN0 * w;
-              v[30] = gN1 * w;
-              v[31] = gN2 * w;
-            }
+            float go = 0.f, dm = 0.f, gs = 0.f;
             const float oF = r[R_OF];
             if (!(oF * I > a.alpha_max)) {
-              v[G_O] = dal * I;
+              go = dal * I;
               const float dI = dal * oF;
               // I >= alpha_min / o_F here, far from zero
-              const float dm = (sig == 0.5f) ? dI * 0.5f * ts_rcp_approx(I) : dI * sig * I / e.m;
+              dm = (sig == 0.5f) ? dI * 0.5f * ts_rcp_approx(I) : dI * sig * I / e.m;
               if constexpr (AUX) {  // dL/dsigma_F = dL/dalpha o_F I ln(ratio)
-                if (a.face_sigma) v[24] = dI * I * logf(e.m);
+                if (a.face_sigma) gs = dI * I * logf(e.m);
               }
-              const float d0 = dm * l0, d1 = dm * l1, d2 = dm * l2;
-              v[G_E + 0] = e.arg == 0 ? d0 : 0.f; v[G_E + 1] = e.arg == 0 ? d1 : 0.f; v[G_E + 2] = e.arg == 0 ? d2 : 0.f;
-              v[G_E + 3] = e.arg == 1 ? d0 : 0.f; v[G_E + 4] = e.arg == 1 ? d1 : 0.f; v[G_E + 5] = e.arg == 1 ? d2 : 0.f;
-              v[G_E + 6] = e.arg == 2 ? d0 : 0.f; v[G_E + 7] = e.arg == 2 ? d1 : 0.f; v[G_E + 8] = e.arg == 2 ? d2 : 0.f;
             }
+            float4* row = reinterpret_cast<float4*>(ring + (fill + __popc(cbm & below)) * EW);
+            row[0] = make_float4(l0, l1, l2, gC0 * w);
+            row[1] = make_float4(gC1 * w, gC2 * w, gD * w, e.arg == 0 ? dm : 0.f);
+            row[2] = make_float4(e.arg == 1 ? dm : 0.f, e.arg == 2 ? dm : 0.f, go, 1.f);
+            if constexpr (AUX) row[3] = make_float4(gN0 * w, gN1 * w, gN2 * w, gs);
             ++contrib;
           }
-          if constexpr (AUX) {
-            // reduce-scatter 32 -> 16 -> 8 -> 4 -> 2 -> 1: lane L ends with the sum of value L
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-              const bool hi = lane & o;
-#pragma unroll
-              for (int i = 0; i < o; ++i) {
-                const float send = hi ? v[i] : v[i + o];
-                const float keep = hi ? v[i + o] : v[i];
-                v[i] = keep + __shfl_xor_sync(FULL, send, o);
-              }
-            }
-            if (v[0] != 0.f) {
-              const uint32_t slot = __float_as_uint(r[R_SLOT]);
-              if ((long long)slot < a.VM) {
-                atomicAdd(a.grad + (size_t)slot * TS_GRAD_WORDS + lane, v[0]);
-              } else {
-                atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
-              }
-            }
-            continue;
-          }
-          // reduce-scatter: 24 -> 12 -> 6 -> 3 values per lane, then a butterfly over 4 lanes
-#pragma unroll
-          for (int i = 0; i < 12; ++i) {
-            const float send = hi16 ? v[i] : v[i + 12];
-            const float keep = hi16 ? v[i + 12] : v[i];
-            v[i] = keep + __shfl_xor_sync(FULL, send, 16);
-          }
-#pragma unroll
-          for (int i = 0; i < 6; ++i) {
-            const float send = hi8 ? v[i] : v[i + 6];
-            const float keep = hi8 ? v[i + 6] : v[i];
-            v[i] = keep + __shfl_xor_sync(FULL, send, 8);
-          }
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const float send = hi4 ? v[i] : v[i + 3];
-            const float keep = hi4 ? v[i + 3] : v[i];
-            v[i] = keep + __shfl_xor_sync(FULL, send, 4);
-          }
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            v[i] += __shfl_xor_sync(FULL, v[i], 2);
-            v[i] += __shfl_xor_sync(FULL, v[i], 1);
-          }
-          const float mine = q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
-          if (q < 3 && mine != 0.f) {
-            const uint32_t slot = __float_as_uint(r[R_SLOT]);
-            if ((long long)slot < a.VM) {
-              atomicAdd(a.grad + (size_t)slot * TS_GRAD_WORDS + widx, mine);
-            } else {
-              atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
-            }
-          }
+          fill += nc;
+          if (lane == 0) gh[ng] = make_uint2(__float_as_uint(r[R_SLOT]), (unsigned)fill);
+          ++ng;
         }
       }
     }
+    if (ng) ring_flush<AUX>(a, ring, gh, ng, lane, ia, ib, has);
   }
   count_add(&a.hdr->bwd_contrib, contrib);
   return ok;
@@ -550,14 +571,15 @@ template <int TW, int TH, bool PERSIST, bool AUX>
 __global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_fwd(RenderArgs a) {
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ RenderSmem sm;
+  __shared__ FwdMasks fm;
   init_bars(sm);
   int seq = 0;
   if (!PERSIST) {
-    fwd_tile<TW, TH, AUX>(a, blockIdx.x, smrec, sm, seq);
+    fwd_tile<TW, TH, AUX>(a, blockIdx.x, smrec, sm, fm, seq);
     return;
   }
   for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    if (!fwd_tile<TW, TH, AUX>(a, t, smrec, sm, seq)) return;
+    if (!fwd_tile<TW, TH, AUX>(a, t, smrec, sm, fm, seq)) return;
 }
 
 template <int TW, int TH, bool PERSIST, bool AUX>
@@ -575,11 +597,17 @@ __global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_
 }
 
 // Dynamic shared memory: two stage buffers of S 128-byte records, then (with the side array) two
-// of S 16-byte side entries.
+// of S 16-byte side entries, then in the backward the warps' rings and their headers.
 template <int TW, int TH, bool AUX>
 cudaError_t launch_pair(bool fwd, bool persist, const RenderArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)2 * a.S * (AUX ? 144 : 128);
+  const size_t smem = (size_t)2 * a.S * (AUX ? 144 : 128) + (fwd ? 0 : (size_t)(TW * TH / 32) * Ring<AUX>::BYTES_PER_WARP);
   if (a.n_tiles == 0) return cudaSuccess;
+  {
+    const void* f = fwd ? (persist ? (const void*)k_render_fwd<TW, TH, true, AUX> : (const void*)k_render_fwd<TW, TH, false, AUX>)
+                        : (persist ? (const void*)k_render_bwd<TW, TH, true, AUX> : (const void*)k_render_bwd<TW, TH, false, AUX>);
+    const cudaError_t e = ts_smem_limit(f, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   if (!persist) {
     if (fwd) k_render_fwd<TW, TH, false, AUX><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
     else k_render_bwd<TW, TH, false, AUX><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);

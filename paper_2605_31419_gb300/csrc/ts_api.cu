@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "ts_internal.cuh"
 
@@ -41,21 +42,32 @@ struct StageTimer {
 
 }  // namespace
 
-cudaError_t ts_smem_limit_once(int key, const void* func, int bytes) {
-  constexpr int kMaxDevices = 64, kKeys = 8;
+cudaError_t ts_smem_limit(const void* func, int bytes) {
+  struct Entry {
+    int dev;
+    const void* func;
+    int bytes;   // the largest limit set so far
+    bool failed;
+  };
   static std::mutex mu;
-  static int done[kMaxDevices][kKeys];  // 0: not yet, 1: set, 2: failed
+  static std::vector<Entry> set;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices || key < 0 || key >= kKeys) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lock(mu);
-  if (done[dev][key] == 0) {
-    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    done[dev][key] = e == cudaSuccess ? 1 : 2;
-    return e;
+  Entry* hit = nullptr;
+  for (Entry& x : set)
+    if (x.dev == dev && x.func == func) hit = &x;
+  if (hit && hit->failed) return cudaErrorInvalidValue;
+  if (hit && hit->bytes >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (!hit) {
+    set.push_back(Entry{dev, func, 0, false});
+    hit = &set.back();
   }
-  return done[dev][key] == 1 ? cudaSuccess : cudaErrorInvalidValue;
+  if (e == cudaSuccess) hit->bytes = bytes;
+  else hit->failed = true;
+  return e;
 }
 
 extern "C" {

@@ -189,10 +189,10 @@ inline TsImageTable ts_image_table(const TsPlanImpl* p) {
   }
   return t;
 }
-// Raise a kernel's dynamic shared-memory limit once per device and kernel (a host call that
-// must not run per launch: the launches of concurrent streams would wait on it).  `key` names
-// the kernel (0..7); returns the first call's status.
-cudaError_t ts_smem_limit_once(int key, const void* func, int bytes);
+// Raise a kernel's dynamic shared-memory limit on the current device to at least `bytes`.  The
+// attribute call runs only when the limit grows (a host call that must not run per launch: the
+// launches of concurrent streams would wait on it); a failed call is remembered and reported again.
+cudaError_t ts_smem_limit(const void* func, int bytes);
 int64_t ts_pho_blocks(const TsView* views, int V);
 int64_t ts_equi_blocks(int64_t M);
 cudaError_t ts_launch_equilateral(const TsPlanImpl* p, const TsWs& w, const ts_map* map, float weight, float* loss,
