@@ -10,21 +10,22 @@
 // Forward: per pixel, front to back: window (Eq. 3) from cancellation-free edge functions,
 // alpha = min(alpha_max, o_F I), skip below alpha_min, stop before the face that would take T
 // below T_min, accumulate colour, depth and opacity (Eq. 4).  Writes C + T bg, D, A = 1 - T, and
-// per pixel T_final and the list position after the last contribution, and per sorted pair the
-// mask of warps that blended the face at one of their pixels.
+// per pixel T_final and the list position after the last contribution, and per sorted pair and
+// warp the mask of the warp's pixels that blended the face.
 //
 // Backward: per pixel, back to front from that position: recover T_n = T_{n+1} / (1 - alpha_n),
 // keep the suffix sum S of later contributions (including the background term), form
 // dL/dalpha_n = T_n v_n - S / (1 - alpha_n) with v_n = gC . c_n + gD z_n + gA, and chain into 23
 // per-face sums (barycentric-weighted gradients of the edge, colour and depth interpolants, of
-// o_F, and the contribution count).  Every sum is over products of two per-pixel factors (a
-// weighted gradient times a barycentric coordinate, or a scalar times one), so a contributing
-// lane appends its 12 factors to its warp's ring in shared memory, one group of rows per face
-// visit.  When the ring is full (and at the end of the tile) lane L of the warp walks the groups,
-// summing word L's products over each group's rows, and adds the sum into the face's accumulator
-// with one atomic: the faces here cover a few pixels of a warp, and a reduction over all 32
-// lanes per visit cost more than the visit itself.  A warp visits only the faces whose forward
-// mask holds its bit.
+// o_F, and the contribution count).  The forward stores, per sorted pair and warp, the 32-bit
+// mask of the warp's pixels that blended the face; the backward queues those (face, pixel)
+// entries back to front and processes them 32 at a time, one per lane, so that no lane idles on
+// a pixel the face does not cover.  Lanes holding entries of the same pixel replay its recurrence
+// in queue order (the same products and sums, in the same order, as a per-pixel loop).  Every
+// per-face sum is over products of two per-entry factors (a weighted gradient times a
+// barycentric coordinate, or a scalar times one); each lane writes its factors to a ring row in
+// shared memory, and lane L then sums word L's products over each face's run of rows and adds it
+// into the face's accumulator with one atomic.
 //
 // Launch forms: one CTA per tile, or persistent CTAs (as many as fit on the GPU) that take tiles
 // from a device counter, keeping their mbarriers across tiles.
@@ -55,7 +56,7 @@ struct RenderArgs {
   float bg0, bg1, bg2;
   int S;
   unsigned int* counter;
-  uint16_t* cmask;
+  uint32_t* lmask;
   const float4* aux;   // per (view, face): camera-space normal and, in .w, sigma_F; else null
   bool normals;        // TS_FLAG_NORMALS: composite the normal map
   bool face_sigma;     // TS_FLAG_FACE_SIGMA: each face's own window exponent
@@ -81,29 +82,29 @@ constexpr int raster_min_blocks(int threads) {
 // Shared state of a render CTA.
 struct RenderSmem {
   uint64_t bar[2];
-  uint32_t smask[2][128];
+  uint16_t smask[2][128];  // per staged face, the warps (sub-blocks) that visit it
   int view;
   int nmax;
   int next_tile;
   int fail;
 };
 
-// Forward only: per staged face, the warps of the tile that blended it and (TS_FLAG_STATS) the
-// number of its pixels that did.
+// Forward only, TS_FLAG_STATS: per staged face, the number of the tile's pixels that blended it.
 struct FwdMasks {
-  uint32_t cm[2][128];
   uint32_t cv[2][128];
 };
 
-// Backward ring: per warp RING_CAP rows of the factors of one contributing pixel, and a header
-// (slot, end row) per face visit.  Row words: 0-2 barycentrics l_k; 3-5 w gC_c; 6 w gD; 7-9 dm
-// routed to the nearest edge (zero for the other two); 10 dL/do_F; 11 one; with the side array
-// 12-14 w gN_c and 15 dL/dsigma_F.
-constexpr int RING_CAP = 32;
+// Backward scratch per warp: a queue of contributing (face, pixel) entries found by the visits,
+// the pixels' back-to-front state, and the ring of one batch's rows.  A ring row holds the
+// factors of one entry; row words: 0-2 barycentrics l_k; 3-5 w gC_c; 6 w gD; 7-9 dm routed to
+// the nearest edge (zero for the other two); 10 dL/do_F; 11 one; with the side array 12-14 w gN_c
+// and 15 dL/dsigma_F.
+constexpr int RING_CAP = 32;   // rows: one batch of entries, one per lane
+constexpr int QUEUE_CAP = 64;  // entries: under 32 waiting plus one visit's up to 32
 template <bool AUX>
 struct Ring {
   static constexpr int EW = AUX ? 16 : 12;
-  static constexpr int BYTES_PER_WARP = RING_CAP * (EW * 4 + 8);
+  static constexpr int BYTES_PER_WARP = RING_CAP * EW * 4 + 32 * 8 + QUEUE_CAP * 2;
 };
 
 template <int TW, int TH>
@@ -171,7 +172,7 @@ __device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, 
 // widened by 0.01 px, is not entirely outside one of the three edges.  Conservative: a pixel with
 // a positive window always keeps its sub-block's bit.
 template <int TW, int TH>
-__device__ __forceinline__ void stage_masks(const float* rb, uint32_t* smask, int cnt, int X0, int Y0) {
+__device__ __forceinline__ void stage_masks(const float* rb, uint16_t* smask, int cnt, int X0, int Y0) {
   constexpr int NSBX = TW / 8;
   for (int j = threadIdx.x; j < cnt; j += TW * TH) {
     const float* r = rb + j * TS_REC_WORDS;
@@ -200,7 +201,7 @@ __device__ __forceinline__ void stage_masks(const float* rb, uint32_t* smask, in
         }
       }
     }
-    smask[j] = mask;
+    smask[j] = (uint16_t)mask;
   }
 }
 
@@ -251,14 +252,13 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
       stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
-      for (int j = threadIdx.x; j < cnt; j += TW * TH) {
-        fm.cm[b][j] = 0u;
-        fm.cv[b][j] = 0u;
-      }
+      if (a.cov)
+        for (int j = threadIdx.x; j < cnt; j += TW * TH) fm.cv[b][j] = 0u;
       __syncthreads();
       if (warp == 0 && st + 1 < nst) issue_stage<AUX>(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase, nbase);
       for (int q = 0; q * 32 < cnt; ++q) {
         const int jq = q * 32 + lane;
+        unsigned lm = 0;  // lane L: this warp's pixels that blended face q * 32 + L
         unsigned bits = __ballot_sync(FULL, jq < cnt && ((sm.smask[b][min(jq, cnt - 1)] >> warp) & 1u));
         while (bits) {
           const int j = q * 32 + __ffs(bits) - 1;
@@ -297,21 +297,21 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
               }
             }
           }
-          // the backward revisits exactly the (warp, face) pairs that blended somewhere
+          // the backward takes exactly these (face, pixel) contributions
           const unsigned bl = __ballot_sync(FULL, blended);
-          if (bl && lane == 0) {
-            atomicOr(&fm.cm[b][j], 1u << warp);
-            if (a.cov) atomicAdd(&fm.cv[b][j], (unsigned)__popc(bl));
-          }
+          if (lane == (j & 31)) lm = bl;
+          if (bl && lane == 0 && a.cov) atomicAdd(&fm.cv[b][j], (unsigned)__popc(bl));
         }
+        if (jq < cnt) a.lmask[(size_t)(rg.x + (uint32_t)(st * S + jq)) * (TW * TH / 32) + warp] = lm;
       }
       const int alive = __syncthreads_count(!done);
-      for (int j = threadIdx.x; j < cnt; j += TW * TH) {
-        a.cmask[rg.x + st * S + j] = (uint16_t)fm.cm[b][j];
-        if (a.cov && fm.cv[b][j]) {  // face m of the record's slot m * V + view
-          const uint32_t slot = __float_as_uint(rb[j * TS_REC_WORDS + R_SLOT]);
-          const long long m = (long long)(slot / (uint32_t)a.V);
-          if (m < a.M) atomicAdd(a.cov + (long long)g.view * a.M + m, fm.cv[b][j]);
+      if (a.cov) {
+        for (int j = threadIdx.x; j < cnt; j += TW * TH) {
+          if (fm.cv[b][j]) {  // face m of the record's slot m * V + view
+            const uint32_t slot = __float_as_uint(rb[j * TS_REC_WORDS + R_SLOT]);
+            const long long m = (long long)(slot / (uint32_t)a.V);
+            if (m < a.M) atomicAdd(a.cov + (long long)g.view * a.M + m, fm.cv[b][j]);
+          }
         }
       }
       if (alive == 0) {
@@ -380,28 +380,6 @@ __device__ __forceinline__ bool ring_word(int lane, int& ia, int& ib) {
   return true;
 }
 
-// Sum each group's rows of the warp's ring into the group's face accumulator (lane L: word L).
-template <bool AUX>
-__device__ __forceinline__ void ring_flush(const RenderArgs& a, const float* ring, const uint2* gh, int ng, int lane,
-                                           int ia, int ib, bool has) {
-  constexpr int EW = Ring<AUX>::EW;
-  __syncwarp();
-  int e = 0;
-  for (int g = 0; g < ng; ++g) {
-    const uint2 h = gh[g];
-    float sum = 0.f;
-    for (; e < (int)h.y; ++e) sum = fmaf(ring[e * EW + ia], ring[e * EW + ib], sum);
-    if (has && sum != 0.f) {
-      if ((long long)h.x < a.VM) {
-        atomicAdd(a.grad + (size_t)h.x * TS_GRAD_WORDS + lane, sum);
-      } else {
-        atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
-      }
-    }
-  }
-  __syncwarp();
-}
-
 template <int TW, int TH, bool AUX>
 __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
                                          int& seq) {
@@ -450,14 +428,17 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
     const float4* nbase = AUX ? a.aux + (size_t)g.view * (size_t)a.M : nullptr;
     if (warp == 0) issue_stage<AUX>(a, smrec, sm.bar, seq & 1, nst - 1, rg.x, n, vbase, nbase);
     constexpr int EW = Ring<AUX>::EW;
-    float* ring = reinterpret_cast<float*>(smrec + (size_t)2 * S * (AUX ? 9 : 8)) + warp * RING_CAP * EW;
-    uint2* gh = reinterpret_cast<uint2*>(reinterpret_cast<float*>(smrec + (size_t)2 * S * (AUX ? 9 : 8)) +
-                                         (TW * TH / 32) * RING_CAP * EW) +
-                warp * RING_CAP;
+    unsigned char* wbase = reinterpret_cast<unsigned char*>(smrec + (size_t)2 * S * (AUX ? 9 : 8)) +
+                           (size_t)warp * Ring<AUX>::BYTES_PER_WARP;
+    float* ring = reinterpret_cast<float*>(wbase);
+    float2* pst = reinterpret_cast<float2*>(wbase + RING_CAP * EW * 4);  // per pixel lane: (T, S)
+    uint16_t* queue = reinterpret_cast<uint16_t*>(wbase + RING_CAP * EW * 4 + 32 * 8);  // face << 5 | pixel
+    pst[lane] = make_float2(T, Sacc);
     int ia, ib;
     const bool has = ring_word<AUX>(lane, ia, ib);
     const unsigned below = (1u << lane) - 1u;
-    int fill = 0, ng = 0;  // the ring's rows and groups in use (the same in every lane)
+    const int xw = g.x - (lane & 7), yw = g.y - (lane >> 3);  // the warp's first pixel
+    int head = 0, fill = 0;  // the queue's entries (the same in every lane)
     for (int k = 0; k < nst; ++k) {
       const int st = nst - 1 - k;
       const int b = seq & 1;
@@ -466,85 +447,144 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
       ++seq;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
-      // the forward's record of which warps blended each face (positions below the tile's
-      // largest list position after a contribution were all written by the forward)
-      for (int j = threadIdx.x; j < cnt; j += TW * TH) sm.smask[b][j] = a.cmask[rg.x + st * S + j];
-      __syncthreads();
       if (warp == 0 && k + 1 < nst) issue_stage<AUX>(a, smrec, sm.bar, b ^ 1, st - 1, rg.x, n, vbase, nbase);
-      // this warp visits only the stage's faces it blended in the forward (back to front)
-      for (int qq = (cnt - 1) >> 5; qq >= 0; --qq) {
-        const int jq = qq * 32 + lane;
-        unsigned bits = __ballot_sync(FULL, jq < cnt && ((sm.smask[b][min(jq, cnt - 1)] >> warp) & 1u));
-        while (bits) {
+      // The forward's lane masks (positions below the tile's largest list position after a
+      // contribution were all written by it) give, per face, the pixels of this warp that blended
+      // it.  Visits back to front queue them; every 32 entries, and at the end of the stage, the
+      // lanes take one entry each.
+      const uint32_t* lmrow = a.lmask + (size_t)(rg.x + (uint32_t)(st * S)) * (TW * TH / 32) + warp;
+      int qq = (cnt - 1) >> 5;
+      unsigned lmc = qq * 32 + lane < cnt ? lmrow[(size_t)(qq * 32 + lane) * (TW * TH / 32)] : 0u;
+      unsigned bits = __ballot_sync(FULL, lmc != 0u);
+      for (;;) {
+        while (!bits && qq > 0) {
+          --qq;
+          lmc = lmrow[(size_t)(qq * 32 + lane) * (TW * TH / 32)];
+          bits = __ballot_sync(FULL, lmc != 0u);
+        }
+        const bool more = bits != 0;
+        if (more) {
           const int hb = 31 - __clz(bits);
           bits &= ~(1u << hb);
           const int j = qq * 32 + hb;
+          const unsigned cbm = __shfl_sync(FULL, lmc, hb);
+          if ((cbm >> lane) & 1u) queue[(head + fill + __popc(cbm & below)) & (QUEUE_CAP - 1)] = (uint16_t)((j << 5) | lane);
+          fill += __popc(cbm);
+        }
+        if (fill >= 32 || (!more && fill > 0)) {
+          const int ne = min(fill, 32);
+          __syncwarp();
+          // -- one entry per lane: face j at pixel lane p ---------------------------------------
+          const bool act = lane < ne;
+          const unsigned ent = queue[(head + lane) & (QUEUE_CAP - 1)];
+          const int j = act ? (int)(ent >> 5) : 0;
+          const int p = act ? (int)(ent & 31u) : lane;
           const float* r = rb + j * TS_REC_WORDS;
-          const int pos = st * S + j;
-          bool cb = false;
-          TsPix e;
-          float I = 0.f, al = 0.f;
+          const float px = (float)(xw + (p & 7)) + 0.5f, py = (float)(yw + (p >> 3)) + 0.5f;
           const float sig = (AUX && a.face_sigma) ? nb[j].w : a.sigma;
-          if (pos < nl) {
-            e = ts_eval_edges(r, g.px, g.py);
-            if (e.m > 0.f) {
-              I = ts_window(e.m, sig);
-              al = fminf(r[R_OF] * I, a.alpha_max);
-              cb = al >= a.alpha_min;
+          const TsPix e = ts_eval_edges(r, px, py);
+          const float I = act ? ts_window(e.m, sig) : 0.f;
+          const float al = fminf(r[R_OF] * I, a.alpha_max);
+          const float ro = ts_rcp_approx(1.f - al);  // 1 - al >= 1 - alpha_max
+          // entries of the same pixel, in queue (back-to-front) order; each lane replays its
+          // pixel's recurrence T <- T / (1 - alpha) over the earlier ones and itself, in order
+          const unsigned peers = __match_any_sync(FULL, act ? p : 32 + lane);
+          const int K = (int)__reduce_max_sync(FULL, (unsigned)__popc(peers));
+          const float2 st0 = pst[p];
+          float Tn = st0.x;
+          {
+            unsigned rem = peers;
+            for (int i = 0; i < K; ++i) {
+              const int src = rem ? __ffs(rem) - 1 : 31;
+              const bool use = rem != 0 && src <= lane;
+              rem &= rem - 1;
+              const float f = __shfl_sync(FULL, ro, src);
+              if (use) Tn *= f;
             }
           }
-          const unsigned cbm = __ballot_sync(FULL, cb);
-          if (!cbm) continue;
-          const int nc = __popc(cbm);
-          if (fill + nc > RING_CAP) {
-            ring_flush<AUX>(a, ring, gh, ng, lane, ia, ib, has);
-            fill = 0;
-            ng = 0;
+          const float qC0 = __shfl_sync(FULL, gC0, p), qC1 = __shfl_sync(FULL, gC1, p);
+          const float qC2 = __shfl_sync(FULL, gC2, p), qD = __shfl_sync(FULL, gD, p);
+          const float qA = __shfl_sync(FULL, gA, p);
+          float qN0 = 0.f, qN1 = 0.f, qN2 = 0.f;
+          if constexpr (AUX) {
+            qN0 = __shfl_sync(FULL, gN0, p);
+            qN1 = __shfl_sync(FULL, gN1, p);
+            qN2 = __shfl_sync(FULL, gN2, p);
           }
-          if (cb) {
-            const float oma = 1.f - al;  // >= 1 - alpha_max
-            const float ro = ts_rcp_approx(oma);
-            const float Tn = T * ro;
-            const float invD = r[R_INVD];
-            const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
-            const float c0 = l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2];
-            const float c1 = l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1];
-            const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
-            const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
-            float val = gC0 * c0 + gC1 * c1 + gC2 * c2 + gD * z + gA;
-            if (AUX && a.normals) {
-              const float4 nn = nb[j];
-              val += gN0 * nn.x + gN1 * nn.y + gN2 * nn.z;
+          const float invD = r[R_INVD];
+          const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
+          const float c0 = l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2];
+          const float c1 = l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1];
+          const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
+          const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
+          float val = qC0 * c0 + qC1 * c1 + qC2 * c2 + qD * z + qA;
+          if (AUX && a.normals) {
+            const float4 nn = nb[j];
+            val += qN0 * nn.x + qN1 * nn.y + qN2 * nn.z;
+          }
+          const float w = al * Tn;
+          const float add = val * al * Tn;  // this face's term of the suffix sum S seen by earlier faces
+          float Sn = st0.y;
+          {
+            unsigned rem = peers;
+            for (int i = 0; i < K; ++i) {
+              const int src = rem ? __ffs(rem) - 1 : 31;
+              const bool use = rem != 0 && src < lane;
+              rem &= rem - 1;
+              const float f = __shfl_sync(FULL, add, src);
+              if (use) Sn += f;
             }
-            const float dal = val * Tn - Sacc * ro;
-            Sacc += val * al * Tn;
-            T = Tn;
-            const float w = al * Tn;
-            float go = 0.f, dm = 0.f, gs = 0.f;
-            const float oF = r[R_OF];
-            if (!(oF * I > a.alpha_max)) {
-              go = dal * I;
-              const float dI = dal * oF;
-              // I >= alpha_min / o_F here, far from zero
-              dm = (sig == 0.5f) ? dI * 0.5f * ts_rcp_approx(I) : dI * sig * I / e.m;
-              if constexpr (AUX) {  // dL/dsigma_F = dL/dalpha o_F I ln(ratio)
-                if (a.face_sigma) gs = dI * I * logf(e.m);
-              }
+          }
+          __syncwarp();  // every lane has read its pixel's state before the last entries replace it
+          if (act && (peers >> lane) == 1u) pst[p] = make_float2(Tn, Sn + add);
+          const float dal = val * Tn - Sn * ro;
+          float go = 0.f, dm = 0.f, gs = 0.f;
+          const float oF = r[R_OF];
+          if (!(oF * I > a.alpha_max)) {
+            go = dal * I;
+            const float dI = dal * oF;
+            // I >= alpha_min / o_F for a contributing entry, far from zero
+            dm = (sig == 0.5f) ? dI * 0.5f * ts_rcp_approx(I) : dI * sig * I / e.m;
+            if constexpr (AUX) {  // dL/dsigma_F = dL/dalpha o_F I ln(ratio)
+              if (a.face_sigma) gs = dI * I * logf(e.m);
             }
-            float4* row = reinterpret_cast<float4*>(ring + (fill + __popc(cbm & below)) * EW);
-            row[0] = make_float4(l0, l1, l2, gC0 * w);
-            row[1] = make_float4(gC1 * w, gC2 * w, gD * w, e.arg == 0 ? dm : 0.f);
+          }
+          if (act) {
+            float4* row = reinterpret_cast<float4*>(ring + lane * EW);
+            row[0] = make_float4(l0, l1, l2, qC0 * w);
+            row[1] = make_float4(qC1 * w, qC2 * w, qD * w, e.arg == 0 ? dm : 0.f);
             row[2] = make_float4(e.arg == 1 ? dm : 0.f, e.arg == 2 ? dm : 0.f, go, 1.f);
-            if constexpr (AUX) row[3] = make_float4(gN0 * w, gN1 * w, gN2 * w, gs);
+            if constexpr (AUX) row[3] = make_float4(qN0 * w, qN1 * w, qN2 * w, gs);
             ++contrib;
           }
-          fill += nc;
-          if (lane == 0) gh[ng] = make_uint2(__float_as_uint(r[R_SLOT]), (unsigned)fill);
-          ++ng;
+          // the batch's faces are runs of consecutive entries; lane L sums word L over each run
+          const int jprev = __shfl_up_sync(FULL, j, 1);  // in every lane, outside any condition
+          const unsigned starts = __ballot_sync(FULL, act && (lane == 0 || j != jprev));
+          __syncwarp();
+          unsigned rem = starts;
+          while (rem) {
+            const int s0 = __ffs(rem) - 1;
+            rem &= rem - 1;
+            const int s1 = rem ? __ffs(rem) - 1 : ne;
+            const int jg = __shfl_sync(FULL, j, s0);
+            float sum = 0.f;
+            for (int q = s0; q < s1; ++q) sum = fmaf(ring[q * EW + ia], ring[q * EW + ib], sum);
+            if (has && sum != 0.f) {
+              const uint32_t slot = __float_as_uint(rb[jg * TS_REC_WORDS + R_SLOT]);
+              if ((long long)slot < a.VM) {
+                atomicAdd(a.grad + (size_t)slot * TS_GRAD_WORDS + lane, sum);
+              } else {
+                atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
+              }
+            }
+          }
+          __syncwarp();
+          head += ne;
+          fill -= ne;
         }
+        if (!more && fill == 0) break;
       }
     }
-    if (ng) ring_flush<AUX>(a, ring, gh, ng, lane, ia, ib, has);
   }
   count_add(&a.hdr->bwd_contrib, contrib);
   return ok;
@@ -668,7 +708,7 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.S = p->prm.tris_per_stage;
   a.hdr = w.hdr;
   a.counter = &w.hdr->tile_counter;
-  a.cmask = w.cmask;
+  a.lmask = w.lmask;
   a.aux = w.aux;
   a.normals = p->normals;
   a.face_sigma = p->face_sigma;

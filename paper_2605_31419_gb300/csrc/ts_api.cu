@@ -167,7 +167,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_grad = take((size_t)VM * TS_GRAD_WORDS * 4);
   p->o_pose = take((size_t)n_views * p->n_pose_blocks * 6 * 4);
   p->o_loss = take((size_t)n_views * p->n_loss_blocks * 2 * 4);
-  p->o_cmask = take((size_t)cap * 2);
+  p->o_lmask = take((size_t)cap * (size_t)(prm->tile_w * prm->tile_h / 32) * 4);
   p->o_pho = take((size_t)n_views * p->n_pho_blocks * 3 * 4);
   p->o_equi = take((size_t)ts_equi_blocks(n_faces) * 4);
   p->o_aux = take((p->normals || p->face_sigma) ? (size_t)VM * 16 : 0);

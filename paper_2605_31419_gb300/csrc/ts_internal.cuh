@@ -91,7 +91,7 @@ struct TsPlanImpl {
   bool face_sigma;   // TS_FLAG_FACE_SIGMA
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
-      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_cmask, o_pho, o_equi, o_aux, o_nloss,
+      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_lmask, o_pho, o_equi, o_aux, o_nloss,
       o_cov, total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
@@ -126,7 +126,7 @@ struct TsWs {
                // (TS_FLAG_FACE_SIGMA) in .w; null without either flag
   float* nloss;  // per (view, 2048-pixel block): partial sums of the normal loss
   uint32_t* cov;  // per (view, face): pixels blended by the forward (TS_FLAG_STATS), else null
-  uint16_t* cmask;  // per sorted pair: the warps of its tile that blended the face in the forward
+  uint32_t* lmask;  // per sorted pair and warp of its tile: the lanes (pixels) that blended the face in the forward
 };
 
 inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
@@ -158,7 +158,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.aux = (p->normals || p->face_sigma) ? (float4*)(b + p->o_aux) : nullptr;
   w.nloss = (float*)(b + p->o_nloss);
   w.cov = p->stats ? (uint32_t*)(b + p->o_cov) : nullptr;
-  w.cmask = (uint16_t*)(b + p->o_cmask);
+  w.lmask = (uint32_t*)(b + p->o_lmask);
   return w;
 }
 
