@@ -227,8 +227,8 @@ __global__ void k_pose_adam(ts_pose* poses, const float* __restrict__ dtau, floa
 }
 
 // Failure-detection probe: one thread waits on an mbarrier phase that nothing completes (no
-// arrival, no copy in flight), with the same bounded wait the raster kernels use, and latches the
-// timeout bit when the limit passes.
+// arrival, no copy in flight) with the library's bounded wait, and latches the timeout bit when
+// the limit passes.
 __global__ void k_timeout_probe(TsDevHeader* hdr, unsigned long long limit_ns) {
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x != 0) return;

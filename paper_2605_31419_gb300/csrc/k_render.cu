@@ -1,11 +1,11 @@
 // k_render.cu -- Eq. 3-4 forward blend and its adjoint, one CTA per (view, tile) at a time.
 //
-// Staging: the tile's depth-sorted face ids select 128-byte records that one warp copies into
-// shared memory with TMA bulk copies (cp.async.bulk, one per record) completing on an mbarrier;
-// two buffers alternate so the next stage streams in while the current one is blended.  Each
-// warp owns an 8 x 4 pixel sub-block of the tile; per stage, a mask per record says which
-// sub-blocks can contain one of the face's covered pixel centres, and each warp walks only the
-// set bits of its own ballot over the stage.
+// Staging: the tile's depth-sorted face ids select 128-byte records that the CTA copies into
+// shared memory with 16-byte cp.async copies (a warp moves four records per instruction; one
+// bulk copy per record was bound by its per-request cost); two buffers alternate so the next
+// stage streams in while the current one is blended.  Each warp owns an 8 x 4 pixel sub-block of
+// the tile; per stage, a mask per record says which sub-blocks can contain one of the face's
+// covered pixel centres, and each warp walks only the set bits of its own ballot over the stage.
 //
 // Forward: per pixel, front to back: window (Eq. 3) from cancellation-free edge functions,
 // alpha = min(alpha_max, o_F I), skip below alpha_min, stop before the face that would take T
@@ -81,7 +81,6 @@ constexpr int raster_min_blocks(int threads) {
 
 // Shared state of a render CTA.
 struct RenderSmem {
-  uint64_t bar[2];
   uint16_t smask[2][128];  // per staged face, the warps (sub-blocks) that visit it
   int view;
   int nmax;
@@ -145,26 +144,31 @@ __device__ __forceinline__ TileGeom<TW, TH> tile_geom(const RenderArgs& a, long 
   return g;
 }
 
-// Warp 0 issues the bulk copies of stage `st` (records [st*S, st*S + cnt) of the tile's list)
-// into buffer `b`; with AUX also each record's 16-byte side entry (normal, sigma_F), after both
-// record buffers.
+// Every thread of the CTA copies 16-byte chunks of stage `st` (records [st*S, st*S + cnt) of the
+// tile's list) into buffer `b` with cp.async, eight chunks per record and, with the side array,
+// one more for the record's side entry (normal, sigma_F) after both record buffers; one commit
+// group per stage.  A warp moves four records per instruction, and no copy engine request is
+// made per record.
 template <bool AUX>
-__device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, uint64_t* bar, int b, int st,
-                                            uint32_t start, int n, const float4* vbase, const float4* nbase) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void issue_stage(const RenderArgs& a, float4* smrec, int b, int st, uint32_t start, int n,
+                                            const float4* vbase, const float4* nbase, int nthreads) {
   const int S = a.S;
   const int cnt = min(S, n - st * S);
-  if (lane == 0) ts_mbar_arrive_expect_tx(&bar[b], (uint32_t)cnt * (AUX ? 144u : 128u));
-  __syncwarp();
-  for (int j = lane; j < cnt; j += 32) {
+  constexpr int PER = AUX ? 9 : 8;
+  for (int i = threadIdx.x; i < cnt * PER; i += nthreads) {
+    const int j = i / PER, c = i - j * PER;
     uint32_t id = __ldg(a.ids + start + (uint32_t)(st * S + j));
     if ((long long)id >= a.M) {  // never expected: record the fault and stage an in-bounds record
       atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
       id = 0;
     }
-    ts_bulk_g2s(smrec + ((size_t)b * S + j) * 8, vbase + (size_t)id * 8, 128u, &bar[b]);
-    if (AUX) ts_bulk_g2s(smrec + (size_t)2 * S * 8 + (size_t)b * S + j, nbase + id, 16u, &bar[b]);
+    if (!AUX || c < 8) {
+      ts_cp_async16(smrec + ((size_t)b * S + j) * 8 + c, vbase + (size_t)id * 8 + c);
+    } else {
+      ts_cp_async16(smrec + (size_t)2 * S * 8 + (size_t)b * S + j, nbase + id);
+    }
   }
+  ts_cp_async_commit();
 }
 
 // For each staged record, the mask of warp sub-blocks (8 x 4 pixels) that can contain one of its
@@ -210,23 +214,15 @@ __device__ __forceinline__ void count_add(unsigned long long* ctr, unsigned v) {
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
 }
 
-// Wait for stage sequence number `seq` (buffer seq & 1, phase (seq >> 1) & 1) in every thread.
-// Returns false on timeout (after latching the error and letting the late copies land).
-__device__ __forceinline__ bool wait_stage(const RenderArgs& a, RenderSmem& sm, int seq) {
-  const bool ok = ts_mbar_wait(&sm.bar[seq & 1], (uint32_t)(seq >> 1) & 1u);
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) {
-      atomicOr(&a.hdr->error_bits, TS_ERRBIT_TIMEOUT);
-      ts_mbar_wait(&sm.bar[seq & 1], (uint32_t)(seq >> 1) & 1u);
-    }
-    return false;
-  }
-  return true;
+// Wait for the stage issued last: each thread's copies (they always complete), then a barrier.
+__device__ __forceinline__ void wait_stage() {
+  ts_cp_async_wait_all();
+  __syncthreads();
 }
 
-// Forward of one tile; seq counts the stages this CTA has waited for so far (mbarrier phases).
+// Forward of one tile; seq counts the stages this CTA has staged so far (buffer seq & 1 is next).
 template <int TW, int TH, bool AUX>
-__device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
+__device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
                                          FwdMasks& fm, int& seq) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -237,17 +233,16 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
   int nl = 0;
   bool done = !g.inimg;
   unsigned contrib = 0;
-  bool ok = true;
   if (n > 0) {
     const int S = a.S;
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
     const float4* nbase = AUX ? a.aux + (size_t)g.view * (size_t)a.M : nullptr;
-    if (warp == 0) issue_stage<AUX>(a, smrec, sm.bar, seq & 1, 0, rg.x, n, vbase, nbase);
+    issue_stage<AUX>(a, smrec, seq & 1, 0, rg.x, n, vbase, nbase, TW * TH);
     for (int st = 0; st < nst; ++st) {
       const int b = seq & 1;
       const int cnt = min(S, n - st * S);
-      if (!wait_stage(a, sm, seq)) { ok = false; break; }
+      wait_stage();
       ++seq;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
@@ -255,7 +250,7 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
       if (a.cov)
         for (int j = threadIdx.x; j < cnt; j += TW * TH) fm.cv[b][j] = 0u;
       __syncthreads();
-      if (warp == 0 && st + 1 < nst) issue_stage<AUX>(a, smrec, sm.bar, b ^ 1, st + 1, rg.x, n, vbase, nbase);
+      if (st + 1 < nst) issue_stage<AUX>(a, smrec, b ^ 1, st + 1, rg.x, n, vbase, nbase, TW * TH);
       for (int q = 0; q * 32 < cnt; ++q) {
         const int jq = q * 32 + lane;
         unsigned lm = 0;  // lane L: this warp's pixels that blended face q * 32 + L
@@ -315,8 +310,8 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
         }
       }
       if (alive == 0) {
-        if (st + 1 < nst) {  // a prefetched stage is in flight: consume its phase before leaving
-          if (!wait_stage(a, sm, seq)) { ok = false; break; }
+        if (st + 1 < nst) {  // a prefetched stage is in flight: let it land before leaving
+          wait_stage();
           ++seq;
         }
         break;
@@ -324,7 +319,7 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
     }
   }
   count_add(&a.hdr->fwd_contrib, contrib);
-  if (ok && g.inimg) {
+  if (g.inimg) {
     const long long HW = (long long)g.vw.W * g.vw.H;
     const long long pi = (long long)g.y * g.vw.W + g.x;
     const long long o = g.vw.pix_off + pi;
@@ -345,7 +340,6 @@ __device__ __forceinline__ bool fwd_tile(const RenderArgs& a, long long tile, fl
     a.tfin[o] = T;
     a.nlast[o] = nl;
   }
-  return ok;
 }
 
 // Lane `lane`'s gradient word as a product of two ring-row words (ia x ib); false for a lane with
@@ -380,8 +374,26 @@ __device__ __forceinline__ bool ring_word(int lane, int& ia, int& ib) {
   return true;
 }
 
+// The edge evaluation of ts_eval_edges from the record's first four 16-byte groups (one vector
+// load each; lanes holding different faces then conflict only within a quarter warp).
+static_assert(R_U0 == 0 && R_V0 == 3 && R_V1 == 4 && R_E0X == 6 && R_E1X == 8 && R_E2X == 10 && R_K0 == 12 &&
+                  R_INVD == 15 && R_OF == 16 && R_C0 == 17 && R_C1 == 20 && R_C2 == 23 && R_Z0 == 26 && R_Z2 == 28,
+              "record layout assumed by the vector loads");
+__device__ __forceinline__ TsPix eval_edges_v(float4 q0, float4 q1, float4 q2, float4 q3, float px, float py) {
+  TsPix o;
+  o.cr0 = ts_det2(q1.z, q1.w, px - q0.x, py - q0.w);
+  o.cr1 = ts_det2(q2.x, q2.y, px - q0.y, py - q1.x);
+  o.cr2 = ts_det2(q2.z, q2.w, px - q0.z, py - q1.y);
+  const float e0 = o.cr0 * q3.x, e1 = o.cr1 * q3.y, e2 = o.cr2 * q3.z;
+  o.m = e0;
+  o.arg = 0;
+  if (e1 < o.m) { o.m = e1; o.arg = 1; }
+  if (e2 < o.m) { o.m = e2; o.arg = 2; }
+  return o;
+}
+
 template <int TW, int TH, bool AUX>
-__device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
+__device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
                                          int& seq) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -420,13 +432,12 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
   // run it after the last ts_bin
   const int n = min(sm.nmax, (int)(rg.y - rg.x));
   unsigned contrib = 0;
-  bool ok = true;
   if (n > 0) {
     const int S = a.S;
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
     const float4* nbase = AUX ? a.aux + (size_t)g.view * (size_t)a.M : nullptr;
-    if (warp == 0) issue_stage<AUX>(a, smrec, sm.bar, seq & 1, nst - 1, rg.x, n, vbase, nbase);
+    issue_stage<AUX>(a, smrec, seq & 1, nst - 1, rg.x, n, vbase, nbase, TW * TH);
     constexpr int EW = Ring<AUX>::EW;
     unsigned char* wbase = reinterpret_cast<unsigned char*>(smrec + (size_t)2 * S * (AUX ? 9 : 8)) +
                            (size_t)warp * Ring<AUX>::BYTES_PER_WARP;
@@ -443,18 +454,18 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
       const int st = nst - 1 - k;
       const int b = seq & 1;
       const int cnt = min(S, n - st * S);
-      if (!wait_stage(a, sm, seq)) { ok = false; break; }
-      ++seq;
-      const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
-      const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
-      if (warp == 0 && k + 1 < nst) issue_stage<AUX>(a, smrec, sm.bar, b ^ 1, st - 1, rg.x, n, vbase, nbase);
       // The forward's lane masks (positions below the tile's largest list position after a
       // contribution were all written by it) give, per face, the pixels of this warp that blended
       // it.  Visits back to front queue them; every 32 entries, and at the end of the stage, the
-      // lanes take one entry each.
+      // lanes take one entry each.  The last chunk's masks load while the stage's copies land.
       const uint32_t* lmrow = a.lmask + (size_t)(rg.x + (uint32_t)(st * S)) * (TW * TH / 32) + warp;
       int qq = (cnt - 1) >> 5;
       unsigned lmc = qq * 32 + lane < cnt ? lmrow[(size_t)(qq * 32 + lane) * (TW * TH / 32)] : 0u;
+      wait_stage();
+      ++seq;
+      const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
+      const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
+      if (k + 1 < nst) issue_stage<AUX>(a, smrec, b ^ 1, st - 1, rg.x, n, vbase, nbase, TW * TH);
       unsigned bits = __ballot_sync(FULL, lmc != 0u);
       for (;;) {
         while (!bits && qq > 0) {
@@ -479,12 +490,15 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
           const unsigned ent = queue[(head + lane) & (QUEUE_CAP - 1)];
           const int j = act ? (int)(ent >> 5) : 0;
           const int p = act ? (int)(ent & 31u) : lane;
-          const float* r = rb + j * TS_REC_WORDS;
+          const float4* r4 = reinterpret_cast<const float4*>(rb + j * TS_REC_WORDS);
           const float px = (float)(xw + (p & 7)) + 0.5f, py = (float)(yw + (p >> 3)) + 0.5f;
           const float sig = (AUX && a.face_sigma) ? nb[j].w : a.sigma;
-          const TsPix e = ts_eval_edges(r, px, py);
+          const float4 q3 = r4[3];  // k_0, k_1, k_2, invD
+          const TsPix e = eval_edges_v(r4[0], r4[1], r4[2], q3, px, py);
+          const float4 q4 = r4[4];  // o_F, colour of vertex 0
+          const float oF = q4.x;
           const float I = act ? ts_window(e.m, sig) : 0.f;
-          const float al = fminf(r[R_OF] * I, a.alpha_max);
+          const float al = fminf(oF * I, a.alpha_max);
           const float ro = ts_rcp_approx(1.f - al);  // 1 - al >= 1 - alpha_max
           // entries of the same pixel, in queue (back-to-front) order; each lane replays its
           // pixel's recurrence T <- T / (1 - alpha) over the earlier ones and itself, in order
@@ -511,12 +525,16 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             qN1 = __shfl_sync(FULL, gN1, p);
             qN2 = __shfl_sync(FULL, gN2, p);
           }
-          const float invD = r[R_INVD];
+          const float invD = q3.w;
           const float l0 = e.cr1 * invD, l1 = e.cr2 * invD, l2 = e.cr0 * invD;
-          const float c0 = l0 * r[R_C0] + l1 * r[R_C1] + l2 * r[R_C2];
-          const float c1 = l0 * r[R_C0 + 1] + l1 * r[R_C1 + 1] + l2 * r[R_C2 + 1];
-          const float c2 = l0 * r[R_C0 + 2] + l1 * r[R_C1 + 2] + l2 * r[R_C2 + 2];
-          const float z = l0 * r[R_Z0] + l1 * r[R_Z1] + l2 * r[R_Z2];
+          const float4 q5 = r4[5], q6 = r4[6];  // colours of vertices 1 and 2, depths z_0, z_1
+          const float4 q7 = r4[7];
+          const float z2 = q7.x;
+          const uint32_t slot = __float_as_uint(q7.w);
+          const float c0 = l0 * q4.y + l1 * q5.x + l2 * q5.w;
+          const float c1 = l0 * q4.z + l1 * q5.y + l2 * q6.x;
+          const float c2 = l0 * q4.w + l1 * q5.z + l2 * q6.y;
+          const float z = l0 * q6.z + l1 * q6.w + l2 * z2;
           float val = qC0 * c0 + qC1 * c1 + qC2 * c2 + qD * z + qA;
           if (AUX && a.normals) {
             const float4 nn = nb[j];
@@ -539,7 +557,6 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
           if (act && (peers >> lane) == 1u) pst[p] = make_float2(Tn, Sn + add);
           const float dal = val * Tn - Sn * ro;
           float go = 0.f, dm = 0.f, gs = 0.f;
-          const float oF = r[R_OF];
           if (!(oF * I > a.alpha_max)) {
             go = dal * I;
             const float dI = dal * oF;
@@ -566,13 +583,13 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
             const int s0 = __ffs(rem) - 1;
             rem &= rem - 1;
             const int s1 = rem ? __ffs(rem) - 1 : ne;
-            const int jg = __shfl_sync(FULL, j, s0);
+            const uint32_t sl = __shfl_sync(FULL, slot, s0);
             float sum = 0.f;
+#pragma unroll 4
             for (int q = s0; q < s1; ++q) sum = fmaf(ring[q * EW + ia], ring[q * EW + ib], sum);
             if (has && sum != 0.f) {
-              const uint32_t slot = __float_as_uint(rb[jg * TS_REC_WORDS + R_SLOT]);
-              if ((long long)slot < a.VM) {
-                atomicAdd(a.grad + (size_t)slot * TS_GRAD_WORDS + lane, sum);
+              if ((long long)sl < a.VM) {
+                atomicAdd(a.grad + (size_t)sl * TS_GRAD_WORDS + lane, sum);
               } else {
                 atomicOr(&a.hdr->error_bits, TS_ERRBIT_BOUNDS);
               }
@@ -587,16 +604,6 @@ __device__ __forceinline__ bool bwd_tile(const RenderArgs& a, long long tile, fl
     }
   }
   count_add(&a.hdr->bwd_contrib, contrib);
-  return ok;
-}
-
-__device__ __forceinline__ void init_bars(RenderSmem& sm) {
-  if (threadIdx.x == 0) {
-    ts_mbar_init(&sm.bar[0], 1);
-    ts_mbar_init(&sm.bar[1], 1);
-    ts_fence_mbar_init();
-  }
-  __syncthreads();
 }
 
 // Next tile of a persistent CTA (the same value in every thread), or -1 when none is left.
@@ -612,28 +619,26 @@ __global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ RenderSmem sm;
   __shared__ FwdMasks fm;
-  init_bars(sm);
   int seq = 0;
   if (!PERSIST) {
     fwd_tile<TW, TH, AUX>(a, blockIdx.x, smrec, sm, fm, seq);
     return;
   }
   for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    if (!fwd_tile<TW, TH, AUX>(a, t, smrec, sm, fm, seq)) return;
+    fwd_tile<TW, TH, AUX>(a, t, smrec, sm, fm, seq);
 }
 
 template <int TW, int TH, bool PERSIST, bool AUX>
 __global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_bwd(RenderArgs a) {
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ RenderSmem sm;
-  init_bars(sm);
   int seq = 0;
   if (!PERSIST) {
     bwd_tile<TW, TH, AUX>(a, blockIdx.x, smrec, sm, seq);
     return;
   }
   for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    if (!bwd_tile<TW, TH, AUX>(a, t, smrec, sm, seq)) return;
+    bwd_tile<TW, TH, AUX>(a, t, smrec, sm, seq);
 }
 
 // Dynamic shared memory: two stage buffers of S 128-byte records, then (with the side array) two

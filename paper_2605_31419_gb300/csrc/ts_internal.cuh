@@ -315,6 +315,14 @@ __device__ __forceinline__ void ts_bulk_g2s(void* dst_smem, const void* src_gmem
       : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared through the load path (cp.async, cache-global), and
+// its group commit and wait (a thread waits for its own copies; a barrier then publishes them).
+__device__ __forceinline__ void ts_cp_async16(void* dst_smem, const void* src_gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ts_smem_u32(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void ts_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void ts_cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t ts_globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
