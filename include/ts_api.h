@@ -173,9 +173,12 @@ ts_status ts_workspace_init(const ts_plan* plan, void* ws, size_t ws_bytes, ts_s
 ts_status ts_project(const ts_plan* plan, const ts_map* map, const ts_pose* poses, void* ws,
                      size_t ws_bytes, ts_stream stream);
 
-/* Depth ordering per tile (Eq. 4, "sorted in depth order"): exclusive scan of tiles touched,
- * emission of 64-bit keys (global tile id << 32 | depth bits) with face-id values, a stable
- * on-device LSD radix sort, and per-tile [start, end) ranges.  Ties keep ascending face id. */
+/* Depth ordering per tile (Eq. 4, "sorted in depth order"): per-tile pair counts and their
+ * exclusive scan (the per-tile [start, end) ranges), placement of each (tile, face) pair in its
+ * tile's segment, and a sort of every segment by (depth bits, face id).  The result is the pair
+ * list of 64-bit keys (global tile id << 32 | depth bits) with face-id values, ascending by key,
+ * ties in ascending face id.  Pairs beyond the plan's capacity are dropped and latch
+ * TS_ERR_CAPACITY (ts_sync_status). */
 ts_status ts_bin(const ts_plan* plan, void* ws, ts_stream stream);
 
 /* Eq. 3-4 forward: per pixel, front-to-back compositing of its tile's list with early

@@ -696,7 +696,7 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.VM = (long long)p->V * p->M;
   a.n_tiles = p->n_tiles;
   a.frec = w.frec;
-  a.ids = w.vals[ts_sort_final_buffer(p)];
+  a.ids = w.vals[0];
   a.ranges = w.ranges;
   a.color = a.depth = a.alpha = nullptr;
   a.tfin = w.tfin;

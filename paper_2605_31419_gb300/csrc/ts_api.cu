@@ -125,14 +125,9 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->n_pix = poff;
   const int64_t VM = (int64_t)n_views * n_faces;
   int64_t cap = pair_capacity ? pair_capacity : std::max<int64_t>(1024, 4 * VM);
-  if (cap >= ((int64_t)1 << 32) - TS_SORT_ITEMS) return TS_ERR_INVALID_ARG;
+  if (cap >= ((int64_t)1 << 32) - 4096) return TS_ERR_INVALID_ARG;
   p->cap = cap;
-  int tb = 0;
-  while (((int64_t)1 << tb) < toff) ++tb;
-  p->tile_bits = tb;
-  p->sort_passes = (31 + tb + 7) / 8;  // depth bit 31 is always 0 for visible faces (positive depth)
-  p->n_scan_blocks = std::max<int64_t>(1, (VM + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
-  p->n_sort_blocks_cap = (cap + TS_SORT_ITEMS - 1) / TS_SORT_ITEMS;
+  p->n_tile_scan_blocks = std::max<int64_t>(1, (toff + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
   p->n_pose_blocks = std::max(1, ts_pose_blocks(n_faces));
   int64_t max_hw = 0;
   for (int v = 0; v < n_views; ++v) max_hw = std::max<int64_t>(max_hw, (int64_t)p->views[v].W * p->views[v].H);
@@ -152,15 +147,12 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_rect = take((size_t)VM * 8);
   p->o_zbits = take((size_t)VM * 4);
   p->o_count = take((size_t)VM * 4);
-  p->o_offs = take((size_t)VM * 4);
-  p->o_bsums = take((size_t)(p->n_scan_blocks + 1) * 4);
+  p->o_tcnt = take((size_t)toff * 4);
+  p->o_bsums = take((size_t)(p->n_tile_scan_blocks + 1) * 4);
+  p->o_tlarge = take((size_t)toff * 4);
   p->o_keys0 = take((size_t)cap * 8);
   p->o_keys1 = take((size_t)cap * 8);
   p->o_vals0 = take((size_t)cap * 4);
-  p->o_vals1 = take((size_t)cap * 4);
-  const int64_t hist_len = 256 * p->n_sort_blocks_cap;
-  p->o_hist = take((size_t)hist_len * 4);
-  p->o_hsums = take((size_t)((hist_len + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS + 1) * 4);
   p->o_ranges = take((size_t)toff * 8);
   p->o_tfin = take((size_t)poff * 4);
   p->o_nlast = take((size_t)poff * 4);
@@ -400,12 +392,11 @@ ts_status ts_sync_status(const ts_plan* plan, void* ws, ts_stream stream, ts_cou
 ts_status ts_debug_copy(const ts_plan* plan, void* ws, int32_t what, void* dst, size_t bytes, ts_stream stream) {
   const TsPlanImpl* p = impl(plan);
   if (!p || !ws || !dst) return TS_ERR_INVALID_ARG;
-  const int fb = ts_sort_final_buffer(p);
   const int64_t VM = (int64_t)p->V * p->M;
   size_t off, avail;
   switch (what) {
-    case 0: off = fb ? p->o_keys1 : p->o_keys0; avail = (size_t)p->cap * 8; break;
-    case 1: off = fb ? p->o_vals1 : p->o_vals0; avail = (size_t)p->cap * 4; break;
+    case 0: off = p->o_keys0; avail = (size_t)p->cap * 8; break;
+    case 1: off = p->o_vals0; avail = (size_t)p->cap * 4; break;
     case 2: off = p->o_ranges; avail = (size_t)p->n_tiles * 8; break;
     case 3: off = p->o_rect; avail = (size_t)VM * 8; break;
     case 4: off = p->o_zbits; avail = (size_t)VM * 4; break;

@@ -15,8 +15,6 @@
 #define TS_REC_WORDS 32            // 128-byte record, a multiple of 16 B for cp.async.bulk
 #define TS_GRAD_WORDS 32           // per-(view, face) gradient slot: 24 accumulators + chain outputs
 #define TS_SCAN_ITEMS 4096         // items per scan block (1024 threads x 4)
-#define TS_SORT_ITEMS 4096         // keys per radix-sort block (256 threads x 16)
-#define TS_SORT_THREADS 256
 #define TS_ERRBIT_CAPACITY 1u
 #define TS_ERRBIT_TIMEOUT 2u
 #define TS_ERRBIT_BOUNDS 4u  // an index failed its bounds check (the access was skipped)
@@ -73,7 +71,8 @@ struct TsDevHeader {
   const int32_t* faces;
   long long n_vertices;
   unsigned int tile_counter;  // work counter of the persistent raster launches
-  unsigned int pad[13];
+  unsigned int n_large;       // tiles listed for the CTA-wide pair sort
+  unsigned int pad[12];
 };
 
 struct TsPlanImpl {
@@ -83,15 +82,14 @@ struct TsPlanImpl {
   int64_t cap;
   ts_raster_params prm;
   int64_t n_tiles, n_pix;
-  int32_t tile_bits, sort_passes;
-  int64_t n_scan_blocks, n_sort_blocks_cap, n_pose_blocks, n_loss_blocks, n_pho_blocks;
+  int64_t n_tile_scan_blocks, n_pose_blocks, n_loss_blocks, n_pho_blocks;
   bool normals;  // TS_FLAG_NORMALS
   bool stats;    // TS_FLAG_STATS
   bool min_opacity;  // TS_FLAG_MIN_OPACITY
   bool face_sigma;   // TS_FLAG_FACE_SIGMA
   // workspace layout (byte offsets)
-  size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_offs, o_bsums, o_keys0, o_keys1,
-      o_vals0, o_vals1, o_hist, o_hsums, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_lmask, o_pho, o_equi, o_aux, o_nloss,
+  size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_tcnt, o_bsums, o_tlarge, o_keys0, o_keys1,
+      o_vals0, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_lmask, o_pho, o_equi, o_aux, o_nloss,
       o_cov, total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
@@ -108,12 +106,11 @@ struct TsWs {
   short4* rect;
   uint32_t* zbits;
   uint32_t* count;
-  uint32_t* offs;
+  uint32_t* tcnt;    // per tile: pairs (binning)
+  uint32_t* tlarge;  // tiles whose pair lists the CTA-wide sort takes
   uint32_t* bsums;
-  unsigned long long* keys[2];
-  uint32_t* vals[2];
-  uint32_t* hist;
-  uint32_t* hsums;
+  unsigned long long* keys[2];  // [0]: the sorted pair keys; [1]: the tile segments before their sort
+  uint32_t* vals[1];            // the sorted pairs' face ids
   uint2* ranges;
   float* tfin;
   int32_t* nlast;
@@ -139,14 +136,12 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.rect = (short4*)(b + p->o_rect);
   w.zbits = (uint32_t*)(b + p->o_zbits);
   w.count = (uint32_t*)(b + p->o_count);
-  w.offs = (uint32_t*)(b + p->o_offs);
+  w.tcnt = (uint32_t*)(b + p->o_tcnt);
+  w.tlarge = (uint32_t*)(b + p->o_tlarge);
   w.bsums = (uint32_t*)(b + p->o_bsums);
   w.keys[0] = (unsigned long long*)(b + p->o_keys0);
   w.keys[1] = (unsigned long long*)(b + p->o_keys1);
   w.vals[0] = (uint32_t*)(b + p->o_vals0);
-  w.vals[1] = (uint32_t*)(b + p->o_vals1);
-  w.hist = (uint32_t*)(b + p->o_hist);
-  w.hsums = (uint32_t*)(b + p->o_hsums);
   w.ranges = (uint2*)(b + p->o_ranges);
   w.tfin = (float*)(b + p->o_tfin);
   w.nlast = (int32_t*)(b + p->o_nlast);
@@ -207,7 +202,6 @@ cudaError_t ts_launch_pose_apply(const TsPlanImpl* p, ts_pose* poses, const floa
 cudaError_t ts_launch_pose_adam(const TsPlanImpl* p, ts_pose* poses, const float* dtau, float* state, float lr_rho,
                                 float lr_theta, float b1, float b2, float eps, cudaStream_t s);
 cudaError_t ts_launch_timeout_probe(const TsWs& w, unsigned long long limit_ns, cudaStream_t s);
-int ts_sort_final_buffer(const TsPlanImpl* p);  // 0 or 1: which key/val buffer holds the sorted pairs
 int ts_pose_blocks(long long M);                 // blocks of the projection-backward kernel
 
 // ------------------------------------------------------------------------------------------

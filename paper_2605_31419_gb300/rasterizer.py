@@ -180,15 +180,6 @@ class Rasterizer:
         B.ts_equilateral(self.plan, m.ts(), self.ws, weight, out, g, stream)
         return out
 
-    def plan_passes(self) -> int:
-        """Radix-sort passes per ts_bin: 8 bits each over 31 depth bits (the sign bit of a positive
-        depth is 0) + ceil(log2 tiles) tile bits."""
-        n_tiles = int(self.layout["tile_off"][-1])
-        tb = 0
-        while (1 << tb) < n_tiles:
-            tb += 1
-        return (31 + tb + 7) // 8
-
     def counters(self, stream=None, raise_on_error=True) -> dict:
         return B.ts_sync_status(self.plan, self.ws, stream, raise_on_error)
 
