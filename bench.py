@@ -557,9 +557,9 @@ def main():
         else:
             roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": None}
-        # setup + project, binning (tile counts, scan (2), starts, scatter, warp and CTA segment
+        # setup + project, binning (tile counts, scan (3), places, ranges, warp and CTA segment
         # sorts), forward, loss (2), raster backward, chain rule + gather, pose reduction
-        launches = 2 + 7 + 1 + 2 + 1 + 2 + 1
+        launches = 2 + 8 + 1 + 2 + 1 + 2 + 1
         line = {
             "metric": "Mpix/s fwd+bwd raster", "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,

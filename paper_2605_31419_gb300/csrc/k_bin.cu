@@ -1,10 +1,15 @@
 // k_bin.cu -- depth ordering per tile (Eq. 4: faces are composited in depth order).
 //
-//  1. per tile, the number of (view, face) pairs whose tile rectangle covers it (atomic counts);
-//  2. an exclusive scan of the counts (two-level, 4096 items per block) gives each tile's segment
-//     [start, end) of the pair list, the pair total and the capacity check;
-//  3. each pair is placed in its tile's segment through an atomic cursor, as the 64-bit key
-//     (float bits of the depth key << 32 | face id) -- unique within a tile;
+//  1. per tile, the number of (view, face) pairs whose tile rectangle covers it.  When every
+//     view's tiles fit in shared memory (TS_BIN_MAX_TILES), one block per (TS_BIN_FACES faces,
+//     view) counts its pairs per tile there and writes a [tile][face block] count matrix; else
+//     global atomic counts per tile;
+//  2. an exclusive scan of the counts (two-level, 4096 items per block; tile-major for the
+//     matrix) gives each tile's segment [start, end) of the pair list -- and with the matrix each
+//     block's first place in it -- the pair total and the capacity check;
+//  3. each pair is placed in its tile's segment (shared-memory atomics on the block's places, or
+//     global atomic cursors) as the 64-bit key (float bits of the depth key << 32 | face id),
+//     unique within a tile;
 //  4. each segment is sorted by that key (bitonic networks: one warp in registers up to 32 pairs,
 //     one warp in shared memory up to 512, one CTA beyond), and written out as the pair list:
 //     key (global tile id << 32 | depth bits) and face id, ascending depth with ties in ascending
@@ -101,6 +106,30 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_bsums(uint32_t* bsums, Len len,
 }
 
 
+// Second level of a plain in-place exclusive scan (blocked: 4 consecutive items per thread).
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(uint32_t* __restrict__ data, Len len,
+                                                       const uint32_t* __restrict__ bsums) {
+  __shared__ uint32_t sm[33];
+  const long long n = len.get();
+  const long long base = (long long)blockIdx.x * TS_SCAN_ITEMS;
+  if (base >= n) return;
+  const long long i0 = base + (long long)threadIdx.x * SCAN_PER;
+  uint32_t c[SCAN_PER];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) {
+    c[k] = (i0 + k < n) ? data[i0 + k] : 0u;
+    s += c[k];
+  }
+  uint32_t tot;
+  uint32_t off = block_excl_scan(s, sm, &tot) + bsums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) {
+    if (i0 + k < n) data[i0 + k] = off;
+    off += c[k];
+  }
+}
+
 // ---------------------------------------------------------------------------- tile segments
 struct TileArgs {
   const uint32_t* count;
@@ -182,6 +211,80 @@ __global__ void __launch_bounds__(256) k_tile_scatter(TileArgs a) {
       if ((long long)pos < a.cap) a.seg[pos] = key;
     }
   }
+}
+
+// Steps 1-3 when every view's tiles fit in shared memory: one block per (block of TS_BIN_FACES
+// faces, view) counts its pairs per tile in shared memory, and the exclusive scan of the
+// [tile][face block] count matrix (tile-major) gives each block its first place in every tile's
+// segment; the block then places its pairs with shared-memory atomics.
+struct MatArgs {
+  const uint32_t* count;
+  const short4* rect;
+  const uint32_t* zbits;
+  const TsView* views;
+  long long M, B, cap, n_tiles;
+  uint32_t* mat;
+  unsigned long long* seg;
+  uint2* ranges;
+  const unsigned long long* n_pairs;
+};
+
+constexpr int BIN_T = 1024;
+
+__global__ void __launch_bounds__(BIN_T) k_bin_counts(MatArgs a) {
+  extern __shared__ uint32_t hcnt[];
+  const int v = blockIdx.y;
+  const long long blk = blockIdx.x;
+  const TsView& vw = a.views[v];
+  const int T = vw.TX * vw.TY;
+  for (int t = threadIdx.x; t < T; t += BIN_T) hcnt[t] = 0u;
+  __syncthreads();
+  const long long m0 = blk * TS_BIN_FACES;
+  for (int i = threadIdx.x; i < TS_BIN_FACES; i += BIN_T) {
+    const long long m = m0 + i;
+    if (m >= a.M) break;
+    const long long idx = (long long)v * a.M + m;
+    if (a.count[idx] == 0) continue;
+    const short4 r = a.rect[idx];
+    for (int ty = r.y; ty <= r.w; ++ty)
+      for (int tx = r.x; tx <= r.z; ++tx) atomicAdd(&hcnt[ty * vw.TX + tx], 1u);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += BIN_T) a.mat[(vw.tile_off + t) * a.B + blk] = hcnt[t];
+}
+
+__global__ void __launch_bounds__(BIN_T) k_bin_place(MatArgs a) {
+  extern __shared__ uint32_t place[];
+  const int v = blockIdx.y;
+  const long long blk = blockIdx.x;
+  const TsView& vw = a.views[v];
+  const int T = vw.TX * vw.TY;
+  for (int t = threadIdx.x; t < T; t += BIN_T) place[t] = a.mat[(vw.tile_off + t) * a.B + blk];
+  __syncthreads();
+  const long long m0 = blk * TS_BIN_FACES;
+  for (int i = threadIdx.x; i < TS_BIN_FACES; i += BIN_T) {
+    const long long m = m0 + i;
+    if (m >= a.M) break;
+    const long long idx = (long long)v * a.M + m;
+    if (a.count[idx] == 0) continue;
+    const short4 r = a.rect[idx];
+    const unsigned long long key = ((unsigned long long)a.zbits[idx] << 32) | (uint32_t)m;
+    for (int ty = r.y; ty <= r.w; ++ty)
+      for (int tx = r.x; tx <= r.z; ++tx) {
+        const uint32_t pos = atomicAdd(&place[ty * vw.TX + tx], 1u);
+        if ((long long)pos < a.cap) a.seg[pos] = key;  // beyond: the scan has latched the capacity bit
+      }
+  }
+}
+
+// [start, end) of each tile from the scanned matrix: its first block's place and the next tile's.
+__global__ void __launch_bounds__(256) k_bin_ranges(MatArgs a) {
+  const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (t >= a.n_tiles) return;
+  const uint32_t start = a.mat[t * a.B];
+  const uint32_t end = t + 1 < a.n_tiles ? a.mat[(t + 1) * a.B]
+                                         : (uint32_t)min(*a.n_pairs, (unsigned long long)0xffffffffu);
+  a.ranges[t] = make_uint2(start, end);
 }
 
 // Step 4.  Bitonic networks in the form whose every compare-exchange moves the smaller key to the
@@ -320,22 +423,43 @@ __global__ void __launch_bounds__(LARGE_T) k_tile_sort_large(SortOut o, unsigned
 cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
   const long long VM = (long long)p->V * p->M;
   cudaError_t e = cudaMemsetAsync(w.ranges, 0, (size_t)p->n_tiles * sizeof(uint2), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.tcnt, 0, (size_t)p->n_tiles * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->n_large, 0, sizeof(unsigned int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->n_pairs, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess || VM == 0) return e;
-  TileArgs ta{w.count, w.rect, w.zbits, w.views, VM, p->M, p->cap, p->n_tiles, w.tcnt, w.ranges, w.keys[1],
-              &w.hdr->error_bits};
-  const unsigned nf = (unsigned)((VM + 255) / 256);
-  k_tile_count<<<nf, 256, 0, s>>>(ta);
-  // 2: scan of the tile counts (the total is the pair count; above the capacity latches its bit)
-  Len lt{p->n_tiles};
-  const unsigned nb = (unsigned)((p->n_tiles + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
-  k_scan_reduce<<<nb, SCAN_T, 0, s>>>(w.tcnt, lt, w.bsums);
-  k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.bsums, lt, &w.hdr->n_pairs, &w.hdr->error_bits, p->cap);
-  k_tile_starts<<<nb, SCAN_T, 0, s>>>(ta, w.bsums);
-  // 3-4: segments, then their sorts
-  k_tile_scatter<<<nf, 256, 0, s>>>(ta);
+  if (p->bin_blocks > 0) {
+    // 1-3 with shared-memory counts: counts, their scan (the total is the pair count; above the
+    // capacity latches its bit), places, ranges
+    MatArgs ma{w.count, w.rect, w.zbits, w.views, p->M, p->bin_blocks, p->cap, p->n_tiles, w.tmat, w.keys[1],
+               w.ranges, &w.hdr->n_pairs};
+    const int smem = (int)(p->max_view_tiles * sizeof(uint32_t));
+    e = ts_smem_limit((const void*)k_bin_counts, smem);
+    if (e == cudaSuccess) e = ts_smem_limit((const void*)k_bin_place, smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)p->bin_blocks, (unsigned)p->V);
+    k_bin_counts<<<grid, BIN_T, smem, s>>>(ma);
+    Len lm{p->n_tiles * p->bin_blocks};
+    const unsigned nb = (unsigned)((lm.n + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
+    k_scan_reduce<<<nb, SCAN_T, 0, s>>>(w.tmat, lm, w.bsums);
+    k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.bsums, lm, &w.hdr->n_pairs, &w.hdr->error_bits, p->cap);
+    k_scan_apply<<<nb, SCAN_T, 0, s>>>(w.tmat, lm, w.bsums);
+    k_bin_place<<<grid, BIN_T, smem, s>>>(ma);
+    k_bin_ranges<<<(unsigned)((p->n_tiles + 255) / 256), 256, 0, s>>>(ma);
+  } else {
+    // 1-3 with global counts: counts, their scan, starts, places
+    e = cudaMemsetAsync(w.tcnt, 0, (size_t)p->n_tiles * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    TileArgs ta{w.count, w.rect, w.zbits, w.views, VM, p->M, p->cap, p->n_tiles, w.tcnt, w.ranges, w.keys[1],
+                &w.hdr->error_bits};
+    const unsigned nf = (unsigned)((VM + 255) / 256);
+    k_tile_count<<<nf, 256, 0, s>>>(ta);
+    Len lt{p->n_tiles};
+    const unsigned nb = (unsigned)((p->n_tiles + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
+    k_scan_reduce<<<nb, SCAN_T, 0, s>>>(w.tcnt, lt, w.bsums);
+    k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.bsums, lt, &w.hdr->n_pairs, &w.hdr->error_bits, p->cap);
+    k_tile_starts<<<nb, SCAN_T, 0, s>>>(ta, w.bsums);
+    k_tile_scatter<<<nf, 256, 0, s>>>(ta);
+  }
+  // 4: the segments' sorts
   SortOut so{w.keys[1], w.keys[0], w.vals[0], w.ranges, p->n_tiles, p->cap, w.tlarge, &w.hdr->n_large};
   k_tile_sort<<<(unsigned)((p->n_tiles + SORT_WARPS_PER_BLOCK - 1) / SORT_WARPS_PER_BLOCK), 32 * SORT_WARPS_PER_BLOCK,
                 0, s>>>(so);

@@ -29,22 +29,23 @@ __global__ void __launch_bounds__(LOSS_T) k_loss_partial(const TsImageTable tab,
   if (base < HW) {
     const float ic = 1.0f / (3.0f * (float)HW), id = lambda_dep / (float)HW;
 #pragma unroll
-    for (int k = 0; k < LOSS_PER; ++k) {
+    for (int k = 0; k < LOSS_PER; ++k) {  // a guard, not an exit: all pixels' loads can be in flight
       const long long i = base + (long long)k * LOSS_T + threadIdx.x;
-      if (i >= HW) break;
+      if (i < HW) {
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        const long long o = 3 * pix_off + ch * HW + i;
-        const float r = C[o] - tC[o];
-        lc += fabsf(r);
-        dC[o] = r > 0.f ? ic : (r < 0.f ? -ic : 0.f);
+        for (int ch = 0; ch < 3; ++ch) {
+          const long long o = 3 * pix_off + ch * HW + i;
+          const float r = C[o] - tC[o];
+          lc += fabsf(r);
+          dC[o] = r > 0.f ? ic : (r < 0.f ? -ic : 0.f);
+        }
+        const long long o = pix_off + i;
+        const float t = tD[o];
+        const float r = D[o] - t;
+        const bool valid = t > 0.f;
+        if (valid) ld += fabsf(r);
+        dD[o] = valid ? (r > 0.f ? id : (r < 0.f ? -id : 0.f)) : 0.f;
       }
-      const long long o = pix_off + i;
-      const float t = tD[o];
-      const float r = D[o] - t;
-      const bool valid = t > 0.f;
-      if (valid) ld += fabsf(r);
-      dD[o] = valid ? (r > 0.f ? id : (r < 0.f ? -id : 0.f)) : 0.f;
     }
   }
 #pragma unroll

@@ -71,23 +71,34 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
     } else {
       vi[0] = 3 * m; vi[1] = 3 * m + 1; vi[2] = 3 * m + 2;
     }
-    float u[3], v[3], z[3], o[3], xv[3], yv[3], wp[3][3];
+    float u[3], v[3], z[3], o[3], xv[3], yv[3], wp[3][3], col[3][3];
     vis = true;
 #pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (vi[k] < 0 || vi[k] >= a.map.n_vertices) vis = false;
+    if (vis) {  // every load of the face up front, so that their latencies overlap
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const long long j = vi[k];
+        wp[k][0] = __ldg(a.map.px + j);
+        wp[k][1] = __ldg(a.map.py + j);
+        wp[k][2] = __ldg(a.map.pz + j);
+        o[k] = __ldg(a.map.op + j);
+        col[k][0] = __ldg(a.map.cr + j);
+        col[k][1] = __ldg(a.map.cg + j);
+        col[k][2] = __ldg(a.map.cb + j);
+      }
+    }
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const long long j = vi[k];
-      if (j < 0 || j >= a.map.n_vertices) { vis = false; break; }
+      if (!vis) break;
       float xc, yc, zc;
-      wp[k][0] = __ldg(a.map.px + j);
-      wp[k][1] = __ldg(a.map.py + j);
-      wp[k][2] = __ldg(a.map.pz + j);
       ts_rigid_f32(P, wp[k][0], wp[k][1], wp[k][2], xc, yc, zc);
       if (!(zc > a.z_near)) { vis = false; break; }
       ts_pinhole_f32(vw, xc, yc, zc, u[k], v[k]);
       z[k] = zc;
       xv[k] = xc;
       yv[k] = yc;
-      o[k] = __ldg(a.map.op + j);
     }
     float area2 = 0.f, len[3] = {0.f, 0.f, 0.f}, per = 0.f, oF = 0.f;
     if (vis) {
@@ -132,14 +143,13 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
       const float invD = 1.0f / area2;
       const float k0 = (per / len[0]) * invD, k1 = (per / len[1]) * invD, k2 = (per / len[2]) * invD;
       float4* rec = a.frec + idx * (TS_REC_WORDS / 4);
-      const long long j0 = vi[0], j1 = vi[1], j2 = vi[2];
       rec[0] = make_float4(u[0], u[1], u[2], v[0]);
       rec[1] = make_float4(v[1], v[2], e0x, e0y);
       rec[2] = make_float4(e1x, e1y, e2x, e2y);
       rec[3] = make_float4(k0, k1, k2, invD);
-      rec[4] = make_float4(oF, __ldg(a.map.cr + j0), __ldg(a.map.cg + j0), __ldg(a.map.cb + j0));
-      rec[5] = make_float4(__ldg(a.map.cr + j1), __ldg(a.map.cg + j1), __ldg(a.map.cb + j1), __ldg(a.map.cr + j2));
-      rec[6] = make_float4(__ldg(a.map.cg + j2), __ldg(a.map.cb + j2), z[0], z[1]);
+      rec[4] = make_float4(oF, col[0][0], col[0][1], col[0][2]);
+      rec[5] = make_float4(col[1][0], col[1][1], col[1][2], col[2][0]);
+      rec[6] = make_float4(col[2][1], col[2][2], z[0], z[1]);
       // gradient slot of this (view, face), face-major so that a face's views are adjacent;
       // cleared here for the raster backward's atomics
       const long long slot = m * a.V + view;

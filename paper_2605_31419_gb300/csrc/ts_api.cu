@@ -105,7 +105,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->V = n_views;
   p->M = n_faces;
   p->prm = *prm;
-  int64_t toff = 0, poff = 0;
+  int64_t toff = 0, poff = 0, max_tiles = 0;
   for (int v = 0; v < n_views; ++v) {
     const ts_camera& c = cams[v];
     if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return TS_ERR_INVALID_ARG;
@@ -119,6 +119,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
     w.pix_off = poff;
     toff += (int64_t)w.TX * w.TY;
     poff += (int64_t)c.width * c.height;
+    max_tiles = std::max<int64_t>(max_tiles, (int64_t)w.TX * w.TY);
   }
   if (toff >= ((int64_t)1 << 31)) return TS_ERR_INVALID_ARG;
   p->n_tiles = toff;
@@ -127,7 +128,12 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   int64_t cap = pair_capacity ? pair_capacity : std::max<int64_t>(1024, 4 * VM);
   if (cap >= ((int64_t)1 << 32) - 4096) return TS_ERR_INVALID_ARG;
   p->cap = cap;
-  p->n_tile_scan_blocks = std::max<int64_t>(1, (toff + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
+  p->max_view_tiles = max_tiles;
+  p->bin_blocks = max_tiles <= TS_BIN_MAX_TILES ? std::max<int64_t>(1, (n_faces + TS_BIN_FACES - 1) / TS_BIN_FACES) : 0;
+  {
+    const int64_t scanned = p->bin_blocks ? toff * p->bin_blocks : toff;
+    p->n_tile_scan_blocks = std::max<int64_t>(1, (scanned + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
+  }
   p->n_pose_blocks = std::max(1, ts_pose_blocks(n_faces));
   int64_t max_hw = 0;
   for (int v = 0; v < n_views; ++v) max_hw = std::max<int64_t>(max_hw, (int64_t)p->views[v].W * p->views[v].H);
@@ -150,6 +156,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_tcnt = take((size_t)toff * 4);
   p->o_bsums = take((size_t)(p->n_tile_scan_blocks + 1) * 4);
   p->o_tlarge = take((size_t)toff * 4);
+  p->o_tmat = take((size_t)toff * (size_t)p->bin_blocks * 4);
   p->o_keys0 = take((size_t)cap * 8);
   p->o_keys1 = take((size_t)cap * 8);
   p->o_vals0 = take((size_t)cap * 4);

@@ -15,6 +15,8 @@
 #define TS_REC_WORDS 32            // 128-byte record, a multiple of 16 B for cp.async.bulk
 #define TS_GRAD_WORDS 32           // per-(view, face) gradient slot: 24 accumulators + chain outputs
 #define TS_SCAN_ITEMS 4096         // items per scan block (1024 threads x 4)
+#define TS_BIN_FACES 8192          // faces per block of the shared-memory tile counts
+#define TS_BIN_MAX_TILES 40960     // the most tiles of a view those counts hold (160 KB)
 #define TS_ERRBIT_CAPACITY 1u
 #define TS_ERRBIT_TIMEOUT 2u
 #define TS_ERRBIT_BOUNDS 4u  // an index failed its bounds check (the access was skipped)
@@ -83,12 +85,14 @@ struct TsPlanImpl {
   ts_raster_params prm;
   int64_t n_tiles, n_pix;
   int64_t n_tile_scan_blocks, n_pose_blocks, n_loss_blocks, n_pho_blocks;
+  int64_t bin_blocks;       // face blocks per view of the shared-memory tile counts (0: global counts)
+  int64_t max_view_tiles;   // the most tiles of one view
   bool normals;  // TS_FLAG_NORMALS
   bool stats;    // TS_FLAG_STATS
   bool min_opacity;  // TS_FLAG_MIN_OPACITY
   bool face_sigma;   // TS_FLAG_FACE_SIGMA
   // workspace layout (byte offsets)
-  size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_tcnt, o_bsums, o_tlarge, o_keys0, o_keys1,
+  size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_tcnt, o_bsums, o_tlarge, o_tmat, o_keys0, o_keys1,
       o_vals0, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_lmask, o_pho, o_equi, o_aux, o_nloss,
       o_cov, total;
   void* events[2 * TS_N_STAGES];
@@ -108,6 +112,7 @@ struct TsWs {
   uint32_t* count;
   uint32_t* tcnt;    // per tile: pairs (binning)
   uint32_t* tlarge;  // tiles whose pair lists the CTA-wide sort takes
+  uint32_t* tmat;    // [tile][face block] pair counts, then their exclusive scan
   uint32_t* bsums;
   unsigned long long* keys[2];  // [0]: the sorted pair keys; [1]: the tile segments before their sort
   uint32_t* vals[1];            // the sorted pairs' face ids
@@ -138,6 +143,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.count = (uint32_t*)(b + p->o_count);
   w.tcnt = (uint32_t*)(b + p->o_tcnt);
   w.tlarge = (uint32_t*)(b + p->o_tlarge);
+  w.tmat = (uint32_t*)(b + p->o_tmat);
   w.bsums = (uint32_t*)(b + p->o_bsums);
   w.keys[0] = (unsigned long long*)(b + p->o_keys0);
   w.keys[1] = (unsigned long long*)(b + p->o_keys1);

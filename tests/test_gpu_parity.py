@@ -164,6 +164,49 @@ def test_edge_cases(oracle, case):
         assert_grad(g["dopa"], r["dopa"], "dopa")
 
 
+def test_bin_global_counts_path_bitexact(oracle):
+    """A view with more tiles than the shared-memory tile counts hold (4096 x 2560 at 8 x 8 tiles:
+    163,840 tiles) takes the global-count path of the binning; its pairs and ranges are the same."""
+    from oracle.oracle import SceneArrays
+    sc = random_triangles_scene(seed=5, n_faces=600, W=4096, H=2560, f=1500.0, side_lo=0.05, side_hi=0.4)
+    p, po = params_pair(tile_w=8, tile_h=8)
+    g = gpu_run(sc, p, backward=False, pair_capacity=1_000_000)
+    assert g["counters"]["status"] == "TS_OK"
+    rast = g["rast"]
+    b = oracle.bin(SceneArrays.of(sc), po)
+    n = int(g["counters"]["n_pairs"])
+    assert n == len(b["keys"]) and n > 0
+    assert np.array_equal(rast.debug("keys").cpu().numpy().view(np.uint64)[:n], b["keys"])
+    assert np.array_equal(rast.debug("ids").cpu().numpy().view(np.uint32)[:n], b["ids"])
+    rg = rast.debug("ranges").cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    empty = b["ranges"][:, 1] == 0
+    assert np.array_equal(rg[~empty], b["ranges"][~empty])
+    assert (rg[empty, 1] - rg[empty, 0] == 0).all()
+
+
+@pytest.mark.parametrize("n_faces", [3000, 40000])
+def test_bin_long_tile_lists_bitexact(oracle, n_faces):
+    """Large faces over a 48 x 32 image: every tile's list holds most faces, so the lists go to
+    the CTA-wide sort (3000: in shared memory; 40000: beyond its 16,384 keys, in place)."""
+    from oracle.oracle import SceneArrays
+    sc = random_triangles_scene(seed=6, n_faces=n_faces, W=48, H=32, f=40.0, side_lo=0.6, side_hi=1.2,
+                                z_lo=1.0, z_hi=2.0)
+    p, po = params_pair()
+    g = gpu_run(sc, p, backward=False, pair_capacity=400_000)
+    assert g["counters"]["status"] == "TS_OK"
+    rast = g["rast"]
+    b = oracle.bin(SceneArrays.of(sc), po)
+    n = int(g["counters"]["n_pairs"])
+    assert n == len(b["keys"])
+    lens = b["ranges"][:, 1] - b["ranges"][:, 0]
+    assert lens.max() > (16384 if n_faces > 16384 else 512)
+    assert np.array_equal(rast.debug("keys").cpu().numpy().view(np.uint64)[:n], b["keys"])
+    assert np.array_equal(rast.debug("ids").cpu().numpy().view(np.uint32)[:n], b["ids"])
+    rg = rast.debug("ranges").cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    empty = b["ranges"][:, 1] == 0
+    assert np.array_equal(rg[~empty], b["ranges"][~empty])
+
+
 def test_capacity_overflow_is_reported():
     import paper_2605_31419_gb300 as ts
     sc = random_triangles_scene(seed=1)
