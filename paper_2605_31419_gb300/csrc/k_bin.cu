@@ -10,7 +10,7 @@
 //  3. each pair is placed in its tile's segment (shared-memory atomics on the block's places, or
 //     global atomic cursors) as the 64-bit key (float bits of the depth key << 32 | face id),
 //     unique within a tile;
-//  4. each segment is sorted by that key (bitonic networks: one warp in registers up to 32 pairs,
+//  4. each segment is sorted by that key (bitonic networks: one warp in registers up to 64 pairs,
 //     one warp in shared memory up to 512, one CTA beyond), and written out as the pair list:
 //     key (global tile id << 32 | depth bits) and face id, ascending depth with ties in ascending
 //     face id -- the order a stable sort of the (view, face)-ordered pairs by (tile, depth) gives.
@@ -340,6 +340,45 @@ __global__ void __launch_bounds__(32 * SORT_WARPS_PER_BLOCK) k_tile_sort(SortOut
       }
     }
     if (lane < n) put_pair(o, t, start + lane, x);
+    return;
+  }
+  if (n <= 64) {  // two keys per lane: x0 at position lane, x1 at position 32 + lane
+    unsigned long long x0 = o.seg[start + lane];
+    unsigned long long x1 = 32 + lane < n ? o.seg[start + 32 + lane] : ~0ull;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {  // each half sorted as in the 32-key network
+      {
+        const unsigned long long y0 = __shfl_xor_sync(0xffffffffu, x0, k - 1);
+        const unsigned long long y1 = __shfl_xor_sync(0xffffffffu, x1, k - 1);
+        const bool lower = (lane & (k >> 1)) == 0;
+        x0 = lower ? min(x0, y0) : max(x0, y0);
+        x1 = lower ? min(x1, y1) : max(x1, y1);
+      }
+#pragma unroll
+      for (int j = k >> 2; j > 0; j >>= 1) {
+        const unsigned long long y0 = __shfl_xor_sync(0xffffffffu, x0, j);
+        const unsigned long long y1 = __shfl_xor_sync(0xffffffffu, x1, j);
+        const bool lower = (lane & j) == 0;
+        x0 = lower ? min(x0, y0) : max(x0, y0);
+        x1 = lower ? min(x1, y1) : max(x1, y1);
+      }
+    }
+    {  // merge of 64: position lane pairs with 63 - lane, i.e. x1 of lane 31 - lane
+      const unsigned long long y0 = __shfl_sync(0xffffffffu, x1, 31 - lane);
+      const unsigned long long y1 = __shfl_sync(0xffffffffu, x0, 31 - lane);
+      x0 = min(x0, y0);
+      x1 = max(x1, y1);
+    }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+      const unsigned long long y0 = __shfl_xor_sync(0xffffffffu, x0, j);
+      const unsigned long long y1 = __shfl_xor_sync(0xffffffffu, x1, j);
+      const bool lower = (lane & j) == 0;
+      x0 = lower ? min(x0, y0) : max(x0, y0);
+      x1 = lower ? min(x1, y1) : max(x1, y1);
+    }
+    put_pair(o, t, start + lane, x0);
+    if (32 + lane < n) put_pair(o, t, start + 32 + lane, x1);
     return;
   }
   if (n > WARP_SORT_MAX) {
