@@ -37,7 +37,7 @@ FLOPS_PHO = 394.0
 # DRAM bytes (read + write) per view of one k_render_bwd launch of this workload, from the ncu
 # capture in profiles/render_kernels_room_4views_full.md (4 views, tile 16x8, 64 faces per stage),
 # scaled by the views of the launch; reported only for that launch configuration
-BWD_TRAFFIC_PER_VIEW = (178.14656e6 + 24.41472e6) / 4
+BWD_TRAFFIC_PER_VIEW = (188.842752e6 + 23.260928e6) / 4
 W, H, F, N_FACES, N_VIEWS = 1200, 680, 600.0, 300_000, 20
 WORKLOAD = "room 1200x680 f=600, 300k faces, 20 poses, fwd+bwd (L1 colour+depth), batched"
 
