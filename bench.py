@@ -38,6 +38,8 @@ FLOPS_PHO = 394.0
 # capture in profiles/render_kernels_room_4views_full.md (4 views, tile 16x8, 64 faces per stage),
 # scaled by the views of the launch; reported only for that launch configuration
 BWD_TRAFFIC_PER_VIEW = (188.842752e6 + 23.260928e6) / 4
+# DRAM bytes per view of one k_render_step launch (None until captured for the current kernel)
+STEP_TRAFFIC_PER_VIEW = None
 W, H, F, N_FACES, N_VIEWS = 1200, 680, 600.0, 300_000, 20
 WORKLOAD = "room 1200x680 f=600, 300k faces, 20 poses, fwd+bwd (L1 colour+depth), batched"
 
@@ -55,6 +57,8 @@ def parse():
     ap.add_argument("--views", type=int, default=N_VIEWS)
     ap.add_argument("--tile", default="16x8")
     ap.add_argument("--stage", type=int, default=64)
+    ap.add_argument("--separate", action="store_true",
+                    help="time ts_render_fwd + ts_l1_loss + ts_render_bwd instead of the fused ts_render_step_l1")
     return ap.parse_args()
 
 
@@ -428,9 +432,14 @@ def main():
 
     def step(r=rast, mp=m, ps=poses, tc=tgt_c, td=tgt_d, g=grad):
         g.pos.zero_(); g.col.zero_(); g.opa.zero_()
-        r.forward(mp, ps)
-        r.l1_loss(tc, td, 0.05)
-        r.backward(r.dC, r.dD, None, g)
+        if args.separate:
+            r.forward(mp, ps)
+            r.l1_loss(tc, td, 0.05)
+            r.backward(r.dC, r.dD, None, g)
+        else:
+            r.project(mp, ps)
+            r.bin()
+            r.step_l1(tc, td, 0.05, g)
         r.pose_grad()
 
     for _ in range(args.warmup):
@@ -513,10 +522,16 @@ def main():
             targets_in = torch.cuda.Event()
             targets_in.record(copy_stream)
             grad.pos.zero_(); grad.col.zero_(); grad.opa.zero_()
-            rast.forward(dm, d_poses)
-            stream.wait_event(targets_in)
-            rast.l1_loss(d_tc, d_td, 0.05)
-            rast.backward(rast.dC, rast.dD, None, grad)
+            if args.separate:
+                rast.forward(dm, d_poses)
+                stream.wait_event(targets_in)
+                rast.l1_loss(d_tc, d_td, 0.05)
+                rast.backward(rast.dC, rast.dD, None, grad)
+            else:
+                rast.project(dm, d_poses)
+                rast.bin()
+                stream.wait_event(targets_in)
+                rast.step_l1(d_tc, d_td, 0.05, grad)
             rast.pose_grad()
             out_pos.copy_(grad.pos, non_blocking=True)
             out_col.copy_(grad.col, non_blocking=True)
@@ -545,26 +560,33 @@ def main():
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
         if names[dom] in ("bwd_raster", "fwd"):
+            fused = names[dom] == "fwd" and not args.separate  # the fwd stage times ts_render_step_l1
+            per = (FLOPS_FWD + FLOPS_BWD) if fused else (FLOPS_BWD if names[dom] == "bwd_raster" else FLOPS_FWD)
             contrib = cnt["bwd_contrib"] if names[dom] == "bwd_raster" else cnt["fwd_contrib"]
-            flops = (FLOPS_BWD if names[dom] == "bwd_raster" else FLOPS_FWD) * contrib
+            flops = per * contrib
             ach = flops / (stage_ms[dom] / 1e3) / 1e12
-            roof = {"kernel": f"k_render_{'bwd' if names[dom] == 'bwd_raster' else 'fwd'}", "bound": "alu",
+            kernel = "k_render_step" if fused else f"k_render_{'bwd' if names[dom] == 'bwd_raster' else 'fwd'}"
+            per_view = {"k_render_step": STEP_TRAFFIC_PER_VIEW, "k_render_bwd": BWD_TRAFFIC_PER_VIEW}.get(kernel)
+            roof = {"kernel": kernel, "bound": "alu",
                     "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
-                    "traffic": (BWD_TRAFFIC_PER_VIEW * sc.n_views if names[dom] == "bwd_raster" and args.tile == "16x8"
+                    "traffic": (per_view * sc.n_views if per_view is not None and args.tile == "16x8"
                                 and args.stage == 64 else None),
                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
-                    "work": f"{contrib} (pixel, face) contributions x {FLOPS_BWD if names[dom] == 'bwd_raster' else FLOPS_FWD:.0f} flops"}
+                    "work": f"{contrib} (pixel, face) contributions x {per:.0f} flops"}
         else:
             roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": None}
         # setup + project, binning (tile counts, scan (3), places, ranges, warp and CTA segment
-        # sorts), forward, loss (2), raster backward, chain rule + gather, pose reduction
-        launches = 2 + 8 + 1 + 2 + 1 + 2 + 1
+        # sorts), then either forward, loss (2) and raster backward, or the fused step and its loss
+        # reduction; chain rule + gather, pose reduction
+        launches = 2 + 8 + (1 + 2 + 1 if args.separate else 2) + 2 + 1
         line = {
             "metric": "Mpix/s fwd+bwd raster", "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "views": sc.n_views, "W": W, "H": H, "faces": sc.n_faces,
+                       "path": ("ts_render_fwd + ts_l1_loss + ts_render_bwd" if args.separate
+                                else "ts_render_step_l1 (forward, L1 loss and backward in one pass per tile)"),
                        "tile": args.tile, "tris_per_stage": args.stage, "l2": "flushed (256 MB write) between steps",
                        "parallelism": f"replicas x{world}"},
             "plain_per_view": {"value": pixels / (plain_ms / 1e3) / 1e6 if plain_ms else None, "unit": "Mpix/s",

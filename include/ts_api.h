@@ -239,6 +239,24 @@ ts_status ts_covisibility(const ts_plan* plan, const uint32_t* visible, float* i
 ts_status ts_normal_loss(const ts_plan* plan, void* ws, const float* normal, const float* tgt_normal, float weight,
                          float* loss, float* dN, ts_stream stream);
 
+/* One training step's raster work in one pass per tile: the Eq. 3-4 forward, the mean-L1 loss of
+ * ts_l1_loss (the L1 part of Eq. 8 with the depth term of Eq. 9) and the backward of ts_render_bwd
+ * driven by that loss's dC and dD (no dA), with the same results as those three calls.  The L1
+ * gradient of a pixel depends on that pixel alone, so each tile runs its backward right after its
+ * forward while its staged records and its pixels' state are still on the chip: no image gradient
+ * is written and read back, and most records are not staged twice.
+ *   tgt_color [3][H][W], tgt_depth [H][W]: targets packed per view (device), as in ts_l1_loss;
+ *   color [3][H][W], depth, alpha [H][W]: outputs as in ts_render_fwd (depth, alpha may be NULL);
+ *   loss: device float [n_views], overwritten (fixed-order sums of per-tile partials);
+ *   dC, dD: NULL, or device images that also receive the loss gradients;
+ *   grad: as in ts_render_bwd (map gradients added; pose partials for ts_pose_grad).
+ * Calls on the workspace: ts_project -> ts_bin -> ts_render_step_l1 [-> ts_pose_grad].  A plan with
+ * TS_FLAG_NORMALS or TS_FLAG_FACE_SIGMA, a NULL required pointer, or a negative or non-finite
+ * lambda_dep returns TS_ERR_INVALID_ARG. */
+ts_status ts_render_step_l1(const ts_plan* plan, void* ws, const float* tgt_color, const float* tgt_depth,
+                           float lambda_dep, float* color, float* depth, float* alpha, float* loss, float* dC,
+                           float* dD, const ts_map_grad* grad, ts_stream stream);
+
 /* Eq. 5-7: dL/dtau per view for the left perturbation Exp(tau) o T_CW, tau = (rho, theta), as
  * sum over the view's visible face vertices of [g_C ; v_C x g_C], reduced deterministically.
  *   dtau: device float [n_views][6], overwritten. */

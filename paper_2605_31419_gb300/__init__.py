@@ -7,7 +7,7 @@ library has not been built: there is no CPU fallback.
 from . import binding  # noqa: F401
 from .binding import (  # noqa: F401
     TsError, ts_default_params, ts_plan_init, ts_workspace_size, ts_workspace_init, ts_project, ts_bin,
-    ts_render_fwd, ts_render_bwd, ts_render_fwd_n, ts_render_bwd_n, ts_pose_grad,
+    ts_render_fwd, ts_render_bwd, ts_render_fwd_n, ts_render_bwd_n, ts_render_step_l1, ts_pose_grad,
     ts_l1_loss, ts_l1_loss_noalloc, ts_pho_loss, ts_normal_loss, ts_equilateral, ts_pose_apply, ts_pose_adam,
     ts_sync_status, ts_face_stats, ts_covisibility, TS_FLAG_PERSISTENT, TS_FLAG_NORMALS, TS_FLAG_STATS,
     TS_FLAG_MIN_OPACITY, TS_FLAG_FACE_SIGMA,

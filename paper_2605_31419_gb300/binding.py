@@ -94,6 +94,8 @@ SIGNATURES = {
     "ts_covisibility": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
     "ts_normal_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, C.c_float, _vp, _vp, _vp]),
     "ts_render_bwd": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, C.POINTER(TsMapGrad), _vp]),
+    "ts_render_step_l1": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp, _vp, _vp,
+                                C.POINTER(TsMapGrad), _vp]),
     "ts_pose_grad": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
     "ts_l1_loss": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
     "ts_pose_apply": (_st, [C.POINTER(TsPlan), _vp, _vp, _vp]),
@@ -272,6 +274,14 @@ def ts_render_bwd(plan, ws, dC, dD, dA, grad: Optional[TsMapGrad], stream=None):
     g = grad if grad is not None else TsMapGrad()
     _check(lib().ts_render_bwd(C.byref(plan), _ptr(ws), _ptr(dC), _ptr(dD), _ptr(dA), C.byref(g), _stream(stream)),
            "ts_render_bwd")
+
+
+def ts_render_step_l1(plan, ws, tgt_color, tgt_depth, lambda_dep, color, depth, alpha, loss, dC, dD,
+                      grad: Optional[TsMapGrad], stream=None):
+    g = grad if grad is not None else TsMapGrad()
+    _check(lib().ts_render_step_l1(C.byref(plan), _ptr(ws), _ptr(tgt_color), _ptr(tgt_depth), float(lambda_dep),
+                                   _ptr(color), _ptr(depth), _ptr(alpha), _ptr(loss), _ptr(dC), _ptr(dD), C.byref(g),
+                                   _stream(stream)), "ts_render_step_l1")
 
 
 def ts_equilateral(plan, tsmap: TsMap, ws, weight, loss, grad: Optional[TsMapGrad] = None, stream=None):

@@ -63,6 +63,14 @@ struct RenderArgs {
   float* normal;       // normal map output (may be null)
   const float* dN;     // gradient w.r.t. the normal map (may be null)
   uint32_t* cov;       // per (view, face) pixels blended by the forward (TS_FLAG_STATS), else null
+  // fused L1 step (ts_render_step_l1): targets, depth weight, optional loss-gradient images and
+  // the per-tile loss partials
+  const float* tC;
+  const float* tD;
+  float lambda_dep;
+  float* dC_out;
+  float* dD_out;
+  float* tloss;
   TsDevHeader* hdr;
 };
 
@@ -82,6 +90,7 @@ constexpr int raster_min_blocks(int threads) {
 // Shared state of a render CTA.
 struct RenderSmem {
   uint16_t smask[2][128];  // per staged face, the warps (sub-blocks) that visit it
+  float lred[16][2];       // fused step: the warps' loss sums
   int view;
   int nmax;
   int next_tile;
@@ -91,6 +100,22 @@ struct RenderSmem {
 // Forward only, TS_FLAG_STATS: per staged face, the number of the tile's pixels that blended it.
 struct FwdMasks {
   uint32_t cv[2][128];
+};
+
+// What a tile's forward leaves for the backward of the fused step, per pixel (thread) and for the
+// stage buffers: the last stage processed, its buffer, and whether the stage before it is still in
+// the other buffer.
+struct TileCarry {
+  float T, C0, C1, C2, D;
+  int nl;
+  int st_last, b_last;
+  bool prev_in;
+};
+
+// The backward's per-pixel inputs in the fused step: T_final and the loss gradients.
+struct PixIn {
+  float T, gC0, gC1, gC2, gD;
+  int nl;
 };
 
 // Backward scratch per warp: a queue of contributing (face, pixel) entries found by the visits,
@@ -221,9 +246,9 @@ __device__ __forceinline__ void wait_stage() {
 }
 
 // Forward of one tile; seq counts the stages this CTA has staged so far (buffer seq & 1 is next).
-template <int TW, int TH, bool AUX>
+template <int TW, int TH, bool AUX, bool FUSED = false>
 __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
-                                         FwdMasks& fm, int& seq) {
+                                         FwdMasks& fm, int& seq, TileCarry* carry = nullptr) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint2 rg = a.ranges[tile];
@@ -233,6 +258,8 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, fl
   int nl = 0;
   bool done = !g.inimg;
   unsigned contrib = 0;
+  int st_last = -1, b_last = 0;
+  bool prefetched = false;
   if (n > 0) {
     const int S = a.S;
     const int nst = (n + S - 1) / S;
@@ -244,6 +271,8 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, fl
       const int cnt = min(S, n - st * S);
       wait_stage();
       ++seq;
+      st_last = st;
+      b_last = b;
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
       stage_masks<TW, TH>(rb, sm.smask[b], cnt, g.X0, g.Y0);
@@ -313,12 +342,24 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, fl
         if (st + 1 < nst) {  // a prefetched stage is in flight: let it land before leaving
           wait_stage();
           ++seq;
+          prefetched = true;
         }
         break;
       }
     }
   }
   count_add(&a.hdr->fwd_contrib, contrib);
+  if constexpr (FUSED) {
+    carry->T = T;
+    carry->C0 = C0;
+    carry->C1 = C1;
+    carry->C2 = C2;
+    carry->D = D;
+    carry->nl = nl;
+    carry->st_last = st_last;
+    carry->b_last = b_last;
+    carry->prev_in = st_last >= 1 && !prefetched;
+  }
   if (g.inimg) {
     const long long HW = (long long)g.vw.W * g.vw.H;
     const long long pi = (long long)g.y * g.vw.W + g.x;
@@ -392,16 +433,26 @@ __device__ __forceinline__ TsPix eval_edges_v(float4 q0, float4 q1, float4 q2, f
   return o;
 }
 
-template <int TW, int TH, bool AUX>
+template <int TW, int TH, bool AUX, bool FUSED = false>
 __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
-                                         int& seq) {
+                                         int& seq, const PixIn* pin = nullptr, const TileCarry* carry = nullptr) {
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint2 rg = a.ranges[tile];
   float T = 0.f, Sacc = 0.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
   float gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
   int nl = 0;
-  if (g.inimg) {
+  if (FUSED) {  // the forward's state and the loss gradients, still in registers
+    if (g.inimg) {
+      T = pin->T;
+      nl = pin->nl;
+      gC0 = pin->gC0;
+      gC1 = pin->gC1;
+      gC2 = pin->gC2;
+      gD = pin->gD;
+      Sacc = T * (gC0 * a.bg0 + gC1 * a.bg1 + gC2 * a.bg2);
+    }
+  } else if (g.inimg) {
     const long long HW = (long long)g.vw.W * g.vw.H;
     const long long pi = (long long)g.y * g.vw.W + g.x;
     const long long o = g.vw.pix_off + pi;
@@ -437,7 +488,7 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
     const int nst = (n + S - 1) / S;
     const float4* vbase = a.frec + (size_t)g.view * (size_t)a.M * 8;
     const float4* nbase = AUX ? a.aux + (size_t)g.view * (size_t)a.M : nullptr;
-    issue_stage<AUX>(a, smrec, seq & 1, nst - 1, rg.x, n, vbase, nbase, TW * TH);
+    if (!FUSED) issue_stage<AUX>(a, smrec, seq & 1, nst - 1, rg.x, n, vbase, nbase, TW * TH);
     constexpr int EW = Ring<AUX>::EW;
     unsigned char* wbase = reinterpret_cast<unsigned char*>(smrec + (size_t)2 * S * (AUX ? 9 : 8)) +
                            (size_t)warp * Ring<AUX>::BYTES_PER_WARP;
@@ -452,7 +503,7 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
     int head = 0, fill = 0;  // the queue's entries (the same in every lane)
     for (int k = 0; k < nst; ++k) {
       const int st = nst - 1 - k;
-      const int b = seq & 1;
+      int b = seq & 1;
       const int cnt = min(S, n - st * S);
       // The forward's lane masks (positions below the tile's largest list position after a
       // contribution were all written by it) give, per face, the pixels of this warp that blended
@@ -461,11 +512,26 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
       const uint32_t* lmrow = a.lmask + (size_t)(rg.x + (uint32_t)(st * S)) * (TW * TH / 32) + warp;
       int qq = (cnt - 1) >> 5;
       unsigned lmc = qq * 32 + lane < cnt ? lmrow[(size_t)(qq * 32 + lane) * (TW * TH / 32)] : 0u;
-      wait_stage();
-      ++seq;
+      if (FUSED) {
+        // the forward's last stage, and the one before it unless a prefetch replaced it, are
+        // still staged; other stages are staged again (all warps are done with both buffers)
+        if (st == carry->st_last) {
+          b = carry->b_last;
+        } else if (st == carry->st_last - 1 && carry->prev_in) {
+          b = carry->b_last ^ 1;
+        } else {
+          __syncthreads();
+          b = 0;
+          issue_stage<AUX>(a, smrec, b, st, rg.x, n, vbase, nbase, TW * TH);
+          wait_stage();
+        }
+      } else {
+        wait_stage();
+        ++seq;
+        if (k + 1 < nst) issue_stage<AUX>(a, smrec, b ^ 1, st - 1, rg.x, n, vbase, nbase, TW * TH);
+      }
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
-      if (k + 1 < nst) issue_stage<AUX>(a, smrec, b ^ 1, st - 1, rg.x, n, vbase, nbase, TW * TH);
       unsigned bits = __ballot_sync(FULL, lmc != 0u);
       for (;;) {
         while (!bits && qq > 0) {
@@ -606,6 +672,64 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
   count_add(&a.hdr->bwd_contrib, contrib);
 }
 
+// The fused L1 step of one tile: the forward, the mean-L1 loss of its pixels (Eq. 8 L1 part with
+// the depth term of Eq. 9: per pixel dL/dC = sign(C - Cbar) / (3HW) on the colour image with its
+// background term, dL/dD = lambda_dep sign(D - Dbar) / (HW) where Dbar > 0), the tile's loss sums
+// in a fixed order, and the backward from those gradients -- the same values ts_render_fwd,
+// ts_l1_loss and ts_render_bwd give, without the images' round trip through memory.
+template <int TW, int TH>
+__device__ __forceinline__ void step_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
+                                          FwdMasks& fm, int& seq) {
+  TileCarry c;
+  fwd_tile<TW, TH, false, true>(a, tile, smrec, sm, fm, seq, &c);
+  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  PixIn pin{c.T, 0.f, 0.f, 0.f, 0.f, c.nl};
+  float lc = 0.f, ld = 0.f;
+  if (g.inimg) {
+    const long long HW = (long long)g.vw.W * g.vw.H;
+    const long long pi = (long long)g.y * g.vw.W + g.x;
+    const long long o = g.vw.pix_off + pi;
+    const float ic = 1.0f / (3.0f * (float)HW), id = a.lambda_dep / (float)HW;
+    const float col[3] = {c.C0 + c.T * a.bg0, c.C1 + c.T * a.bg1, c.C2 + c.T * a.bg2};  // the colour image
+    float gc[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const long long q = 3 * g.vw.pix_off + ch * HW + pi;
+      const float r = col[ch] - a.tC[q];
+      lc += fabsf(r);
+      gc[ch] = r > 0.f ? ic : (r < 0.f ? -ic : 0.f);
+      if (a.dC_out) a.dC_out[q] = gc[ch];
+    }
+    const float t = a.tD[o];
+    const float r = c.D - t;
+    const bool valid = t > 0.f;
+    if (valid) ld += fabsf(r);
+    pin.gD = valid ? (r > 0.f ? id : (r < 0.f ? -id : 0.f)) : 0.f;
+    if (a.dD_out) a.dD_out[o] = pin.gD;
+    pin.gC0 = gc[0];
+    pin.gC1 = gc[1];
+    pin.gC2 = gc[2];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lc += __shfl_xor_sync(FULL, lc, o);
+    ld += __shfl_xor_sync(FULL, ld, o);
+  }
+  if (lane == 0) {
+    sm.lred[warp][0] = lc;
+    sm.lred[warp][1] = ld;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    float sum = 0.f;
+#pragma unroll
+    for (int w = 0; w < TW * TH / 32; ++w) sum += sm.lred[w][threadIdx.x];
+    a.tloss[2 * tile + threadIdx.x] = sum;
+  }
+  bwd_tile<TW, TH, false, true>(a, tile, smrec, sm, seq, &pin, &c);
+}
+
 // Next tile of a persistent CTA (the same value in every thread), or -1 when none is left.
 __device__ __forceinline__ long long next_tile(const RenderArgs& a, RenderSmem& sm) {
   __syncthreads();
@@ -639,6 +763,71 @@ __global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_
   }
   for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
     bwd_tile<TW, TH, AUX>(a, t, smrec, sm, seq);
+}
+
+// The fused step kernel.  Its forward's coverage counts (TS_FLAG_STATS) live in the space of the
+// backward's rings, which the forward does not use.
+template <int TW, int TH, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_step(RenderArgs a) {
+  extern __shared__ __align__(128) float4 smrec[];
+  __shared__ RenderSmem sm;
+  static_assert(sizeof(FwdMasks) <= (TW * TH / 32) * Ring<false>::BYTES_PER_WARP, "coverage counts fit the rings");
+  FwdMasks& fm = *reinterpret_cast<FwdMasks*>(smrec + (size_t)2 * a.S * 8);
+  int seq = 0;
+  if (!PERSIST) {
+    step_tile<TW, TH>(a, blockIdx.x, smrec, sm, fm, seq);
+    return;
+  }
+  for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm)) step_tile<TW, TH>(a, t, smrec, sm, fm, seq);
+}
+
+// Per view, the sum of its tiles' loss partials in a fixed order.
+__global__ void __launch_bounds__(256) k_loss_tiles(const TsView* __restrict__ views, const float* __restrict__ tloss,
+                                                    float lambda_dep, float* __restrict__ loss) {
+  __shared__ float red[256][2];
+  const TsView& vw = views[blockIdx.x];
+  const long long t0 = vw.tile_off, nt = (long long)vw.TX * vw.TY;
+  float x = 0.f, y = 0.f;
+  for (long long t = threadIdx.x; t < nt; t += 256) {
+    x += tloss[2 * (t0 + t)];
+    y += tloss[2 * (t0 + t) + 1];
+  }
+  red[threadIdx.x][0] = x;
+  red[threadIdx.x][1] = y;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[threadIdx.x][0] += red[threadIdx.x + o][0];
+      red[threadIdx.x][1] += red[threadIdx.x + o][1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double HW = (double)vw.W * vw.H;
+    loss[blockIdx.x] = (float)((double)red[0][0] / (3.0 * HW) + (double)lambda_dep * (double)red[0][1] / HW);
+  }
+}
+
+template <int TW, int TH>
+cudaError_t launch_step(bool persist, const RenderArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)2 * a.S * 128 + (size_t)(TW * TH / 32) * Ring<false>::BYTES_PER_WARP;
+  if (a.n_tiles == 0) return cudaSuccess;
+  const void* f = persist ? (const void*)k_render_step<TW, TH, true> : (const void*)k_render_step<TW, TH, false>;
+  cudaError_t e = ts_smem_limit(f, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (!persist) {
+    k_render_step<TW, TH, false><<<(unsigned)a.n_tiles, TW * TH, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_step<TW, TH, true>, TW * TH, smem);
+  const long long grid = std::max(1LL, std::min<long long>(a.n_tiles, (long long)sms * std::max(per_sm, 1)));
+  e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  k_render_step<TW, TH, true><<<(unsigned)grid, TW * TH, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 // Dynamic shared memory: two stage buffers of S 128-byte records, then (with the side array) two
@@ -720,6 +909,10 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.cov = w.cov;
   a.normal = nullptr;
   a.dN = nullptr;
+  a.tC = a.tD = nullptr;
+  a.lambda_dep = 0.f;
+  a.dC_out = a.dD_out = nullptr;
+  a.tloss = nullptr;
   return a;
 }
 
@@ -743,4 +936,32 @@ cudaError_t ts_launch_render_bwd(const TsPlanImpl* p, const TsWs& w, const float
   a.dA = dA;
   a.dN = dN;
   return dispatch(false, p, a, s);
+}
+
+cudaError_t ts_launch_render_step(const TsPlanImpl* p, const TsWs& w, const float* tgt_color, const float* tgt_depth,
+                                  float lambda_dep, float* color, float* depth, float* alpha, float* loss, float* dC,
+                                  float* dD, cudaStream_t s) {
+  RenderArgs a = base_args(p, w);
+  a.color = color;
+  a.depth = depth;
+  a.alpha = alpha;
+  a.tC = tgt_color;
+  a.tD = tgt_depth;
+  a.lambda_dep = lambda_dep;
+  a.dC_out = dC;
+  a.dD_out = dD;
+  a.tloss = w.tloss;
+  const int tw = p->prm.tile_w, th = p->prm.tile_h;
+  const bool persist = (p->prm.flags & TS_FLAG_PERSISTENT) != 0;
+  cudaError_t e;
+  if (tw == 16 && th == 8) e = launch_step<16, 8>(persist, a, s);
+  else if (tw == 16 && th == 16) e = launch_step<16, 16>(persist, a, s);
+  else if (tw == 8 && th == 8) e = launch_step<8, 8>(persist, a, s);
+  else if (tw == 32 && th == 8) e = launch_step<32, 8>(persist, a, s);
+  else if (tw == 16 && th == 32) e = launch_step<16, 32>(persist, a, s);
+  else if (tw == 32 && th == 16) e = launch_step<32, 16>(persist, a, s);
+  else e = cudaErrorInvalidValue;
+  if (e != cudaSuccess) return e;
+  k_loss_tiles<<<p->V, 256, 0, s>>>(w.views, w.tloss, lambda_dep, loss);
+  return cudaGetLastError();
 }

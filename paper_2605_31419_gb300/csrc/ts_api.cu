@@ -157,6 +157,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_bsums = take((size_t)(p->n_tile_scan_blocks + 1) * 4);
   p->o_tlarge = take((size_t)toff * 4);
   p->o_tmat = take((size_t)toff * (size_t)p->bin_blocks * 4);
+  p->o_tloss = take((size_t)toff * 2 * 4);
   p->o_keys0 = take((size_t)cap * 8);
   p->o_keys1 = take((size_t)cap * 8);
   p->o_vals0 = take((size_t)cap * 4);
@@ -282,6 +283,28 @@ ts_status ts_render_bwd_n(const ts_plan* plan, void* ws, const float* dC, const 
   {
     StageTimer t(p, TS_STAGE_BWD_RASTER, s);
     e = ts_launch_render_bwd(p, w, dC, dD, dA, dN, s);
+  }
+  if (e != cudaSuccess) return TS_ERR_CUDA;
+  StageTimer t(p, TS_STAGE_BWD_PROJECT, s);
+  ts_map_grad none;
+  memset(&none, 0, sizeof(none));
+  return cuda_status(ts_launch_project_bwd(p, w, grad ? grad : &none, s));
+}
+
+ts_status ts_render_step_l1(const ts_plan* plan, void* ws, const float* tgt_color, const float* tgt_depth,
+                           float lambda_dep, float* color, float* depth, float* alpha, float* loss, float* dC,
+                           float* dD, const ts_map_grad* grad, ts_stream stream) {
+  const TsPlanImpl* p = impl(plan);
+  if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) || !tgt_color || !tgt_depth || !color || !loss)
+    return TS_ERR_INVALID_ARG;
+  if (!(lambda_dep >= 0.0f) || !std::isfinite(lambda_dep)) return TS_ERR_INVALID_ARG;
+  if (p->normals || p->face_sigma) return TS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  TsWs w = ts_ws(p, ws);
+  cudaError_t e;
+  {
+    StageTimer t(p, TS_STAGE_FWD, s);
+    e = ts_launch_render_step(p, w, tgt_color, tgt_depth, lambda_dep, color, depth, alpha, loss, dC, dD, s);
   }
   if (e != cudaSuccess) return TS_ERR_CUDA;
   StageTimer t(p, TS_STAGE_BWD_PROJECT, s);

@@ -92,7 +92,7 @@ struct TsPlanImpl {
   bool min_opacity;  // TS_FLAG_MIN_OPACITY
   bool face_sigma;   // TS_FLAG_FACE_SIGMA
   // workspace layout (byte offsets)
-  size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_tcnt, o_bsums, o_tlarge, o_tmat, o_keys0, o_keys1,
+  size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_tcnt, o_bsums, o_tlarge, o_tmat, o_tloss, o_keys0, o_keys1,
       o_vals0, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_lmask, o_pho, o_equi, o_aux, o_nloss,
       o_cov, total;
   void* events[2 * TS_N_STAGES];
@@ -113,6 +113,7 @@ struct TsWs {
   uint32_t* tcnt;    // per tile: pairs (binning)
   uint32_t* tlarge;  // tiles whose pair lists the CTA-wide sort takes
   uint32_t* tmat;    // [tile][face block] pair counts, then their exclusive scan
+  float* tloss;      // fused L1 step: per tile, the colour and depth L1 sums
   uint32_t* bsums;
   unsigned long long* keys[2];  // [0]: the sorted pair keys; [1]: the tile segments before their sort
   uint32_t* vals[1];            // the sorted pairs' face ids
@@ -144,6 +145,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.tcnt = (uint32_t*)(b + p->o_tcnt);
   w.tlarge = (uint32_t*)(b + p->o_tlarge);
   w.tmat = (uint32_t*)(b + p->o_tmat);
+  w.tloss = (float*)(b + p->o_tloss);
   w.bsums = (uint32_t*)(b + p->o_bsums);
   w.keys[0] = (unsigned long long*)(b + p->o_keys0);
   w.keys[1] = (unsigned long long*)(b + p->o_keys1);
@@ -177,6 +179,9 @@ cudaError_t ts_launch_normal_loss(const TsPlanImpl* p, const TsWs& w, const floa
                                   float weight, float* loss, float* dN, cudaStream_t s);
 cudaError_t ts_launch_render_fwd(const TsPlanImpl* p, const TsWs& w, float* color, float* depth, float* alpha,
                                  float* normal, cudaStream_t s);
+cudaError_t ts_launch_render_step(const TsPlanImpl* p, const TsWs& w, const float* tgt_color, const float* tgt_depth,
+                                  float lambda_dep, float* color, float* depth, float* alpha, float* loss, float* dC,
+                                  float* dD, cudaStream_t s);
 cudaError_t ts_launch_render_bwd(const TsPlanImpl* p, const TsWs& w, const float* dC, const float* dD,
                                  const float* dA, const float* dN, cudaStream_t s);
 cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_map_grad* g, cudaStream_t s);

@@ -126,6 +126,17 @@ class Rasterizer:
         else:
             B.ts_render_bwd(self.plan, self.ws, dC, dD, dA, g, stream)
 
+    def step_l1(self, tgt_color, tgt_depth, lambda_dep: float = 0.05, grad: Optional[Map] = None, stream=None,
+                loss_grads: bool = False):
+        """The forward, the mean-L1 loss and the backward of one step in one pass per tile (after
+        ``project`` and ``bin``): the images in the rasterizer's buffers, the per-view loss, and the
+        map gradients added into ``grad``; ``pose_grad`` then gives the pose gradients.  With
+        ``loss_grads`` the loss's image gradients are also written to ``dC`` and ``dD``."""
+        g = B.make_grad(grad.pos, grad.col, grad.opa, grad.sigma) if grad is not None else None
+        B.ts_render_step_l1(self.plan, self.ws, tgt_color, tgt_depth, lambda_dep, self.color, self.depth, self.alpha,
+                            self.loss_v, self.dC if loss_grads else None, self.dD if loss_grads else None, g, stream)
+        return self.loss_v
+
     def pose_grad(self, out=None, stream=None):
         out = self.dtau if out is None else out
         B.ts_pose_grad(self.plan, self.ws, out, stream)

@@ -90,6 +90,19 @@ def test_device_calls_reject_null_arguments(ts):
     assert L.ts_render_bwd(C.byref(plan), C.c_void_p(256), None, None, None, None, None) == 1
     assert L.ts_pose_grad(C.byref(plan), None, None, None) == 1
     vp = [C.c_void_p(256)] * 4
+    # fused L1 step: null targets or outputs, a negative or non-finite depth weight, and a plan with
+    # the normal map
+    z = C.c_void_p(256)
+    assert L.ts_render_step_l1(C.byref(plan), z, None, z, C.c_float(0.05), z, None, None, z, None, None, None,
+                               None) == 1
+    assert L.ts_render_step_l1(C.byref(plan), z, z, z, C.c_float(0.05), None, None, None, z, None, None, None,
+                               None) == 1
+    for lam in (-1.0, float("inf"), float("nan")):
+        assert L.ts_render_step_l1(C.byref(plan), z, z, z, C.c_float(lam), z, None, None, z, None, None, None,
+                                   None) == 1
+    nplan = ts.ts_plan_init(np.array([[10, 10, 5, 5, 16, 16]]), 4, ts.ts_default_params(flags=ts.TS_FLAG_NORMALS))
+    assert L.ts_render_step_l1(C.byref(nplan), z, z, z, C.c_float(0.05), z, None, None, z, None, None, None,
+                               None) == 1
     # photometric loss: null buffers, lambda_ssim outside [0, 1], negative or non-finite lambda_dep
     assert L.ts_pho_loss(C.byref(plan), C.c_void_p(256), *vp, C.c_float(0.2), C.c_float(0.05), None, None, None,
                          None) == 1

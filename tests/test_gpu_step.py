@@ -1,0 +1,95 @@
+"""The fused L1 step (ts_render_step_l1) against the separate calls and the oracle (needs a GB300).
+
+Against ts_render_fwd + ts_l1_loss + ts_render_bwd on the same inputs: the images and the loss's
+image gradients bit for bit (the same per-pixel arithmetic), the per-view loss to float rounding
+(other partial sums).  Against the oracle: the loss, the map gradients and the pose gradient with
+the tolerances of the separate path.  The scenes cover tiles whose lists span many stages (the
+backward stages them again) and tiles whose pixels all stop early (a prefetched stage replaced the
+one before the last).
+"""
+import numpy as np
+import pytest
+
+from harness import assert_grad, assert_images, assert_pose_grad, gpu_run, oracle_run, pack_targets, params_pair
+from ts_synth.scenes import random_triangles_scene, room_map, trajectory_poses, noise_targets, Scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged_room():
+    pos, col, opa = room_map(3, 20000)
+    cams = np.array([[70.0, 70.0, 50.0, 37.5, 100, 75], [40.0, 40.0, 28.5, 16.5, 57, 33],
+                     [90.0, 90.0, 61.0, 40.0, 123, 81]])
+    sc = Scene(pos, col, opa, None, cams, trajectory_poses(1003, 3))
+    sc.tgt_color, sc.tgt_depth = noise_targets(4, cams)
+    return sc
+
+
+SCENES = {
+    "c1": lambda: random_triangles_scene(seed=1),
+    "ragged_room": _ragged_room,
+    # lists of ~1500 faces per tile: 24 stages of 64, all but the last two staged again
+    "long_lists": lambda: random_triangles_scene(seed=6, n_faces=3000, W=48, H=32, f=40.0, side_lo=0.6,
+                                                 side_hi=1.2, z_lo=1.0, z_hi=2.0),
+    # faint faces, lists of ~100: no pixel stops, the last two stages are both still staged
+    "translucent": lambda: random_triangles_scene(seed=8, n_faces=150, W=64, H=48, f=60.0, side_lo=0.6,
+                                                  side_hi=1.2, z_lo=1.0, z_hi=2.0, opa_lo=0.02, opa_hi=0.05),
+    # nearly opaque faces: pixels stop after a few faces, most tiles end the forward early
+    "opaque": lambda: random_triangles_scene(seed=7, n_faces=4000, W=96, H=64, f=80.0, side_lo=0.3, side_hi=0.8,
+                                             opa_lo=0.995, opa_hi=1.0),
+}
+
+
+def step_run(sc, p, lambda_dep=0.05, pair_capacity=0):
+    import torch
+    import paper_2605_31419_gb300 as ts
+    rast = ts.Rasterizer(sc.cams, sc.n_faces, p, pair_capacity=pair_capacity)
+    m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa, sc.faces)
+    poses = ts.poses_tensor(sc.poses)
+    tc, td = pack_targets(sc)
+    tc = torch.as_tensor(tc, dtype=torch.float32, device="cuda")
+    td = torch.as_tensor(td, dtype=torch.float32, device="cuda")
+    rast.project(m, poses)
+    rast.bin()
+    g = m.zeros_like()
+    loss = rast.step_l1(tc, td, lambda_dep, g, loss_grads=True)
+    dtau = rast.pose_grad()
+    torch.cuda.synchronize()
+    f = lambda t: t.cpu().numpy().astype(np.float64)  # noqa: E731
+    return dict(color=f(rast.color), depth=f(rast.depth), alpha=f(rast.alpha), loss_v=f(loss), dC=f(rast.dC),
+                dD=f(rast.dD), dpos=f(g.pos).T, dcol=f(g.col).T, dopa=f(g.opa), dtau=f(dtau),
+                counters=rast.counters(raise_on_error=False))
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_step_matches_separate_calls_and_oracle(oracle, name):
+    sc = SCENES[name]()
+    p, po = params_pair()
+    s = step_run(sc, p, pair_capacity=1_000_000)
+    assert s["counters"]["status"] == "TS_OK"
+    g = gpu_run(sc, p, pair_capacity=1_000_000)
+    for k in ("color", "depth", "alpha", "dC", "dD"):
+        assert np.array_equal(s[k], g[k]), f"{k} differs from the separate calls"
+    assert_images(s["loss_v"], g["loss_v"], "loss vs separate", atol=1e-7, rtol=1e-6)
+    assert s["counters"]["fwd_contrib"] == s["counters"]["bwd_contrib"] == g["counters"]["bwd_contrib"] > 0
+    r = oracle_run(oracle, sc, po)
+    assert_images(s["loss_v"], r["loss_v"], "loss", atol=1e-6, rtol=1e-5)
+    assert_grad(s["dpos"], r["dpos"], "dpos")
+    assert_grad(s["dcol"], r["dcol"], "dcol")
+    assert_grad(s["dopa"], r["dopa"], "dopa")
+    assert_pose_grad(s["dtau"], r["dtau"], r["dtau_abs"])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)], ids=lambda t: f"{t[0]}x{t[1]}")
+def test_step_tiles_and_persistent(oracle, tile):
+    import paper_2605_31419_gb300 as ts
+    sc = SCENES["c1"]()
+    for flags in (0, ts.TS_FLAG_PERSISTENT):
+        p, po = params_pair(tile_w=tile[0], tile_h=tile[1], flags=flags)
+        s = step_run(sc, p)
+        g = gpu_run(sc, p)
+        for k in ("color", "dC", "dD"):
+            assert np.array_equal(s[k], g[k]), k
+        r = oracle_run(oracle, sc, po)
+        assert_grad(s["dpos"], r["dpos"], "dpos")
+        assert_grad(s["dopa"], r["dopa"], "dopa")
