@@ -91,6 +91,7 @@ constexpr int raster_min_blocks(int threads) {
 struct RenderSmem {
   uint16_t smask[2][128];  // per staged face, the warps (sub-blocks) that visit it
   float lred[16][2];       // fused step: the warps' loss sums
+  int lmax[16];            // fused step: the warps' largest last positions
   int view;
   int nmax;
   int next_tile;
@@ -116,6 +117,7 @@ struct TileCarry {
 struct PixIn {
   float T, gC0, gC1, gC2, gD;
   int nl;
+  int nmax;  // the same in every thread: the tile's largest nl
 };
 
 // Backward scratch per warp: a queue of contributing (face, pixel) entries found by the visits,
@@ -248,8 +250,9 @@ __device__ __forceinline__ void wait_stage() {
 // Forward of one tile; seq counts the stages this CTA has staged so far (buffer seq & 1 is next).
 template <int TW, int TH, bool AUX, bool FUSED = false>
 __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
-                                         FwdMasks& fm, int& seq, TileCarry* carry = nullptr) {
-  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
+                                         FwdMasks& fm, int& seq, TileCarry* carry = nullptr,
+                                         const TileGeom<TW, TH>* gin = nullptr) {
+  const TileGeom<TW, TH> g = FUSED ? *gin : tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint2 rg = a.ranges[tile];
   const int n = (int)(rg.y - rg.x);
@@ -435,8 +438,9 @@ __device__ __forceinline__ TsPix eval_edges_v(float4 q0, float4 q1, float4 q2, f
 
 template <int TW, int TH, bool AUX, bool FUSED = false>
 __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
-                                         int& seq, const PixIn* pin = nullptr, const TileCarry* carry = nullptr) {
-  const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
+                                         int& seq, const PixIn* pin = nullptr, const TileCarry* carry = nullptr,
+                                         const TileGeom<TW, TH>* gin = nullptr) {
+  const TileGeom<TW, TH> g = FUSED ? *gin : tile_geom<TW, TH>(a, tile, sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint2 rg = a.ranges[tile];
   float T = 0.f, Sacc = 0.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
@@ -472,16 +476,22 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
     }
     Sacc = T * (gC0 * a.bg0 + gC1 * a.bg1 + gC2 * a.bg2);
   }
-  if (threadIdx.x == 0) sm.nmax = 0;
-  __syncthreads();
-  {
-    const int m = __reduce_max_sync(FULL, (unsigned)nl);
-    if (lane == 0 && m) atomicMax(&sm.nmax, m);
+  int nmax;
+  if (FUSED) {
+    nmax = pin->nmax;  // the tile's largest last position, reduced with the loss sums
+  } else {
+    if (threadIdx.x == 0) sm.nmax = 0;
+    __syncthreads();
+    {
+      const int m = __reduce_max_sync(FULL, (unsigned)nl);
+      if (lane == 0 && m) atomicMax(&sm.nmax, m);
+    }
+    __syncthreads();
+    nmax = sm.nmax;
   }
-  __syncthreads();
   // positions come from the forward pass over the same lists; clamp in case the caller did not
   // run it after the last ts_bin
-  const int n = min(sm.nmax, (int)(rg.y - rg.x));
+  const int n = min(nmax, (int)(rg.y - rg.x));
   unsigned contrib = 0;
   if (n > 0) {
     const int S = a.S;
@@ -681,10 +691,10 @@ template <int TW, int TH>
 __device__ __forceinline__ void step_tile(const RenderArgs& a, long long tile, float4* smrec, RenderSmem& sm,
                                           FwdMasks& fm, int& seq) {
   TileCarry c;
-  fwd_tile<TW, TH, false, true>(a, tile, smrec, sm, fm, seq, &c);
   const TileGeom<TW, TH> g = tile_geom<TW, TH>(a, tile, sm);
+  fwd_tile<TW, TH, false, true>(a, tile, smrec, sm, fm, seq, &c, &g);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  PixIn pin{c.T, 0.f, 0.f, 0.f, 0.f, c.nl};
+  PixIn pin{c.T, 0.f, 0.f, 0.f, 0.f, c.nl, 0};
   float lc = 0.f, ld = 0.f;
   if (g.inimg) {
     const long long HW = (long long)g.vw.W * g.vw.H;
@@ -716,9 +726,11 @@ __device__ __forceinline__ void step_tile(const RenderArgs& a, long long tile, f
     lc += __shfl_xor_sync(FULL, lc, o);
     ld += __shfl_xor_sync(FULL, ld, o);
   }
+  const int wmax = (int)__reduce_max_sync(FULL, (unsigned)c.nl);
   if (lane == 0) {
     sm.lred[warp][0] = lc;
     sm.lred[warp][1] = ld;
+    sm.lmax[warp] = wmax;
   }
   __syncthreads();
   if (threadIdx.x < 2) {
@@ -727,7 +739,9 @@ __device__ __forceinline__ void step_tile(const RenderArgs& a, long long tile, f
     for (int w = 0; w < TW * TH / 32; ++w) sum += sm.lred[w][threadIdx.x];
     a.tloss[2 * tile + threadIdx.x] = sum;
   }
-  bwd_tile<TW, TH, false, true>(a, tile, smrec, sm, seq, &pin, &c);
+#pragma unroll
+  for (int w = 0; w < TW * TH / 32; ++w) pin.nmax = max(pin.nmax, sm.lmax[w]);
+  bwd_tile<TW, TH, false, true>(a, tile, smrec, sm, seq, &pin, &c, &g);
 }
 
 // Next tile of a persistent CTA (the same value in every thread), or -1 when none is left.

@@ -93,3 +93,31 @@ def test_step_tiles_and_persistent(oracle, tile):
         r = oracle_run(oracle, sc, po)
         assert_grad(s["dpos"], r["dpos"], "dpos")
         assert_grad(s["dopa"], r["dopa"], "dopa")
+
+
+def test_step_with_map_statistics(oracle):
+    """With TS_FLAG_STATS the fused step counts each face's blended pixels (in the shared memory
+    its backward later uses for the rings): the same counts as the separate forward."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    sc = _ragged_room()
+    p, po = params_pair(flags=ts.TS_FLAG_STATS)
+    rast = ts.Rasterizer(sc.cams, sc.n_faces, p)
+    m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa, sc.faces)
+    poses = ts.poses_tensor(sc.poses)
+    tc, td = pack_targets(sc)
+    tc = torch.as_tensor(tc, dtype=torch.float32, device="cuda")
+    td = torch.as_tensor(td, dtype=torch.float32, device="cuda")
+    rast.forward(m, poses)
+    sep = rast.face_stats()
+    sep = {k: v.cpu().numpy() for k, v in sep.items()}
+    rast.project(m, poses)
+    rast.bin()
+    g = m.zeros_like()
+    rast.step_l1(tc, td, 0.05, g)
+    fused = {k: v.cpu().numpy() for k, v in rast.face_stats().items()}
+    assert sep["coverage"].sum() > 0
+    for k in ("coverage", "area", "visible", "n_visible"):
+        assert np.array_equal(fused[k], sep[k]), k
+    r = oracle_run(oracle, sc, po)
+    assert_grad(g.pos.cpu().numpy().astype(np.float64).T, r["dpos"], "dpos")
