@@ -39,7 +39,7 @@ FLOPS_PHO = 394.0
 # scaled by the views of the launch; reported only for that launch configuration
 BWD_TRAFFIC_PER_VIEW = (188.842752e6 + 23.260928e6) / 4
 # DRAM bytes per view of one k_render_step launch (ncu capture of the 4-view case)
-STEP_TRAFFIC_PER_VIEW = (150.627584e6 + 99.631616e6) / 4
+STEP_TRAFFIC_PER_VIEW = (150.714112e6 + 99.946240e6) / 4
 W, H, F, N_FACES, N_VIEWS = 1200, 680, 600.0, 300_000, 20
 WORKLOAD = "room 1200x680 f=600, 300k faces, 20 poses, fwd+bwd (L1 colour+depth), batched"
 
