@@ -348,8 +348,8 @@ ts_status ts_plan_layout(const ts_plan* plan, int64_t* pix_off, int64_t* tile_of
 ts_status ts_debug_copy(const ts_plan* plan, void* ws, int32_t what, void* dst, size_t bytes,
                         ts_stream stream);
 
-/* Failure-detection probe: launches one thread that waits, with the bounded wait every staged
- * kernel uses, for an mbarrier phase that nothing completes; after limit_us microseconds
+/* Failure-detection probe: launches one thread that waits, with the library's bounded wait, for
+ * an mbarrier phase that nothing completes; after limit_us microseconds
  * (1..5,000,000) it latches the timeout bit, which ts_sync_status then reports as TS_ERR_TIMEOUT.
  * Nothing is copied and nothing faults; ts_workspace_init clears the bit. */
 ts_status ts_debug_timeout_probe(const ts_plan* plan, void* ws, uint32_t limit_us, ts_stream stream);

@@ -28,7 +28,8 @@
 // into the face's accumulator with one atomic.
 //
 // Launch forms: one CTA per tile, or persistent CTAs (as many as fit on the GPU) that take tiles
-// from a device counter, keeping their mbarriers across tiles.
+// from a device counter.  The fused L1 step (ts_render_step_l1) runs a tile's forward, its loss
+// and its backward in one CTA.
 #include <algorithm>
 
 #include "ts_internal.cuh"

@@ -1,9 +1,9 @@
 // ts_internal.cuh -- internal declarations shared by libts translation units (sm_103a).
 //
 // Layout of the device workspace, the per-(view, face) screen-space record, the host plan, and
-// the device helpers every kernel uses: the fixed-order FP32 projection (Eq. 1), the
-// cancellation-free edge functions (Eq. 2-3), the TMA bulk copy with an mbarrier, and bounded
-// waits that report a timeout instead of hanging.
+// the device helpers the kernels use: the fixed-order FP32 projection (Eq. 1), the
+// cancellation-free edge functions (Eq. 2-3), 16-byte cp.async staging, and an mbarrier wait
+// that reports a timeout instead of hanging (the failure-detection probe).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -306,19 +306,6 @@ __device__ __forceinline__ void ts_fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ void ts_mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ts_smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// One TMA bulk copy global -> shared, completing on an mbarrier (16-byte aligned, size % 16 == 0).
-__device__ __forceinline__ void ts_bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          ts_smem_u32(dst_smem)),
-      "l"(src_gmem), "r"(bytes), "r"(ts_smem_u32(bar))
-      : "memory");
-}
 
 // 16-byte asynchronous copy global -> shared through the load path (cp.async, cache-global), and
 // its group commit and wait (a thread waits for its own copies; a barrier then publishes them).
