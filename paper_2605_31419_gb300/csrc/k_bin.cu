@@ -230,6 +230,8 @@ struct MatArgs {
 };
 
 constexpr int BIN_T = 1024;
+constexpr int BIN_PER = TS_BIN_FACES / BIN_T;  // faces per thread
+static_assert(TS_BIN_FACES % BIN_T == 0, "whole faces per thread");
 
 __global__ void __launch_bounds__(BIN_T) k_bin_counts(MatArgs a) {
   extern __shared__ uint32_t hcnt[];
@@ -239,13 +241,20 @@ __global__ void __launch_bounds__(BIN_T) k_bin_counts(MatArgs a) {
   const int T = vw.TX * vw.TY;
   for (int t = threadIdx.x; t < T; t += BIN_T) hcnt[t] = 0u;
   __syncthreads();
-  const long long m0 = blk * TS_BIN_FACES;
-  for (int i = threadIdx.x; i < TS_BIN_FACES; i += BIN_T) {
-    const long long m = m0 + i;
-    if (m >= a.M) break;
+  const long long m0 = blk * TS_BIN_FACES + threadIdx.x;
+  uint32_t cnt[BIN_PER];
+  short4 rc[BIN_PER];
+#pragma unroll
+  for (int k = 0; k < BIN_PER; ++k) {  // all loads first, so that their latencies overlap
+    const long long m = m0 + (long long)k * BIN_T;
     const long long idx = (long long)v * a.M + m;
-    if (a.count[idx] == 0) continue;
-    const short4 r = a.rect[idx];
+    cnt[k] = m < a.M ? a.count[idx] : 0u;
+    rc[k] = m < a.M ? a.rect[idx] : make_short4(0, 0, -1, -1);
+  }
+#pragma unroll
+  for (int k = 0; k < BIN_PER; ++k) {
+    if (cnt[k] == 0) continue;  // (an invisible face's rectangle is -1)
+    const short4 r = rc[k];
     for (int ty = r.y; ty <= r.w; ++ty)
       for (int tx = r.x; tx <= r.z; ++tx) atomicAdd(&hcnt[ty * vw.TX + tx], 1u);
   }
@@ -261,14 +270,22 @@ __global__ void __launch_bounds__(BIN_T) k_bin_place(MatArgs a) {
   const int T = vw.TX * vw.TY;
   for (int t = threadIdx.x; t < T; t += BIN_T) place[t] = a.mat[(vw.tile_off + t) * a.B + blk];
   __syncthreads();
-  const long long m0 = blk * TS_BIN_FACES;
-  for (int i = threadIdx.x; i < TS_BIN_FACES; i += BIN_T) {
-    const long long m = m0 + i;
-    if (m >= a.M) break;
+  const long long m0 = blk * TS_BIN_FACES + threadIdx.x;
+  uint32_t cnt[BIN_PER], zb[BIN_PER];
+  short4 rc[BIN_PER];
+#pragma unroll
+  for (int k = 0; k < BIN_PER; ++k) {  // all loads first, so that their latencies overlap
+    const long long m = m0 + (long long)k * BIN_T;
     const long long idx = (long long)v * a.M + m;
-    if (a.count[idx] == 0) continue;
-    const short4 r = a.rect[idx];
-    const unsigned long long key = ((unsigned long long)a.zbits[idx] << 32) | (uint32_t)m;
+    cnt[k] = m < a.M ? a.count[idx] : 0u;
+    rc[k] = m < a.M ? a.rect[idx] : make_short4(0, 0, -1, -1);
+    zb[k] = m < a.M ? a.zbits[idx] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < BIN_PER; ++k) {
+    if (cnt[k] == 0) continue;  // (an invisible face's rectangle is -1)
+    const short4 r = rc[k];
+    const unsigned long long key = ((unsigned long long)zb[k] << 32) | (uint32_t)(m0 + (long long)k * BIN_T);
     for (int ty = r.y; ty <= r.w; ++ty)
       for (int tx = r.x; tx <= r.z; ++tx) {
         const uint32_t pos = atomicAdd(&place[ty * vw.TX + tx], 1u);
