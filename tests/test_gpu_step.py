@@ -121,3 +121,41 @@ def test_step_with_map_statistics(oracle):
         assert np.array_equal(fused[k], sep[k]), k
     r = oracle_run(oracle, sc, po)
     assert_grad(g.pos.cpu().numpy().astype(np.float64).T, r["dpos"], "dpos")
+
+
+@pytest.mark.parametrize("case", ["empty", "all_culled", "single_bg", "offscreen_partial", "sigma1", "opaque_stack"])
+def test_step_edge_cases(oracle, case):
+    """The fused step on the separate path's edge cases: the same images and loss gradients as the
+    separate calls, and the oracle's gradients."""
+    from test_gpu_parity import _single
+    kw = {}
+    if case == "empty":
+        sc = _single(np.zeros((0, 3)))
+    elif case == "all_culled":
+        sc = _single([[0, 0, -1], [1, 0, -1], [0, 1, -1], [0, 0, 0.001], [1, 0, 0.001], [0, 1, 0.001]])
+    elif case == "single_bg":
+        sc = _single([[-0.5, -0.4, 1.5], [0.6, -0.2, 2.0], [0.0, 0.5, 1.8]])
+        kw = dict(bg=(0.2, 0.4, 0.6))
+    elif case == "offscreen_partial":
+        sc = _single([[-1.5, -0.4, 1.5], [0.6, -1.2, 2.0], [0.0, 0.5, 1.8], [0.2, 0.2, 1.0], [3.0, 0.3, 1.0],
+                      [0.4, 2.0, 1.0]])
+    elif case == "sigma1":
+        sc = random_triangles_scene(seed=8, n_faces=300, W=48, H=36, f=40.0)
+        kw = dict(sigma=1.0)
+    else:
+        z = np.array([1.0, 2.0, 4.0, 8.0, 0.5, 16.0])
+        tri = np.array([[-0.3, -0.3], [0.4, -0.3], [-0.3, 0.35]])
+        sc = _single([[x * zz, y * zz, zz] for zz in z for (x, y) in tri])
+        sc.opa[:] = 0.9
+    p, po = params_pair(**kw)
+    s = step_run(sc, p)
+    g = gpu_run(sc, p)
+    for k in ("color", "depth", "alpha", "dC", "dD"):
+        assert np.array_equal(s[k], g[k]), k
+    assert_images(s["loss_v"], g["loss_v"], "loss vs separate", atol=1e-7, rtol=1e-6)
+    r = oracle_run(oracle, sc, po)
+    assert_images(s["loss_v"], r["loss_v"], "loss", atol=1e-6, rtol=1e-5)
+    if sc.n_faces:
+        assert_grad(s["dpos"], r["dpos"], "dpos")
+        assert_grad(s["dcol"], r["dcol"], "dcol")
+        assert_grad(s["dopa"], r["dopa"], "dopa")
