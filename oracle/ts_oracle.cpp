@@ -435,7 +435,11 @@ Term eval_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px, dou
   const double oF = face_opacity(o[0], o[1], o[2], c.p.min_opacity != 0);
   t.I = I;
   t.ratio = ratio;
+#if ORACLE_MUTANT == 23
+  t.clamped = false;  // no alpha_max clamp
+#else
   t.clamped = oF * I > c.p.alpha_max;
+#endif
   t.alpha = t.clamped ? c.p.alpha_max : oF * I;
   for (int ch = 0; ch < 3; ++ch) {
     t.col[ch] = 0;
@@ -542,7 +546,11 @@ double walk_pixel(const Ctx& c, const Bins& b, int view, int x, int y, std::vect
     if (!(t.ratio > 0)) continue;           // outside the face: window is 0
     if (t.alpha < c.p.alpha_min) continue;  // R9 skip
     const double Tn = T * (1.0 - t.alpha);
+#if ORACLE_MUTANT == 24
+    if (Tn < c.p.T_min) continue;           // skip the face and keep walking
+#else
     if (Tn < c.p.T_min) break;              // R9 stop before this face
+#endif
     if (out) out->push_back(Contrib{i, m, t.alpha, T, t});
 #if ORACLE_MUTANT == 4
     T = Tn;
@@ -629,7 +637,11 @@ DualTerm dual_term(const Ctx& c, int view, int64_t m, const Proj& pr, double px,
 #endif
   DualTerm t;
   Dual a = oF * I;
+#if ORACLE_MUTANT == 23
+  t.alpha = a;
+#else
   t.alpha = a.v > c.p.alpha_max ? Dual(c.p.alpha_max) : a;
+#endif
   for (int ch = 0; ch < 3; ++ch) t.col[ch] = lam[0] * col[0][ch] + lam[1] * col[1][ch] + lam[2] * col[2][ch];
 #if ORACLE_MUTANT == 7
   t.z = lam[1] * zc[0] + lam[2] * zc[1] + lam[0] * zc[2];

@@ -276,6 +276,71 @@ def pin_termination_stack(o: Oracle):
 
 
 # ---------------------------------------------------------------------------------------------
+# The alpha_max clamp of the compositing (alpha = min(alpha_max, o_F I)): an opaque face at its
+# incentre, where I = 1, has alpha = alpha_max exactly and passes no gradient through alpha
+# ---------------------------------------------------------------------------------------------
+_TRI_345 = [(10.0, 10.0), (20.0, 10.0), (10.0, 17.5)]  # 3-4-5 triangle x 2.5; incentre (12.5, 12.5)
+
+
+def pin_alpha_max_clamp(o: Oracle):
+    z = 2.0
+    verts = [[u * z, v * z, z] for (u, v) in _TRI_345]  # fronto-parallel: projects to _TRI_345 (f = 1, c = 0)
+    cols = [[0.9, 0.1, 0.2], [0.2, 0.8, 0.3], [0.1, 0.3, 0.7]]
+    bg = (0.1, 0.2, 0.3)
+    sc = _single_face_scene(verts, cols, [1.0, 1.0, 1.0], cam=(1.0, 1.0, 0.0, 0.0, 32, 32))
+    sa = SceneArrays.of(sc)
+    i = 12 * 32 + 12  # pixel (12, 12) samples the incentre
+    tri = [c for q in _TRI_345 for c in q]
+    cp = _bary_solve(tri, 12.5, 12.5) @ sa.col  # vertex colours as stored (float32)
+    for T_min in (1e-4, 0.0):
+        prm = Params(bg=bg, T_min=T_min)
+        f = o.forward(sa, prm)
+        assert abs(f["alpha"][i] - 0.99) < 1e-12, f["alpha"][i]
+        assert abs(f["T_final"][i] - 0.01) < 1e-12, f["T_final"][i]
+        assert abs(f["depth"][i] - 0.99 * z) < 1e-12
+        for ch in range(3):
+            assert abs(f["color"][ch * 1024 + i] - (0.99 * cp[ch] + 0.01 * bg[ch])) < 1e-12, ch
+        assert o.pixel_trace(sa, prm, 0, 12, 12)["alpha"].tolist() == [0.99]
+        # a loss on the clamped pixel alone: alpha is constant there, so the opacities get nothing
+        # while the colours get alpha * lambda_k per channel
+        dC = np.zeros(3 * 1024)
+        dC[i] = 1.0
+        g = o.backward(sa, prm, dC)
+        assert np.all(g["dopa"] == 0.0), g["dopa"]
+        lam = _bary_solve(tri, 12.5, 12.5)
+        assert np.allclose(g["dcol"][:, 0], 0.99 * lam, atol=1e-12), g["dcol"]
+
+
+# ---------------------------------------------------------------------------------------------
+# Termination: the walk STOPS before the face that would take T below T_min; a later face that
+# would keep T above T_min is not blended either
+# ---------------------------------------------------------------------------------------------
+def pin_stop_at_tmin(o: Oracle):
+    # six faces of opacity 0.8 at depths 1..6 (the sixth would take T = 0.2^6 = 6.4e-5 below 1e-4),
+    # then a face of opacity 0.01 at depth 7 (T 0.2^5 * 0.99 = 3.2e-4 would stay above T_min)
+    depths = [1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0]
+    opas = [0.8] * 6 + [0.01]
+    verts = [[u * z, v * z, z] for z in depths for (u, v) in _TRI_345]
+    cols = [[0.1 * k, 0.5, 1.0 - 0.1 * k] for k in range(len(depths)) for _ in range(3)]
+    sc = _single_face_scene(verts, cols, [o_ for o_ in opas for _ in range(3)], cam=(1.0, 1.0, 0.0, 0.0, 32, 32))
+    sa = SceneArrays.of(sc)
+    prm = Params()
+    tr = o.pixel_trace(sa, prm, 0, 12, 12)
+    assert list(tr["faces"]) == [0, 1, 2, 3, 4], tr["faces"]
+    a = float(np.float32(0.8))
+    assert abs(tr["T_final"] - (1 - a) ** 5) < 1e-15
+    f = o.forward(sa, prm)
+    i = 12 * 32 + 12
+    assert f["n_last"][i] == 5, f["n_last"][i]
+    assert abs(f["T_final"][i] - (1 - a) ** 5) < 1e-15
+    w = a * (1 - a) ** np.arange(5)
+    assert abs(f["depth"][i] - (w * np.asarray(depths[:5])).sum()) < 1e-12
+    # with T_min = 0 every face blends, the last one included
+    tr0 = o.pixel_trace(sa, Params(T_min=0.0), 0, 12, 12)
+    assert list(tr0["faces"]) == list(range(7)), tr0["faces"]
+
+
+# ---------------------------------------------------------------------------------------------
 # Binning: per-tile depth-sorted lists by brute force over tiles x faces
 # ---------------------------------------------------------------------------------------------
 def pin_binning_bruteforce(o: Oracle):
@@ -750,7 +815,8 @@ def pin_fd_gradients(o: Oracle, seeds=(21, 22), sigmas=(1.0, 0.5)):
 
 
 ALL_PINS = [pin_window_closed_form, pin_barycentric, pin_projection, pin_single_triangle, pin_coverage_bruteforce,
-            pin_fronto_parallel_depth, pin_transmittance_product, pin_termination_stack, pin_binning_bruteforce,
+            pin_fronto_parallel_depth, pin_transmittance_product, pin_termination_stack, pin_alpha_max_clamp,
+            pin_stop_at_tmin, pin_binning_bruteforce,
             pin_sort_ties, pin_l1_loss, pin_ssim_scipy, pin_ssim_closed_forms, pin_pho_fd,
             pin_normal_closed_forms, pin_normal_loss, pin_min_opacity_variant, pin_face_sigma_variant,
             pin_face_stats,

@@ -12,14 +12,15 @@ leave different vertices; and for the rendered normal map (Eq. 12) a normal left
 gives it and a normal in world instead of camera space; and in the map statistics (Sec. 3.4) twice
 the projected area and a coverage that also counts skipped contributions; and for the min-opacity
 variant the mean's derivative under the minimum's value; and for the learnable-sigma variant a
-derivative in sigma without the logarithm.
+derivative in sigma without the logarithm; and in the compositing of Eq. 4 a dropped alpha_max clamp, and a
+walk that skips the face that would take T below T_min instead of stopping there.
 """
 import pytest
 
 import oracle_pins as P
 from oracle.oracle import Oracle
 
-MUTANTS = list(range(1, 23))
+MUTANTS = list(range(1, 25))
 
 
 @pytest.mark.parametrize("k", MUTANTS)
