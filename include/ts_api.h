@@ -266,7 +266,8 @@ ts_status ts_pose_grad(const ts_plan* plan, void* ws, float* dtau, ts_stream str
  *   loss_v = sum |C - Cbar| / (3HW) + lambda_dep * sum_{Dbar > 0} |D - Dbar| / (HW),
  * with dC = dloss/dC and dD = dloss/dD (overwritten; sign(0) = 0).  All pointers device, packed
  * per view; loss: float [n_views], overwritten.  Deterministic.  Uses only the workspace's
- * partial-sum region: no earlier call on the workspace is needed. */
+ * partial-sum region: no earlier call on the workspace is needed.  A negative or non-finite
+ * lambda_dep returns TS_ERR_INVALID_ARG. */
 ts_status ts_l1_loss(const ts_plan* plan, void* ws, const float* color, const float* depth,
                      const float* tgt_color, const float* tgt_depth, float lambda_dep, float* loss,
                      float* dC, float* dD, ts_stream stream);
@@ -295,9 +296,14 @@ ts_status ts_pho_loss(const ts_plan* plan, void* ws, const float* color, const f
  * Needs no plan and no workspace and allocates nothing: the per-block partial sums live in one
  * static device array of 512 KiB (65536 (view, 2048-pixel block) slots), held by every GPU that
  * loads the library until the process exits.  n_views * ceil(max W*H / 2048) above 65536 returns
- * TS_ERR_INVALID_ARG, as do null pointers and bad sizes.  The first call on a device looks up the
- * array's address (make it before any stream capture).  Each call rewrites every slot it reads,
- * so nothing carries over between calls; calls that overlap on the GPU share the array and race. */
+ * TS_ERR_INVALID_ARG, as do null pointers, bad sizes and a negative or non-finite lambda_dep.
+ * The buffers and the stream must belong to the current device, whose copy of the array the call
+ * uses; the cameras alone fix how far the kernels read and write, so each buffer must hold what
+ * they describe.  The first call on a device looks up the array's address (make it before any
+ * stream capture); the address stays valid while the device's context lives, so after a
+ * cudaDeviceReset the call must not be used on that device again.  Each call rewrites every slot
+ * it reads, so nothing carries over between calls; calls that overlap on the GPU share the array
+ * and race. */
 ts_status ts_l1_loss_noalloc(const ts_camera* cams, int32_t n_views, const float* color, const float* depth,
                              const float* tgt_color, const float* tgt_depth, float lambda_dep, float* loss,
                              float* dC, float* dD, ts_stream stream);

@@ -2,21 +2,28 @@
 
 ``render(rast, map, poses, tau)`` returns the packed colour, depth and opacity images; its
 backward calls ``ts_render_bwd`` (map gradients) and ``ts_pose_grad`` (dL/dtau for the left
-perturbation Exp(tau) o T_CW, Eq. 5-7).  ``tau`` is a [V, 6] tensor evaluated at zero: the
-returned pose gradient is the manifold gradient at the given poses, which gradient-descent
-tracking then applies with ``ts_pose_apply`` (T <- Exp(-lr * g) o T).
+perturbation Exp(tau) o T_CW, Eq. 5-7).  ``tau`` is a [V, 6] tensor of zeros that the caller
+supplies to ask for the pose gradient: the returned gradient is the manifold gradient at the
+given poses, which gradient-descent tracking then applies with ``ts_pose_apply``
+(T <- Exp(-lr * g) o T).  Its values are not read on the hot path (reading them would
+synchronise the host with the device); with the environment variable TS_DEBUG_CHECKS=1 the
+forward checks that they are zero.
 """
 from __future__ import annotations
+
+import os
 
 import torch
 
 from .rasterizer import Map, Rasterizer
 
+_DEBUG_CHECKS = os.environ.get("TS_DEBUG_CHECKS", "0") == "1"
+
 
 class RenderFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, rast: Rasterizer, faces, poses, pos, col, opa, tau):
-        if tau is not None and bool(torch.any(tau != 0)):
+        if tau is not None and _DEBUG_CHECKS and bool(torch.any(tau != 0)):  # host sync: debug only
             raise ValueError("tau is the pose perturbation at zero; apply steps with ts_pose_apply")
         m = Map(pos.contiguous(), col.contiguous(), opa.contiguous(), faces)
         C, D, A = rast.forward(m, poses)

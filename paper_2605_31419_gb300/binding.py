@@ -305,12 +305,44 @@ def ts_pho_loss(plan, ws, color, depth, tgt_color, tgt_depth, lambda_ssim, lambd
            "ts_pho_loss")
 
 
-def ts_l1_loss_noalloc(cams, color, depth, tgt_color, tgt_depth, lambda_dep, loss, dC, dD, stream=None):
-    """The L1 loss without a plan or workspace (static device scratch); see include/ts_api.h."""
+def check_noalloc_args(cams, color, depth, tgt_color, tgt_depth, loss, dC, dD):
+    """Host-side checks of ts_l1_loss_noalloc's tensors, before anything is launched.
+
+    The entry point has no plan that fixes the image sizes: the cameras alone set how far its
+    kernels read and write.  So every tensor must be float32, contiguous and on one CUDA device,
+    with 3 * sum(W * H) elements for the colour images, sum(W * H) for the depth images and
+    n_views for the loss.  Raises ValueError otherwise."""
     arr = cameras(cams)
-    _check(lib().ts_l1_loss_noalloc(arr, len(arr), _ptr(color), _ptr(depth), _ptr(tgt_color), _ptr(tgt_depth),
-                                    float(lambda_dep), _ptr(loss), _ptr(dC), _ptr(dD), _stream(stream)),
-           "ts_l1_loss_noalloc")
+    P = int(sum(int(c.width) * int(c.height) for c in arr))
+    want = {"color": 3 * P, "depth": P, "tgt_color": 3 * P, "tgt_depth": P, "loss": len(arr), "dC": 3 * P, "dD": P}
+    ts = dict(color=color, depth=depth, tgt_color=tgt_color, tgt_depth=tgt_depth, loss=loss, dC=dC, dD=dD)
+    for name, t in ts.items():
+        if t is None:
+            raise ValueError(f"ts_l1_loss_noalloc: {name} is required")
+        if str(t.dtype) != "torch.float32" or not t.is_contiguous():
+            raise ValueError(f"ts_l1_loss_noalloc: {name} must be a contiguous float32 tensor")
+        if t.numel() != want[name]:
+            raise ValueError(f"ts_l1_loss_noalloc: {name} has {t.numel()} elements, the cameras need {want[name]}")
+    dev = None
+    for name, t in ts.items():
+        if t.device.type != "cuda":
+            raise ValueError(f"ts_l1_loss_noalloc: {name} must be on a CUDA device")
+        if dev is not None and t.device != dev:
+            raise ValueError("ts_l1_loss_noalloc: all tensors must be on one device")
+        dev = t.device
+    return arr, dev
+
+
+def ts_l1_loss_noalloc(cams, color, depth, tgt_color, tgt_depth, lambda_dep, loss, dC, dD, stream=None):
+    """The L1 loss without a plan or workspace (static device scratch); see include/ts_api.h.
+    The call runs with the tensors' device current, so that the scratch array and the default
+    stream are that device's."""
+    import torch
+    arr, dev = check_noalloc_args(cams, color, depth, tgt_color, tgt_depth, loss, dC, dD)
+    with torch.cuda.device(dev):
+        _check(lib().ts_l1_loss_noalloc(arr, len(arr), _ptr(color), _ptr(depth), _ptr(tgt_color), _ptr(tgt_depth),
+                                        float(lambda_dep), _ptr(loss), _ptr(dC), _ptr(dD), _stream(stream)),
+               "ts_l1_loss_noalloc")
 
 
 def ts_pose_adam(plan, poses, dtau, state, lr_rho, lr_theta, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

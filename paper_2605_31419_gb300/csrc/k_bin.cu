@@ -521,6 +521,6 @@ cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
                 0, s>>>(so);
   e = ts_smem_limit((const void*)k_tile_sort_large, (int)(LARGE_SMEM_ITEMS * sizeof(unsigned long long)));
   if (e != cudaSuccess) return e;
-  k_tile_sort_large<<<152, LARGE_T, LARGE_SMEM_ITEMS * sizeof(unsigned long long), s>>>(so, w.keys[1]);
+  k_tile_sort_large<<<(unsigned)ts_sm_count(), LARGE_T, LARGE_SMEM_ITEMS * sizeof(unsigned long long), s>>>(so, w.keys[1]);
   return cudaGetLastError();
 }

@@ -20,75 +20,16 @@ __global__ void __launch_bounds__(LOSS_T) k_loss_partial(const TsImageTable tab,
                                                          const float* __restrict__ tD, float lambda_dep,
                                                          float* __restrict__ dC, float* __restrict__ dD,
                                                          float* __restrict__ part, int nblk) {
-  __shared__ float red[LOSS_T / 32][2];
   const int v = blockIdx.y;
-  const long long HW = (long long)tab.W[v] * tab.H[v];
-  const long long pix_off = tab.pix_off[v];
-  const long long base = (long long)blockIdx.x * LOSS_T * LOSS_PER;
-  float lc = 0.f, ld = 0.f;
-  if (base < HW) {
-    const float ic = 1.0f / (3.0f * (float)HW), id = lambda_dep / (float)HW;
-#pragma unroll
-    for (int k = 0; k < LOSS_PER; ++k) {  // a guard, not an exit: all pixels' loads can be in flight
-      const long long i = base + (long long)k * LOSS_T + threadIdx.x;
-      if (i < HW) {
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          const long long o = 3 * pix_off + ch * HW + i;
-          const float r = C[o] - tC[o];
-          lc += fabsf(r);
-          dC[o] = r > 0.f ? ic : (r < 0.f ? -ic : 0.f);
-        }
-        const long long o = pix_off + i;
-        const float t = tD[o];
-        const float r = D[o] - t;
-        const bool valid = t > 0.f;
-        if (valid) ld += fabsf(r);
-        dD[o] = valid ? (r > 0.f ? id : (r < 0.f ? -id : 0.f)) : 0.f;
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    lc += __shfl_xor_sync(0xffffffffu, lc, o);
-    ld += __shfl_xor_sync(0xffffffffu, ld, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5][0] = lc;
-    red[threadIdx.x >> 5][1] = ld;
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    float s = 0.f;
-#pragma unroll
-    for (int w = 0; w < LOSS_T / 32; ++w) s += red[w][threadIdx.x];
-    part[((long long)v * nblk + blockIdx.x) * 2 + threadIdx.x] = s;
-  }
+  ts_l1_loss_block<LOSS_T, LOSS_PER>((long long)tab.W[v] * tab.H[v], tab.pix_off[v],
+                                     (long long)blockIdx.x * LOSS_T * LOSS_PER, C, D, tC, tD, lambda_dep, dC, dD,
+                                     part + ((long long)v * nblk + blockIdx.x) * 2);
 }
 
 __global__ void __launch_bounds__(LOSS_T) k_loss_final(const TsImageTable tab, const float* __restrict__ part,
                                                        int nblk, float lambda_dep, float* __restrict__ loss) {
-  __shared__ float red[LOSS_T][2];
   const int v = blockIdx.x;
-  float a = 0.f, b = 0.f;
-  for (int k = threadIdx.x; k < nblk; k += LOSS_T) {
-    a += part[((long long)v * nblk + k) * 2];
-    b += part[((long long)v * nblk + k) * 2 + 1];
-  }
-  red[threadIdx.x][0] = a;
-  red[threadIdx.x][1] = b;
-  __syncthreads();
-  for (int o = LOSS_T / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red[threadIdx.x][0] += red[threadIdx.x + o][0];
-      red[threadIdx.x][1] += red[threadIdx.x + o][1];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double HW = (double)tab.W[v] * tab.H[v];
-    loss[v] = (float)((double)red[0][0] / (3.0 * HW) + (double)lambda_dep * (double)red[0][1] / HW);
-  }
+  ts_l1_loss_final<LOSS_T>((long long)tab.W[v] * tab.H[v], part + (long long)v * nblk * 2, nblk, lambda_dep, loss + v);
 }
 
 // Normal loss of Eq. 12 per view: sum over pixels with a sensor normal (Nbar != 0) of

@@ -347,9 +347,12 @@ __global__ void __launch_bounds__(256) k_pose_reduce(const float* __restrict__ p
 
 }  // namespace
 
+// The gather's block count fixes the partial-sum layout of the pose gradient and so its summation
+// order: a constant cap (not the device's SM count) keeps dtau's rounding the same on every GPU.
+constexpr long long POSE_BLOCKS_MAX = 2432;
 int ts_pose_blocks(long long M) {
   const long long want = (M + PG_WARPS * PG_F - 1) / (PG_WARPS * PG_F);
-  return (int)std::max<long long>(1, std::min<long long>(want, 152LL * 16));
+  return (int)std::max<long long>(1, std::min<long long>(want, POSE_BLOCKS_MAX));
 }
 
 cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_map_grad* g, cudaStream_t s) {
@@ -376,7 +379,7 @@ cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_m
   a.part = w.pose;
   a.nblocks = (int)p->n_pose_blocks;
   const long long chunks = (a.VM + 31) / 32;
-  const long long grid_a = std::min<long long>((chunks + PA_WARPS - 1) / PA_WARPS, 152LL * 8);
+  const long long grid_a = std::min<long long>((chunks + PA_WARPS - 1) / PA_WARPS, (long long)ts_sm_count() * 8);
   k_pbwd_chain<<<(unsigned)grid_a, PA_T, 0, s>>>(a);
   const size_t smem = (size_t)PG_WARPS * p->V * 8 * sizeof(float);  // <= 32 KiB for 256 views
   k_pbwd_gather<<<(unsigned)p->n_pose_blocks, PG_T, smem, s>>>(a);

@@ -70,6 +70,20 @@ cudaError_t ts_smem_limit(const void* func, int bytes) {
   return e;
 }
 
+int ts_sm_count() {
+  static std::mutex mu;
+  static std::vector<std::pair<int, int>> seen;  // (device, SMs)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& x : seen)
+    if (x.first == dev) return x.second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+  seen.emplace_back(dev, sms);
+  return sms;
+}
+
 extern "C" {
 
 void ts_default_params(ts_raster_params* o) {
@@ -325,7 +339,7 @@ ts_status ts_l1_loss(const ts_plan* plan, void* ws, const float* color, const fl
                      const float* tgt_depth, float lambda_dep, float* loss, float* dC, float* dD, ts_stream stream) {
   const TsPlanImpl* p = impl(plan);
   if (!p || !ws || !color || !depth || !tgt_color || !tgt_depth || !loss || !dC || !dD) return TS_ERR_INVALID_ARG;
-  if (!(lambda_dep >= 0.0f)) return TS_ERR_INVALID_ARG;
+  if (!(lambda_dep >= 0.0f) || !std::isfinite(lambda_dep)) return TS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   StageTimer t(p, TS_STAGE_LOSS, s);
   return cuda_status(ts_launch_l1_loss(p, ts_ws(p, ws), color, depth, tgt_color, tgt_depth, lambda_dep, loss, dC, dD, s));

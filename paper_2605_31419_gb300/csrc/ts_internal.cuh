@@ -214,6 +214,8 @@ cudaError_t ts_launch_pose_adam(const TsPlanImpl* p, ts_pose* poses, const float
                                 float lr_theta, float b1, float b2, float eps, cudaStream_t s);
 cudaError_t ts_launch_timeout_probe(const TsWs& w, unsigned long long limit_ns, cudaStream_t s);
 int ts_pose_blocks(long long M);                 // blocks of the projection-backward kernel
+// Streaming multiprocessors of the current device (queried once per device; 1 if the query fails).
+int ts_sm_count();
 
 // ------------------------------------------------------------------------------------------
 // Device helpers
@@ -337,6 +339,81 @@ __device__ __forceinline__ bool ts_mbar_wait(uint64_t* bar, uint32_t parity, uin
     if (it == 0) t0 = ts_globaltimer();
     else if ((it & 63) == 0 && ts_globaltimer() - t0 > limit_ns) return false;
   }
+}
+
+// Mean-L1 colour + depth loss (Eq. 8 L1 part, Eq. 9), one block of NT * PER pixels of one view
+// (W x H pixels at pix_off in the packed images): writes dC = sign(C - Cbar) / (3HW) and
+// dD = lambda_dep sign(D - Dbar) / (HW) where Dbar > 0 (else 0), and the block's colour and depth
+// L1 sums, reduced in a fixed order, to part[0..1].  Every thread of the block must call it.
+template <int NT, int PER>
+__device__ __forceinline__ void ts_l1_loss_block(long long HW, long long pix_off, long long base, const float* C,
+                                                 const float* D, const float* tC, const float* tD, float lambda_dep,
+                                                 float* dC, float* dD, float* part) {
+  __shared__ float red[NT / 32][2];
+  float lc = 0.f, ld = 0.f;
+  if (base < HW) {
+    const float ic = 1.0f / (3.0f * (float)HW), id = lambda_dep / (float)HW;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {  // a guard, not an exit: all pixels' loads can be in flight
+      const long long i = base + (long long)k * NT + threadIdx.x;
+      if (i < HW) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          const long long o = 3 * pix_off + ch * HW + i;
+          const float r = C[o] - tC[o];
+          lc += fabsf(r);
+          dC[o] = r > 0.f ? ic : (r < 0.f ? -ic : 0.f);
+        }
+        const long long o = pix_off + i;
+        const float t = tD[o];
+        const float r = D[o] - t;
+        const bool valid = t > 0.f;
+        if (valid) ld += fabsf(r);
+        dD[o] = valid ? (r > 0.f ? id : (r < 0.f ? -id : 0.f)) : 0.f;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lc += __shfl_xor_sync(0xffffffffu, lc, o);
+    ld += __shfl_xor_sync(0xffffffffu, ld, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = lc;
+    red[threadIdx.x >> 5][1] = ld;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    float sum = 0.f;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) sum += red[w][threadIdx.x];
+    part[threadIdx.x] = sum;
+  }
+}
+
+// The view's loss from its nblk block partials part[2k], part[2k + 1], summed in a fixed order:
+// colour sum / (3HW) + lambda_dep * depth sum / (HW).  Every thread of the block must call it.
+template <int NT>
+__device__ __forceinline__ void ts_l1_loss_final(long long HW, const float* part, int nblk, float lambda_dep,
+                                                 float* loss) {
+  __shared__ float red[NT][2];
+  float a = 0.f, b = 0.f;
+  for (int k = threadIdx.x; k < nblk; k += NT) {
+    a += part[2 * (long long)k];
+    b += part[2 * (long long)k + 1];
+  }
+  red[threadIdx.x][0] = a;
+  red[threadIdx.x][1] = b;
+  __syncthreads();
+  for (int o = NT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[threadIdx.x][0] += red[threadIdx.x + o][0];
+      red[threadIdx.x][1] += red[threadIdx.x + o][1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    *loss = (float)((double)red[0][0] / (3.0 * (double)HW) + (double)lambda_dep * (double)red[0][1] / (double)HW);
 }
 
 #endif  // __CUDACC__

@@ -124,3 +124,29 @@ def test_device_calls_reject_null_arguments(ts):
     # misaligned workspace
     assert L.ts_bin(C.byref(plan), C.c_void_p(8), None) == 1
     assert ts.ts_status_string(3) == "pair capacity exceeded"
+
+
+def test_noalloc_binding_checks_tensors_before_any_launch(ts):
+    """ts_l1_loss_noalloc has no plan: the cameras alone fix how far its kernels reach, so the
+    binding checks every tensor's size, type, layout and device on the host (CPU tensors here)."""
+    import torch
+    cams = np.array([[40.0, 40.0, 28.5, 16.5, 57, 33], [10.0, 10.0, 4.0, 3.0, 8, 6]])
+    P = 57 * 33 + 8 * 6
+    ok = dict(color=torch.zeros(3 * P), depth=torch.zeros(P), tgt_color=torch.zeros(3 * P), tgt_depth=torch.zeros(P),
+              loss=torch.zeros(2), dC=torch.zeros(3 * P), dD=torch.zeros(P))
+    for name in ok:
+        bad = dict(ok)
+        bad[name] = torch.zeros(ok[name].numel() - 1)  # one element short
+        with pytest.raises(ValueError, match=name):
+            ts.ts_l1_loss_noalloc(cams, bad["color"], bad["depth"], bad["tgt_color"], bad["tgt_depth"], 0.05,
+                                  bad["loss"], bad["dC"], bad["dD"])
+    bad = dict(ok)
+    bad["dD"] = torch.zeros(P, dtype=torch.float64)
+    with pytest.raises(ValueError, match="float32"):
+        ts.binding.check_noalloc_args(cams, **bad)
+    bad = dict(ok)
+    bad["color"] = torch.zeros(2 * 3 * P)[::2]
+    with pytest.raises(ValueError, match="contiguous"):
+        ts.binding.check_noalloc_args(cams, **bad)
+    with pytest.raises(ValueError, match="CUDA"):  # right sizes, but host memory
+        ts.binding.check_noalloc_args(cams, **ok)

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from harness import assert_grad, assert_images, assert_pose_grad, gpu_run, oracle_run, pack_targets, params_pair
-from ts_synth.scenes import random_triangles_scene, room_map, trajectory_poses, noise_targets, Scene
+from ts_synth.scenes import random_triangles_scene, room_map, room_scene, trajectory_poses, noise_targets, Scene
 
 pytestmark = pytest.mark.gpu
 
@@ -159,3 +159,77 @@ def test_step_edge_cases(oracle, case):
         assert_grad(s["dpos"], r["dpos"], "dpos")
         assert_grad(s["dcol"], r["dcol"], "dcol")
         assert_grad(s["dopa"], r["dopa"], "dopa")
+
+
+# ------------------------------------------------------------ the benchmarked launch at full size
+def test_step_full_size_room(oracle):
+    """ts_render_step_l1 in the launch the benchmark times: 1200x680, 300k faces, 20 views, tile
+    16x8, 64 faces per stage.
+
+    (1) With the benchmark's noise targets: colour, depth, alpha and the loss gradients of all 20
+    views bit for bit against ts_render_fwd + ts_l1_loss (the same per-pixel arithmetic), the loss
+    to float rounding and the map gradients within the gradient tolerance (atomic order).
+    (2) Against the oracle: views 0 and 13 get targets at +-0.01 from the oracle's own render
+    (random sign per element), so the sign of every L1 residual is the same on both sides; the
+    other 18 views get the separate calls' render as their target, so every residual there is
+    exactly 0 and, with sign(0) = 0, they add nothing to the map gradients.  The fused step's map
+    gradients, the sampled views' pose gradients and loss then match the oracle on those 2 views."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    from oracle.oracle import SceneArrays
+    sc = room_scene(3, 300_000, 20, 1200, 680, 600.0, target_seed=4)
+    p, po = params_pair(tile_w=16, tile_h=8, tris_per_stage=64)
+    off = np.concatenate([[0], np.cumsum(sc.cams[:, 4] * sc.cams[:, 5])]).astype(int)
+    # (1) the benchmark's own targets
+    s = step_run(sc, p)
+    g = gpu_run(sc, p)
+    assert s["counters"]["status"] == "TS_OK" and g["counters"]["status"] == "TS_OK"
+    for k in ("color", "depth", "alpha", "dC", "dD"):
+        assert np.array_equal(s[k], g[k]), f"{k} differs from the separate calls"
+    assert_images(s["loss_v"], g["loss_v"], "loss vs separate", atol=1e-7, rtol=1e-6)
+    assert s["counters"]["fwd_contrib"] == s["counters"]["bwd_contrib"] == g["counters"]["bwd_contrib"] > 0
+    for k in ("dpos", "dcol", "dopa"):
+        assert_grad(s[k], g[k], f"{k} vs separate")
+    assert np.allclose(s["dtau"], g["dtau"], rtol=1e-3, atol=1e-3 * np.abs(g["dtau"]).max())
+    # (2) targets that pin every residual's sign
+    views = (0, 13)
+    sub = sc.subset_views(list(views))
+    sa = SceneArrays.of(sub)
+    f = oracle.forward(sa, po)
+    rng = np.random.default_rng(31)
+    tc_o = f["color"] + 0.01 * np.where(rng.random(f["color"].size) < 0.5, -1.0, 1.0)
+    td_o = f["depth"] + 0.01 * np.where(rng.random(f["depth"].size) < 0.5, -1.0, 1.0)
+    tc_o, td_o = tc_o.astype(np.float32).astype(np.float64), td_o.astype(np.float32).astype(np.float64)
+    lo = oracle.l1_loss(sa, f["color"], f["depth"], tc_o, td_o, 0.05)
+    r = oracle.backward(sa, po, lo["dC"], lo["dD"])
+    so = np.concatenate([[0], np.cumsum(sub.cams[:, 4] * sub.cams[:, 5])]).astype(int)
+    tc, td = g["color"].copy(), g["depth"].copy()
+    for i, v in enumerate(views):
+        tc[3 * off[v]:3 * off[v + 1]] = tc_o[3 * so[i]:3 * so[i + 1]]
+        td[off[v]:off[v + 1]] = td_o[so[i]:so[i + 1]]
+        HW = int(off[v + 1] - off[v])
+        sc.tgt_color[v] = tc[3 * off[v]:3 * off[v + 1]].astype(np.float32).reshape(3, -1, sc.cams[v, 4].astype(int))
+        sc.tgt_depth[v] = td[off[v]:off[v + 1]].astype(np.float32).reshape(-1, sc.cams[v, 4].astype(int))
+        assert sc.tgt_depth[v].size == HW
+    for v in range(sc.n_views):
+        if v not in views:
+            W_ = int(sc.cams[v, 4])
+            sc.tgt_color[v] = g["color"][3 * off[v]:3 * off[v + 1]].astype(np.float32).reshape(3, -1, W_)
+            sc.tgt_depth[v] = g["depth"][off[v]:off[v + 1]].astype(np.float32).reshape(-1, W_)
+    del g
+    torch.cuda.empty_cache()
+    s = step_run(sc, p)
+    for v in range(sc.n_views):
+        if v not in views:
+            assert not s["dC"][3 * off[v]:3 * off[v + 1]].any() and not s["dD"][off[v]:off[v + 1]].any(), v
+            assert s["loss_v"][v] == 0.0, v
+    for i, v in enumerate(views):
+        # the same residual signs; magnitudes 1/(3HW) and lambda_dep/HW, formed in FP32 on the GPU
+        assert_images(s["dC"][3 * off[v]:3 * off[v + 1]], lo["dC"][3 * so[i]:3 * so[i + 1]], f"dC[{v}]", 0.0, 1e-6)
+        assert_images(s["dD"][off[v]:off[v + 1]], lo["dD"][so[i]:so[i + 1]], f"dD[{v}]", 0.0, 1e-6)
+        assert_images(s["color"][3 * off[v]:3 * off[v + 1]], f["color"][3 * so[i]:3 * so[i + 1]], f"color[{v}]")
+        assert_pose_grad(s["dtau"][v], r["dtau"][i], r["dtau_abs"][i])
+    assert_images(s["loss_v"][list(views)], lo["loss_v"], "loss", atol=1e-6, rtol=1e-5)
+    assert_grad(s["dpos"], r["dpos"], "dpos")
+    assert_grad(s["dcol"], r["dcol"], "dcol")
+    assert_grad(s["dopa"], r["dopa"], "dopa")

@@ -46,11 +46,66 @@ def test_noalloc_loss_matches_workspace_loss_twice():
         assert torch.equal(dC, ref_dC) and torch.equal(dD, ref_dD)
 
 
+def _limit_cams(n_views):
+    """One 1024 x 1024 view (512 blocks of 2048 pixels) and n_views - 1 views of one pixel: the
+    scratch holds n_views * 512 slots, 65536 for 128 views."""
+    cams = np.tile([[1.0, 1.0, 0.5, 0.5, 1, 1]], (n_views, 1))
+    cams[0] = [500.0, 500.0, 512.0, 512.0, 1024, 1024]
+    return cams
+
+
+def _tensors(cams, seed):
+    import torch
+    rng = np.random.default_rng(seed)
+    C, D, tC, tD = (torch.as_tensor(a, device="cuda") for a in _inputs(rng, cams))
+    P = D.numel()
+    return C, D, tC, tD, torch.empty(len(cams), device="cuda"), torch.empty(3 * P, device="cuda"), \
+        torch.empty(P, device="cuda")
+
+
+def test_noalloc_at_the_limit_matches_and_allocates_nothing():
+    """128 views of which one is 1024 x 1024: exactly the 65536 slots of the scratch.  The result
+    equals ts_l1_loss, and a second call leaves the device's free memory unchanged."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    cams = _limit_cams(128)
+    rast = ts.Rasterizer(cams, 1)
+    C, D, tC, tD, loss, dC, dD = _tensors(cams, 5)
+    ref_loss, ref_dC, ref_dD = torch.empty_like(loss), torch.empty_like(dC), torch.empty_like(dD)
+    ts.ts_l1_loss(rast.plan, rast.ws, C, D, tC, tD, 0.05, ref_loss, ref_dC, ref_dD)
+    ts.ts_l1_loss_noalloc(cams, C, D, tC, tD, 0.05, loss, dC, dD)  # warm-up: the scratch lookup
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    loss.fill_(-1.0)
+    ts.ts_l1_loss_noalloc(cams, C, D, tC, tD, 0.05, loss, dC, dD)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    l, rl = loss.cpu().numpy().astype(np.float64), ref_loss.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(l - rl) <= 1e-7 + 1e-5 * np.abs(rl)), (l, rl)
+    assert torch.equal(dC, ref_dC) and torch.equal(dD, ref_dD)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
     import paper_2605_31419_gb300 as ts
-    big = np.tile([[600.0, 600.0, 600.0, 340.0, 16384, 16384]], (1, 1))  # 131072 blocks > 65536 slots
+    # one huge view: 131072 blocks > 65536 slots (the C entry point rejects it; the tensors are
+    # placeholders of one element, so the binding's own size check is bypassed by calling libts)
+    big = ts.binding.cameras(np.array([[600.0, 600.0, 600.0, 340.0, 16384, 16384]]))
     t = torch.empty(1, device="cuda")
+    p = t.data_ptr()
+    st = ts.binding.lib().ts_l1_loss_noalloc(big, 1, p, p, p, p, 0.05, p, p, p, None)
+    assert st == 1
+    # 129 views of the limit's shape: 66048 slots, one view more than the scratch holds
+    cams = _limit_cams(129)
+    C, D, tC, tD, loss, dC, dD = _tensors(cams, 6)
+    loss.fill_(-1.0)
     with pytest.raises(ts.TsError) as e:
-        ts.ts_l1_loss_noalloc(big, t, t, t, t, 0.05, t, t, t)
+        ts.ts_l1_loss_noalloc(cams, C, D, tC, tD, 0.05, loss, dC, dD)
     assert e.value.status == 1
+    torch.cuda.synchronize()
+    assert torch.all(loss == -1.0)  # nothing was launched
+    # a non-finite depth weight
+    cams = _limit_cams(2)
+    C, D, tC, tD, loss, dC, dD = _tensors(cams, 7)
+    with pytest.raises(ts.TsError):
+        ts.ts_l1_loss_noalloc(cams, C, D, tC, tD, float("inf"), loss, dC, dD)
