@@ -149,7 +149,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(sc, time_budget_s=20.0):
+def cpu_baseline(sc, time_budget_s=20.0, single_thread=True):
     """The oracle (as it stands) on one view of the workload, all host cores: fwd + L1 + bwd."""
     from oracle.oracle import Oracle, Params, SceneArrays, pack_targets
     o = Oracle()
@@ -170,9 +170,98 @@ def cpu_baseline(sc, time_budget_s=20.0):
         if time.perf_counter() > t_end or len(times) >= 3 or times[-1] > 0.5 * time_budget_s:
             break
     t = float(np.median(times))
-    return {"value": W * H / t / 1e6, "unit": "Mpix/s", "cores": nthreads, "kind": "oracle",
-            "sample": f"1 of {sc.n_views} views (1200x680, {sc.n_faces} faces): fwd + L1 loss + bwd, "
-                      f"median of {len(times)} runs, {t:.2f} s each"}
+    out = {"value": W * H / t / 1e6, "unit": "Mpix/s", "cores": nthreads, "kind": "oracle",
+           "sample": f"1 of {sc.n_views} views (1200x680, {sc.n_faces} faces): fwd + L1 loss + bwd, "
+                     f"median of {len(times)} runs, {t:.2f} s each"}
+    if single_thread:
+        prm.n_threads = 1
+        t0 = time.perf_counter()
+        f = o.forward(sa, prm)
+        lo = o.l1_loss(sa, f["color"], f["depth"], tc, td, 0.05)
+        o.backward(sa, prm, lo["dC"], lo["dD"])
+        t1 = time.perf_counter() - t0
+        out["single_thread"] = {"value": W * H / t1 / 1e6, "unit": "Mpix/s", "cores": 1, "seconds": t1}
+    return out
+
+
+def bench_c1(ts, torch, dev, flush, stream, reps=50):
+    """The plain single view: 160x120 (f = 150), 2,000 random triangles at the identity pose, one
+    forward (colour, depth, opacity) and one backward of the L1 colour + depth loss against a
+    seeded target.  Device time per step through the separate calls and through the fused step,
+    each eager and replayed from a captured CUDA graph; and the oracle on the same view."""
+    from oracle.oracle import Oracle, Params, SceneArrays, pack_targets
+    from ts_synth import random_triangles_scene
+    sc = random_triangles_scene(seed=1)
+    r = ts.Rasterizer(sc.cams, sc.n_faces)
+    m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa, device=dev)
+    poses = ts.poses_tensor(sc.poses, device=dev)
+    tcn, tdn = pack_targets(sc)
+    tc = torch.as_tensor(tcn, dtype=torch.float32, device=dev)
+    td = torch.as_tensor(tdn, dtype=torch.float32, device=dev)
+    g = m.zeros_like()
+
+    def sep():
+        g.pos.zero_(); g.col.zero_(); g.opa.zero_()
+        r.forward(m, poses)
+        r.l1_loss(tc, td, 0.05)
+        r.backward(r.dC, r.dD, None, g)
+        r.pose_grad()
+
+    def fused():
+        g.pos.zero_(); g.col.zero_(); g.opa.zero_()
+        r.project(m, poses)
+        r.bin()
+        r.step_l1(tc, td, 0.05, g)
+        r.pose_grad()
+
+    def timed(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    out = {"workload": "160x120 f=150, 2,000 random faces (sides 2-10 cm, depth 0.5-4 m), identity pose, "
+                       "fwd + L1 loss + bwd, one view", "pixels": 19200, "faces": sc.n_faces}
+    res = {}
+    for name, fn in (("separate", sep), ("fused", fused)):
+        res[name + "_eager_ms"] = timed(fn)
+        gr = torch.cuda.CUDAGraph()
+        s2 = torch.cuda.Stream(device=dev)
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s2):
+            fn()
+            with torch.cuda.graph(gr, stream=s2):
+                fn()
+        stream.wait_stream(s2)
+        res[name + "_graph_ms"] = timed(gr.replay)
+    best = min(res.values())
+    cnt = r.counters()
+    out.update({"ms": res, "mpix_s": 19200 / best / 1e3, "triangles_per_s": sc.n_faces / (best / 1e3),
+                "visible_faces": int(cnt["n_visible"]), "best": min(res, key=res.get)})
+    # the oracle on the same view, all host cores and one
+    o = Oracle()
+    sa = SceneArrays.of(sc)
+    for label, nth in (("oracle_all_cores", os.cpu_count() or 1), ("oracle_1_thread", 1)):
+        prm = Params(n_threads=nth)
+        ts_ = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            f = o.forward(sa, prm)
+            lo = o.l1_loss(sa, f["color"], f["depth"], tcn, tdn, 0.05)
+            o.backward(sa, prm, lo["dC"], lo["dD"])
+            ts_.append(time.perf_counter() - t0)
+        t = float(np.median(ts_))
+        out[label] = {"mpix_s": 19200 / t / 1e6, "ms": t * 1e3, "cores": nth}
+    return out
 
 
 def bench_mapping_window(ts, torch, dev, n_faces=1_000_000, steps=5):
@@ -200,6 +289,25 @@ def bench_mapping_window(ts, torch, dev, n_faces=1_000_000, steps=5):
     torch.cuda.empty_cache()
     batched = ts.MultiViewStep(m, cams, poses, tc, td, None, grad)
     ms_batched = ts.batch.time_ms(batched.step, iters=steps)
+    # where the batched step's time goes: libts records events around each stage on the stream
+    names = ts.binding.STAGES
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(names))]
+    st_ = torch.cuda.current_stream()
+    for e in ev:
+        e.record(st_)
+    ts.ts_set_stage_events(batched.rast.plan, ev)
+    stage_ms = np.zeros(len(names))
+    for _ in range(steps):
+        batched.step()
+        torch.cuda.synchronize()
+        stage_ms += [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(len(names))]
+    ts.ts_set_stage_events(batched.rast.plan, None)
+    stage_ms /= steps
+    cnt = batched.rast.counters()
+    out["batched_stages_ms"] = {("fused_fwd_loss_bwd" if n == "fwd" else n): float(t) for n, t in zip(names, stage_ms)
+                                if n not in ("bwd_raster", "loss")}
+    out["batched_counters"] = {k: int(cnt[k]) for k in ("n_visible", "n_pairs", "fwd_contrib")}
+    out["batched_path"] = "ts_render_step_l1" if batched.fused else "separate calls"
     del batched
     torch.cuda.empty_cache()
     best, _ = ts.autotune(m, cams, poses, tc, td, grad, tiles=((16, 8), (8, 8), (16, 16), (32, 8)), stages=(64, 128),
@@ -263,7 +371,7 @@ def bench_tracking(ts, torch, dev, n_hyp=64, iters=100):
             "median_error_after": {"cm": float(np.median(e1[:, 0]) * 100), "deg": float(np.median(e1[:, 1]))}}
 
 
-def bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max, reps=10):
+def bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max, n_sm, reps=10):
     """The fused photometric loss of Eq. 8-10 ((1 - 0.2) L1 + 0.2 D-SSIM on colour, 0.05 L1 on depth)
     with its image gradients, on the bench's rendered views; device time with the L2 flushed."""
     call = (rast.plan, rast.ws, rast.color, rast.depth, tgt_c, tgt_d, 0.2, 0.05, rast.loss_v, rast.dC, rast.dD)
@@ -284,7 +392,7 @@ def bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_pea
             "mpix_s": pixels / (t / 1e3) / 1e6,
             "roofline": {"kernel": "k_pho_tile", "bound": "alu", "achieved": ach, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
-                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                         "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                          "work": f"{3 * pixels} pixel-channels x {FLOPS_PHO:.0f} flops"}}
 
 
@@ -335,10 +443,14 @@ def bench_variants(ts, torch, sc, m, poses, tgt_c, tgt_d, flush, stream, params,
     return out
 
 
-def bench_serving(ts, torch, dev, rates=(200, 500, 1000, 2000), seconds=2.0, n_faces=2_000_000):
+def bench_serving(ts, torch, dev, rates=(200, 500, 1000, 2000), seconds=10.0, n_faces=2_000_000, drain=5.0):
     """Serving: device-resident 2M-face map; Poisson arrivals of render (one forward) and track
-    (10 pose iterations) requests, resolutions uniform over 256x256, 640x480 and 1200x680,
-    poses on a seeded trajectory; continuous batching; p50/p99 latency and Mpix/s per rate."""
+    (10 pose iterations) requests, resolutions uniform over 256x256, 640x480 and 1200x680, poses on
+    a seeded trajectory, 10 s of arrivals per rate.  Each stream is served twice: by the continuous
+    batching server and by the plain one-request-at-a-time loop (the baseline), each run ending 5 s
+    after the last arrival; requests unfinished by then are counted as not served (and as infinitely
+    late in the percentiles).  At 1000 req/s the served run is repeated with the plain L1 tracking
+    loss (lambda_ssim = 0) to show the D-SSIM term's share."""
     from ts_synth.scenes import perturb_pose, request_stream, room_map, trajectory_poses
     res = ((256, 256, 256.0), (640, 480, 525.0), (1200, 680, 600.0))
     pos, col, opa = room_map(6, n_faces)
@@ -352,11 +464,12 @@ def bench_serving(ts, torch, dev, rates=(200, 500, 1000, 2000), seconds=2.0, n_f
             C, D, _ = r.forward(m, ts.poses_tensor(gts[k][None, :], device=dev))
             targets[(W_, H_, k)] = (C.clone().view(3, H_, W_), D.clone().view(H_, W_))
         del r
-    srv = ts.Server(m, max_views=32, max_pixels=16_000_000, track_iters=10)
-    out = {"workload": f"2M-face room, Poisson render/track 50/50, {seconds:.0f} s per rate, resolutions "
-                       "256x256 / 640x480 / 1200x680, track = 10 pose iterations"}
-    rng = np.random.default_rng(6)
-    for rate in rates:
+    out = {"workload": f"2M-face room, Poisson render/track 50/50, {seconds:.0f} s of arrivals per rate, resolutions "
+                       f"256x256 / 640x480 / 1200x680, track = 10 pose iterations (0.8 L1 + 0.2 D-SSIM + 0.05 depth); "
+                       f"runs end {drain:.0f} s after the last arrival"}
+
+    def stream_of(rate, seed):
+        rng = np.random.default_rng(seed)
         reqs = []
         for i, d in enumerate(request_stream(6 + rate, rate, seconds, resolutions=res, n_poses=n_poses)):
             W_, H_, f = d["W"], d["H"], d["f"]
@@ -367,12 +480,107 @@ def bench_serving(ts, torch, dev, rates=(200, 500, 1000, 2000), seconds=2.0, n_f
             else:
                 tc, td = targets[(W_, H_, d["pose_index"])]
                 reqs.append(ts.Request(i, "track", cam, perturb_pose(gt, rng, 0.02, 1.0), d["t"], tc, td))
-        srv.stats.update(steps=0, pixels=0, rejected_for_memory=0)
-        srv.run(reqs, realtime=True, max_seconds=seconds * 5)
+        return reqs
+
+    def served(rate, lambda_ssim=0.2):
+        srv = ts.Server(m, max_views=32, max_pixels=16_000_000, track_iters=10, lambda_ssim=lambda_ssim)
+        reqs = stream_of(rate, 6)
+        srv.run(reqs, realtime=True, drain_seconds=drain)
         st = ts.latency_stats(reqs, srv.stats["seconds"])
         st["steps"] = srv.stats["steps"]
+        del srv
+        torch.cuda.empty_cache()
+        return st
+
+    for rate in rates:
+        st = {"served": served(rate)}
+        reqs = stream_of(rate, 6)
+        secs = ts.serve_plain(m, reqs, track_iters=10, realtime=True, drain_seconds=drain)
+        st["plain"] = ts.latency_stats(reqs, secs)
+        torch.cuda.empty_cache()
+        st["served_over_plain_mpix"] = st["served"]["mpix_s"] / max(st["plain"]["mpix_s"], 1e-9)
         out[f"{rate}_req_s"] = st
+    out["1000_req_s_served_l1_only"] = served(1000, lambda_ssim=0.0)
     return out
+
+
+def bench_e2e(ts, torch, dev, rast, m, poses, tgt_c, tgt_d, grad, flush, stream, pixels, args):
+    """The step end to end through the public API, as a training loop with a double-buffered input
+    pipeline runs it: every step copies its inputs (map, poses, targets) from pinned host memory
+    and reads its results (map gradients, pose gradients, per-view loss) back into pinned host
+    memory.  Step k+1's inputs cross on a copy stream while step k computes, and step k's results
+    cross on another while step k+1 computes; each buffer is reused only after the step that read
+    it has finished.  The timed region spans all K steps: the first step's input copy and the last
+    step's result copy are inside it, and the L2 flush before every step is part of each step."""
+    h_in = [t.cpu().pin_memory() for t in (m.pos, m.col, m.opa, poses, tgt_c, tgt_d)]
+    h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (grad.pos, grad.col, grad.opa)]
+    h_out += [torch.empty(rast.V, 6).pin_memory(), torch.empty(rast.V).pin_memory()]
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = sum(t.numel() * t.element_size() for t in h_out)
+    d_in = [[torch.empty_like(t, device=dev) for t in h_in] for _ in range(2)]
+    d_grad = [m.zeros_like() for _ in range(2)]
+    d_tau = [torch.empty(rast.V, 6, device=dev) for _ in range(2)]
+    d_loss = [torch.empty(rast.V, device=dev) for _ in range(2)]
+    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    K = max(10, args.steps)
+
+    def run(separate):
+        comp_done = [None, None]
+        out_read = [None, None]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        up.wait_stream(stream)
+        for k in range(K):
+            b = k % 2
+            if comp_done[b] is not None:
+                up.wait_event(comp_done[b])  # step k-2 has finished reading buffer b
+            with torch.cuda.stream(up):
+                for d, h in zip(d_in[b], h_in):
+                    d.copy_(h, non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(up)
+            stream.wait_event(ready)
+            if out_read[b] is not None:
+                stream.wait_event(out_read[b])  # step k-2's results have left buffer b
+            pos, col, opa, ps, tc, td = d_in[b]
+            dm, g = ts.Map(pos, col, opa), d_grad[b]
+            flush.fill_(1.0)
+            g.pos.zero_(); g.col.zero_(); g.opa.zero_()
+            if separate:
+                rast.forward(dm, ps)
+                rast.l1_loss(tc, td, 0.05)
+                rast.backward(rast.dC, rast.dD, None, g)
+            else:
+                rast.project(dm, ps)
+                rast.bin()
+                rast.step_l1(tc, td, 0.05, g)
+            rast.pose_grad(out=d_tau[b])
+            d_loss[b].copy_(rast.loss_v)
+            comp_done[b] = torch.cuda.Event()
+            comp_done[b].record(stream)
+            down.wait_event(comp_done[b])
+            with torch.cuda.stream(down):
+                for h, d in zip(h_out, (g.pos, g.col, g.opa, d_tau[b], d_loss[b])):
+                    h.copy_(d, non_blocking=True)
+            out_read[b] = torch.cuda.Event()
+            out_read[b].record(down)
+        stream.wait_stream(down)
+        stream.wait_stream(up)
+        t1.record(stream)
+        t1.synchronize()
+        return t0.elapsed_time(t1) / K
+
+    vals = {}
+    for separate in ((True,) if args.separate else (False, True)):
+        run(separate)  # warm-up of the pipeline
+        vals["ts_render_fwd + ts_l1_loss + ts_render_bwd" if separate else "ts_render_step_l1"] = \
+            pixels / (run(separate) / 1e3) / 1e6
+    best = max(vals, key=vals.get)
+    return {"value": vals[best], "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "path": best, "by_path": vals, "steps": K,
+            "pipeline": "inputs of step k+1 cross while step k computes; results of step k cross while step k+1 "
+                        "computes; first input copy and last result copy inside the timed region"}
 
 
 def run_reference(args):
@@ -383,7 +591,7 @@ def run_reference(args):
     steps = []
     base = None
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(sc, time_budget_s=0.0)
+        r = cpu_baseline(sc, time_budget_s=0.0, single_thread=False)
         if i >= args.warmup:
             steps.append(W * H / r["value"] / 1e6)
         base = r
@@ -495,78 +703,15 @@ def main():
     # -- end to end: pinned host inputs in, results out, through the same API ---------------------
     e2e = None
     if rank == 0:
-        h_pos, h_col, h_opa = m.pos.cpu().pin_memory(), m.col.cpu().pin_memory(), m.opa.cpu().pin_memory()
-        h_poses = poses.cpu().pin_memory()
-        h_tc, h_td = tgt_c.cpu().pin_memory(), tgt_d.cpu().pin_memory()
-        out_pos, out_col, out_opa = (torch.empty_like(h_pos).pin_memory(), torch.empty_like(h_col).pin_memory(),
-                                     torch.empty_like(h_opa).pin_memory())
-        out_tau, out_loss = torch.empty(sc.n_views, 6).pin_memory(), torch.empty(sc.n_views).pin_memory()
-        h2d = sum(t.numel() * t.element_size() for t in (h_pos, h_col, h_opa, h_poses, h_tc, h_td))
-        d2h = sum(t.numel() * t.element_size() for t in (out_pos, out_col, out_opa, out_tau, out_loss))
-        d_pos, d_col, d_opa = torch.empty_like(m.pos), torch.empty_like(m.col), torch.empty_like(m.opa)
-        d_poses, d_tc, d_td = torch.empty_like(poses), torch.empty_like(tgt_c), torch.empty_like(tgt_d)
-        dm = ts.Map(d_pos, d_col, d_opa)
-
-        copy_stream = torch.cuda.Stream(device=dev)
-
-        def e2e_step(separate):
-            # the map and poses feed the projection; the targets are first read by the loss (or the
-            # fused step), so they cross on a second stream while the projection and the sort (and
-            # with the separate calls the forward) run.  Host-to-device copies share a copy engine
-            # in issue order: the map goes first.
-            for d, hsrc in ((d_pos, h_pos), (d_col, h_col), (d_opa, h_opa), (d_poses, h_poses)):
-                d.copy_(hsrc, non_blocking=True)
-            copy_stream.wait_stream(stream)  # the previous step has finished reading the targets
-            with torch.cuda.stream(copy_stream):
-                d_tc.copy_(h_tc, non_blocking=True)
-                d_td.copy_(h_td, non_blocking=True)
-            targets_in = torch.cuda.Event()
-            targets_in.record(copy_stream)
-            grad.pos.zero_(); grad.col.zero_(); grad.opa.zero_()
-            if separate:
-                rast.forward(dm, d_poses)
-                stream.wait_event(targets_in)
-                rast.l1_loss(d_tc, d_td, 0.05)
-                rast.backward(rast.dC, rast.dD, None, grad)
-            else:
-                rast.project(dm, d_poses)
-                rast.bin()
-                stream.wait_event(targets_in)
-                rast.step_l1(d_tc, d_td, 0.05, grad)
-            rast.pose_grad()
-            out_pos.copy_(grad.pos, non_blocking=True)
-            out_col.copy_(grad.col, non_blocking=True)
-            out_opa.copy_(grad.opa, non_blocking=True)
-            out_tau.copy_(rast.dtau, non_blocking=True)
-            out_loss.copy_(rast.loss_v, non_blocking=True)
-
-        # both public paths; from host memory the separate calls can hide the targets' copy behind
-        # the forward, which the fused step cannot, so the faster one is the end-to-end figure
-        e2e_vals = {}
-        for separate in ((True,) if args.separate else (False, True)):
-            e2e_step(separate)
-            torch.cuda.synchronize()
-            e_ms = []
-            for _ in range(max(3, args.steps // 2)):
-                flush.fill_(1.0)
-                b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                b0.record(stream)
-                e2e_step(separate)
-                b1.record(stream)
-                b1.synchronize()
-                e_ms.append(b0.elapsed_time(b1))
-            e2e_vals["ts_render_fwd + ts_l1_loss + ts_render_bwd" if separate else "ts_render_step_l1"] = \
-                pixels / (float(np.mean(e_ms)) / 1e3) / 1e6
-        best = max(e2e_vals, key=e2e_vals.get)
-        e2e = {"value": e2e_vals[best], "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "path": best, "by_path": e2e_vals}
+        e2e = bench_e2e(ts, torch, dev, rast, m, poses, tgt_c, tgt_d, grad, flush, stream, pixels, args)
 
     if rank == 0:
         peaks, peak_src = measured_peaks()
         names = ts.binding.STAGES
         dom = int(np.argmax(stage_ms))
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
         if names[dom] in ("bwd_raster", "fwd"):
             fused = names[dom] == "fwd" and not args.separate  # the fwd stage times ts_render_step_l1
             per = (FLOPS_FWD + FLOPS_BWD) if fused else (FLOPS_BWD if names[dom] == "bwd_raster" else FLOPS_FWD)
@@ -575,12 +720,18 @@ def main():
             ach = flops / (stage_ms[dom] / 1e3) / 1e12
             kernel = "k_render_step" if fused else f"k_render_{'bwd' if names[dom] == 'bwd_raster' else 'fwd'}"
             per_view = {"k_render_step": STEP_TRAFFIC_PER_VIEW, "k_render_bwd": BWD_TRAFFIC_PER_VIEW}.get(kernel)
+            traffic = (per_view * sc.n_views if per_view is not None and args.tile == "16x8"
+                       and args.stage == 64 else None)
             roof = {"kernel": kernel, "bound": "alu",
                     "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
-                    "traffic": (per_view * sc.n_views if per_view is not None and args.tile == "16x8"
-                                and args.stage == 64 else None),
-                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                    "traffic": traffic,
+                    "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                     "work": f"{contrib} (pixel, face) contributions x {per:.0f} flops"}
+            if traffic is not None:
+                # the same launch against the memory roofline: its measured DRAM bytes over its time
+                gbs = traffic / (stage_ms[dom] / 1e3) / 1e9
+                roof.update({"hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+                             "hbm_frac": gbs / peaks["hbm_gbs"], "hbm_peak_source": peak_src})
         else:
             roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": None}
@@ -604,7 +755,15 @@ def main():
             "roofline": roof, "peaks": peak_src, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clocks,
         }
-        line["pho_loss"] = bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max)
+        line["triangles_per_s"] = {
+            "face_views": sc.n_faces * sc.n_views / t_step,
+            "visible_records": cnt["n_visible"] / t_step,
+            "tile_pairs": cnt["n_pairs"] / t_step,
+            "note": "face_views: input faces x views per second of step time; visible_records: (view, face) "
+                    "records that survived culling per second; tile_pairs: (tile, face) pairs per second"}
+        line["pho_loss"] = bench_pho_loss(ts, torch, rast, tgt_c, tgt_d, flush, stream, pixels, alu_peak, sm_max,
+                                          n_sm)
+        line["c1_plain_single_view"] = bench_c1(ts, torch, dev, flush, stream)
         if not args.no_extras:
             del rast
             torch.cuda.empty_cache()

@@ -103,6 +103,13 @@ typedef struct {
  * (ts_map_grad.gsigma); the global sigma is then unused. */
 #define TS_FLAG_FACE_SIGMA 16
 
+/* ts_raster_params.flags: a forward-only plan, for callers that render without differentiating
+ * (the render requests of a serving loop).  Its workspace holds no gradient slots and no per-pair
+ * lane masks, the projection clears no gradient slots and the forward records no lane masks.
+ * ts_render_bwd, ts_render_bwd_n, ts_render_step_l1 and ts_pose_grad on such a plan return
+ * TS_ERR_INVALID_ARG. */
+#define TS_FLAG_FORWARD_ONLY 32
+
 /* The map (Sec. 3.1): N vertices with position, colour, opacity as structure-of-arrays float32
  * device buffers, and M faces.  faces = NULL selects triangle-soup mode (face m uses vertices
  * 3m, 3m+1, 3m+2; N = 3M); otherwise faces is device int32 [M][3].  The buffers must stay valid

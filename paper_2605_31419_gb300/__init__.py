@@ -10,7 +10,7 @@ from .binding import (  # noqa: F401
     ts_render_fwd, ts_render_bwd, ts_render_fwd_n, ts_render_bwd_n, ts_render_step_l1, ts_pose_grad,
     ts_l1_loss, ts_l1_loss_noalloc, ts_pho_loss, ts_normal_loss, ts_equilateral, ts_pose_apply, ts_pose_adam,
     ts_sync_status, ts_face_stats, ts_covisibility, TS_FLAG_PERSISTENT, TS_FLAG_NORMALS, TS_FLAG_STATS,
-    TS_FLAG_MIN_OPACITY, TS_FLAG_FACE_SIGMA,
+    TS_FLAG_MIN_OPACITY, TS_FLAG_FACE_SIGMA, TS_FLAG_FORWARD_ONLY,
     ts_plan_layout,
     ts_debug_copy, ts_debug_timeout_probe, ts_set_stage_events, ts_status_string,
 )
@@ -21,4 +21,4 @@ from .rasterizer import Map, Rasterizer, poses_tensor  # noqa: E402,F401
 from .autograd import RenderFunction, render  # noqa: E402,F401
 from .tracking import Tracker, pose_error  # noqa: E402,F401
 from .batch import MultiViewStep, autotune, params_of  # noqa: E402,F401
-from .serve import Request, Server, latency_stats  # noqa: E402,F401
+from .serve import Request, Server, latency_stats, serve_plain  # noqa: E402,F401

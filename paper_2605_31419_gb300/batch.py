@@ -34,7 +34,8 @@ class MultiViewStep:
         zero where there is none) are given: the plan then renders the normal map
         (TS_FLAG_NORMALS) and its gradient joins the backward;
       * lambda_equi E_equi (Eq. 14) on the map's faces when lambda_equi > 0 (needs ``grad``).
-    Map gradients accumulate into ``grad``; per-view values are in ``losses()``."""
+    Map gradients accumulate into ``grad``; per-view values are in ``losses()``.  With the plain L1
+    loss (no D-SSIM, no normals) the step is the fused ts_render_step_l1 pass."""
 
     def __init__(self, m: Map, cams, poses: torch.Tensor, tgt_color: torch.Tensor, tgt_depth: torch.Tensor,
                  params: Optional[B.TsRasterParams] = None, grad: Optional[Map] = None, lambda_dep: float = 0.05,
@@ -55,10 +56,23 @@ class MultiViewStep:
         self.want_pose = want_pose
         self.graph: Optional[torch.cuda.CUDAGraph] = None
 
+    @property
+    def fused(self) -> bool:
+        """True when the loss is the plain L1 colour + depth term: the step then runs the forward,
+        the loss and the backward in one pass per tile (ts_render_step_l1)."""
+        return self.lambda_ssim == 0 and self.tn is None
+
     def step(self):
         r = self.rast
         r.project(self.map, self.poses)
         r.bin()
+        if self.fused:
+            r.step_l1(self.tc, self.td, self.lambda_dep, self.grad)
+            if self.lambda_equi > 0:
+                r.equilateral(self.map, self.lambda_equi, self.grad, out=self.equi)
+            if self.want_pose:
+                r.pose_grad()
+            return
         r.render_fwd()
         if self.lambda_ssim > 0:
             r.pho_loss(self.tc, self.td, self.lambda_ssim, self.lambda_dep)

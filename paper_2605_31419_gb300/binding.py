@@ -25,6 +25,7 @@ TS_FLAG_NORMALS = 2
 TS_FLAG_STATS = 4
 TS_FLAG_MIN_OPACITY = 8
 TS_FLAG_FACE_SIGMA = 16
+TS_FLAG_FORWARD_ONLY = 32
 DEBUG = dict(keys=0, ids=1, ranges=2, rect=3, zbits=4, count=5, T_final=6, n_last=7, records=8)
 
 

@@ -1,9 +1,15 @@
 // k_project.cu -- Eq. 1-3 per (view, face): projection, culling and the screen-space record.
 //
-// One thread per (view, face), view-major so that a warp reads 32 consecutive faces' vertex
-// data (coalesced structure-of-arrays loads).  The projection, area, perimeter, inradius, face
-// opacity, pixel box and depth key follow one fixed FP32 operation order (no FMA contraction,
-// IEEE division and square root), so culling, tiles and depth keys are reproducible bit for bit.
+// One thread per face and block of views: the thread loads its face's vertex data once (a warp
+// reads 32 consecutive faces: coalesced structure-of-arrays loads) and projects it into each view
+// of its block, writing the (view, face) outputs view-major, so that every store of a warp is to
+// 32 consecutive (view, face) entries.  The view blocks are as large as the face count allows
+// while still filling the GPU, so a map is read from memory once per block of views instead of
+// once per view.  The projection, area, perimeter, inradius, face opacity, pixel box and depth key
+// follow one fixed FP32 operation order (no FMA contraction, IEEE division and square root), so
+// culling, tiles and depth keys are reproducible bit for bit.
+#include <algorithm>
+
 #include "ts_internal.cuh"
 
 namespace {
@@ -57,26 +63,25 @@ struct ProjArgs {
   TsDevHeader* hdr;
 };
 
-__global__ void __launch_bounds__(256) k_project(ProjArgs a) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  bool vis = false;
-  if (idx < a.VM) {
-    const int view = (int)(idx / a.M);
-    const long long m = idx - (long long)view * a.M;
-    const TsView vw = a.views[view];
-    const ts_pose P = a.poses[view];
+__global__ void __launch_bounds__(256, 3) k_project(ProjArgs a, int views_per_block) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v0 = (int)blockIdx.y * views_per_block;
+  const int v1 = min(a.V, v0 + views_per_block);
+  // the face's vertex data, loaded once for the block of views (all loads up front, so that their
+  // latencies overlap)
+  float o[3], wp[3][3], col[3][3];
+  bool face_ok = m < a.M;
+  if (face_ok) {
     long long vi[3];
     if (a.map.faces) {
       vi[0] = a.map.faces[3 * m]; vi[1] = a.map.faces[3 * m + 1]; vi[2] = a.map.faces[3 * m + 2];
     } else {
       vi[0] = 3 * m; vi[1] = 3 * m + 1; vi[2] = 3 * m + 2;
     }
-    float u[3], v[3], z[3], o[3], xv[3], yv[3], wp[3][3], col[3][3];
-    vis = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-      if (vi[k] < 0 || vi[k] >= a.map.n_vertices) vis = false;
-    if (vis) {  // every load of the face up front, so that their latencies overlap
+      if (vi[k] < 0 || vi[k] >= a.map.n_vertices) face_ok = false;
+    if (face_ok) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const long long j = vi[k];
@@ -89,112 +94,124 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs a) {
         col[k][2] = __ldg(a.map.cb + j);
       }
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (!vis) break;
-      float xc, yc, zc;
-      ts_rigid_f32(P, wp[k][0], wp[k][1], wp[k][2], xc, yc, zc);
-      if (!(zc > a.z_near)) { vis = false; break; }
-      ts_pinhole_f32(vw, xc, yc, zc, u[k], v[k]);
-      z[k] = zc;
-      xv[k] = xc;
-      yv[k] = yc;
-    }
-    float area2 = 0.f, len[3] = {0.f, 0.f, 0.f}, per = 0.f, oF = 0.f;
-    if (vis) {
-      const float du1 = __fsub_rn(u[1], u[0]), dv1 = __fsub_rn(v[1], v[0]);
-      const float du2 = __fsub_rn(u[2], u[0]), dv2 = __fsub_rn(v[2], v[0]);
-      area2 = __fsub_rn(__fmul_rn(du1, dv2), __fmul_rn(du2, dv1));
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int j = (i + 1) % 3;
-        const float ex = __fsub_rn(u[j], u[i]), ey = __fsub_rn(v[j], v[i]);
-        len[i] = __fsqrt_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)));
-      }
-      per = __fadd_rn(__fadd_rn(len[0], len[1]), len[2]);
-      const float r = __fdiv_rn(fabsf(area2), per);
-      if (!(r >= a.r_min)) vis = false;
-      oF = a.min_opacity ? fminf(o[0], fminf(o[1], o[2])) : __fdiv_rn(__fadd_rn(__fadd_rn(o[0], o[1]), o[2]), 3.0f);
-      if (oF < a.alpha_min) vis = false;
-    }
-    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-    if (vis) {
-      const float umin = fminf(u[0], fminf(u[1], u[2])), umax = fmaxf(u[0], fmaxf(u[1], u[2]));
-      const float vmin = fminf(v[0], fminf(v[1], v[2])), vmax = fmaxf(v[0], fmaxf(v[1], v[2]));
-      const float fx0 = ceilf(__fsub_rn(umin, 0.5f)), fx1 = floorf(__fsub_rn(umax, 0.5f));
-      const float fy0 = ceilf(__fsub_rn(vmin, 0.5f)), fy1 = floorf(__fsub_rn(vmax, 0.5f));
-      const float Wm = (float)(vw.W - 1), Hm = (float)(vw.H - 1);
-      if (!(fx0 <= fx1) || fx1 < 0.0f || fx0 > Wm) vis = false;
-      if (!(fy0 <= fy1) || fy1 < 0.0f || fy0 > Hm) vis = false;
-      if (vis) {
-        x0 = fx0 < 0.0f ? 0 : (int)fx0;
-        x1 = fx1 > Wm ? vw.W - 1 : (int)fx1;
-        y0 = fy0 < 0.0f ? 0 : (int)fy0;
-        y1 = fy1 > Hm ? vw.H - 1 : (int)fy1;
-      }
-    }
-    if (vis) {
-      const float zk = __fdiv_rn(__fadd_rn(__fadd_rn(z[0], z[1]), z[2]), 3.0f);
-      a.zbits[idx] = __float_as_uint(zk);
-      // record: edge vectors, normalised edge-function scales s_i / D2, barycentric scale 1 / D2
-      const float e0x = u[1] - u[0], e0y = v[1] - v[0];
-      const float e1x = u[2] - u[1], e1y = v[2] - v[1];
-      const float e2x = u[0] - u[2], e2y = v[0] - v[2];
-      const float invD = 1.0f / area2;
-      const float k0 = (per / len[0]) * invD, k1 = (per / len[1]) * invD, k2 = (per / len[2]) * invD;
-      float4* rec = a.frec + idx * (TS_REC_WORDS / 4);
-      rec[0] = make_float4(u[0], u[1], u[2], v[0]);
-      rec[1] = make_float4(v[1], v[2], e0x, e0y);
-      rec[2] = make_float4(e1x, e1y, e2x, e2y);
-      rec[3] = make_float4(k0, k1, k2, invD);
-      rec[4] = make_float4(oF, col[0][0], col[0][1], col[0][2]);
-      rec[5] = make_float4(col[1][0], col[1][1], col[1][2], col[2][0]);
-      rec[6] = make_float4(col[2][1], col[2][2], z[0], z[1]);
-      // gradient slot of this (view, face), face-major so that a face's views are adjacent;
-      // cleared here for the raster backward's atomics
-      const long long slot = m * a.V + view;
-      rec[7] = make_float4(z[2], __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
-                           __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)slot));
-      float4* gs = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
-#pragma unroll
-      for (int i = 0; i < TS_GRAD_WORDS / 4; ++i) gs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      const int tx0 = x0 / a.tile_w, tx1 = x1 / a.tile_w, ty0 = y0 / a.tile_h, ty1 = y1 / a.tile_h;
-      a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
-      a.count[idx] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-      if (a.cov) a.cov[idx] = 0u;
-      float4 ax = make_float4(0.f, 0.f, 0.f, a.sigma ? __ldg(a.sigma + m) : 0.f);
-      if (a.normals) {
-        // unit normal (v1 - v0) x (v2 - v0), turned towards the camera.  The edge vectors are
-        // taken in world space, where nearby float32 positions subtract almost exactly, and the
-        // unit normal is then rotated by R: camera-space edges would be differences of
-        // metre-sized coordinates and lose ~1e-5 of the normal for centimetre faces.
-        float e1[3], e2[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          e1[c] = wp[1][c] - wp[0][c];
-          e2[c] = wp[2][c] - wp[0][c];
-        }
-        const float wx = e1[1] * e2[2] - e1[2] * e2[1], wy = e1[2] * e2[0] - e1[0] * e2[2];
-        const float wz = e1[0] * e2[1] - e1[1] * e2[0];
-        const float inv = rsqrtf(wx * wx + wy * wy + wz * wz);
-        float nc[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) nc[r] = (P.R[3 * r] * wx + P.R[3 * r + 1] * wy + P.R[3 * r + 2] * wz) * inv;
-        const float facing =
-            nc[0] * (xv[0] + xv[1] + xv[2]) + nc[1] * (yv[0] + yv[1] + yv[2]) + nc[2] * (z[0] + z[1] + z[2]);
-        const float sg = facing > 0.f ? -1.f : 1.f;
-        ax.x = sg * nc[0];
-        ax.y = sg * nc[1];
-        ax.z = sg * nc[2];
-      }
-      if (a.aux) a.aux[idx] = ax;
-    } else {
-      a.rect[idx] = make_short4(-1, -1, -1, -1);
-      a.count[idx] = 0u;
-    }
   }
-  const unsigned ball = __ballot_sync(0xffffffffu, vis);
-  if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&a.hdr->n_visible, (unsigned long long)__popc(ball));
+  const float sig_m = (face_ok && a.sigma) ? __ldg(a.sigma + m) : 0.f;
+  for (int view = v0; view < v1; ++view) {
+    const long long idx = (long long)view * a.M + m;
+    bool vis = face_ok;
+    if (m < a.M) {
+      const TsView vw = a.views[view];
+      const ts_pose P = a.poses[view];
+      float u[3], v[3], z[3], xv[3], yv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (!vis) break;
+        float xc, yc, zc;
+        ts_rigid_f32(P, wp[k][0], wp[k][1], wp[k][2], xc, yc, zc);
+        if (!(zc > a.z_near)) { vis = false; break; }
+        ts_pinhole_f32(vw, xc, yc, zc, u[k], v[k]);
+        z[k] = zc;
+        xv[k] = xc;
+        yv[k] = yc;
+      }
+      float area2 = 0.f, len[3] = {0.f, 0.f, 0.f}, per = 0.f, oF = 0.f;
+      if (vis) {
+        const float du1 = __fsub_rn(u[1], u[0]), dv1 = __fsub_rn(v[1], v[0]);
+        const float du2 = __fsub_rn(u[2], u[0]), dv2 = __fsub_rn(v[2], v[0]);
+        area2 = __fsub_rn(__fmul_rn(du1, dv2), __fmul_rn(du2, dv1));
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const int j = (i + 1) % 3;
+          const float ex = __fsub_rn(u[j], u[i]), ey = __fsub_rn(v[j], v[i]);
+          len[i] = __fsqrt_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)));
+        }
+        per = __fadd_rn(__fadd_rn(len[0], len[1]), len[2]);
+        const float r = __fdiv_rn(fabsf(area2), per);
+        if (!(r >= a.r_min)) vis = false;
+        oF = a.min_opacity ? fminf(o[0], fminf(o[1], o[2])) : __fdiv_rn(__fadd_rn(__fadd_rn(o[0], o[1]), o[2]), 3.0f);
+        if (oF < a.alpha_min) vis = false;
+      }
+      int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+      if (vis) {
+        const float umin = fminf(u[0], fminf(u[1], u[2])), umax = fmaxf(u[0], fmaxf(u[1], u[2]));
+        const float vmin = fminf(v[0], fminf(v[1], v[2])), vmax = fmaxf(v[0], fmaxf(v[1], v[2]));
+        const float fx0 = ceilf(__fsub_rn(umin, 0.5f)), fx1 = floorf(__fsub_rn(umax, 0.5f));
+        const float fy0 = ceilf(__fsub_rn(vmin, 0.5f)), fy1 = floorf(__fsub_rn(vmax, 0.5f));
+        const float Wm = (float)(vw.W - 1), Hm = (float)(vw.H - 1);
+        if (!(fx0 <= fx1) || fx1 < 0.0f || fx0 > Wm) vis = false;
+        if (!(fy0 <= fy1) || fy1 < 0.0f || fy0 > Hm) vis = false;
+        if (vis) {
+          x0 = fx0 < 0.0f ? 0 : (int)fx0;
+          x1 = fx1 > Wm ? vw.W - 1 : (int)fx1;
+          y0 = fy0 < 0.0f ? 0 : (int)fy0;
+          y1 = fy1 > Hm ? vw.H - 1 : (int)fy1;
+        }
+      }
+      if (vis) {
+        const float zk = __fdiv_rn(__fadd_rn(__fadd_rn(z[0], z[1]), z[2]), 3.0f);
+        a.zbits[idx] = __float_as_uint(zk);
+        // record: edge vectors, normalised edge-function scales s_i / D2, barycentric scale 1 / D2
+        const float e0x = u[1] - u[0], e0y = v[1] - v[0];
+        const float e1x = u[2] - u[1], e1y = v[2] - v[1];
+        const float e2x = u[0] - u[2], e2y = v[0] - v[2];
+        const float invD = 1.0f / area2;
+        const float k0 = (per / len[0]) * invD, k1 = (per / len[1]) * invD, k2 = (per / len[2]) * invD;
+        float4* rec = a.frec + idx * (TS_REC_WORDS / 4);
+        rec[0] = make_float4(u[0], u[1], u[2], v[0]);
+        rec[1] = make_float4(v[1], v[2], e0x, e0y);
+        rec[2] = make_float4(e1x, e1y, e2x, e2y);
+        rec[3] = make_float4(k0, k1, k2, invD);
+        rec[4] = make_float4(oF, col[0][0], col[0][1], col[0][2]);
+        rec[5] = make_float4(col[1][0], col[1][1], col[1][2], col[2][0]);
+        rec[6] = make_float4(col[2][1], col[2][2], z[0], z[1]);
+        // gradient slot of this (view, face), face-major so that a face's views are adjacent;
+        // cleared here for the raster backward's atomics
+        const long long slot = m * a.V + view;
+        rec[7] = make_float4(z[2], __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
+                             __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)slot));
+        if (a.grad) {  // null for a forward-only plan
+          float4* gs = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
+#pragma unroll
+          for (int i = 0; i < TS_GRAD_WORDS / 4; ++i) gs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int tx0 = x0 / a.tile_w, tx1 = x1 / a.tile_w, ty0 = y0 / a.tile_h, ty1 = y1 / a.tile_h;
+        a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
+        a.count[idx] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        if (a.cov) a.cov[idx] = 0u;
+        float4 ax = make_float4(0.f, 0.f, 0.f, sig_m);
+        if (a.normals) {
+          // unit normal (v1 - v0) x (v2 - v0), turned towards the camera.  The edge vectors are
+          // taken in world space, where nearby float32 positions subtract almost exactly, and the
+          // unit normal is then rotated by R: camera-space edges would be differences of
+          // metre-sized coordinates and lose ~1e-5 of the normal for centimetre faces.
+          float e1[3], e2[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            e1[c] = wp[1][c] - wp[0][c];
+            e2[c] = wp[2][c] - wp[0][c];
+          }
+          const float wx = e1[1] * e2[2] - e1[2] * e2[1], wy = e1[2] * e2[0] - e1[0] * e2[2];
+          const float wz = e1[0] * e2[1] - e1[1] * e2[0];
+          const float inv = rsqrtf(wx * wx + wy * wy + wz * wz);
+          float nc[3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) nc[r] = (P.R[3 * r] * wx + P.R[3 * r + 1] * wy + P.R[3 * r + 2] * wz) * inv;
+          const float facing =
+              nc[0] * (xv[0] + xv[1] + xv[2]) + nc[1] * (yv[0] + yv[1] + yv[2]) + nc[2] * (z[0] + z[1] + z[2]);
+          const float sg = facing > 0.f ? -1.f : 1.f;
+          ax.x = sg * nc[0];
+          ax.y = sg * nc[1];
+          ax.z = sg * nc[2];
+        }
+        if (a.aux) a.aux[idx] = ax;
+      } else {
+        a.rect[idx] = make_short4(-1, -1, -1, -1);
+        a.count[idx] = 0u;
+      }
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, vis);
+    if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&a.hdr->n_visible, (unsigned long long)__popc(ball));
+  }
 }
 
 }  // namespace
@@ -234,6 +251,11 @@ cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* 
   a.zbits = w.zbits;
   a.count = w.count;
   a.hdr = w.hdr;
-  k_project<<<(unsigned)((VM + 255) / 256), 256, 0, s>>>(a);
+  // views per thread: as many as keep about 16 resident warps of faces per SM busy
+  const long long face_blocks = (p->M + 255) / 256;
+  const long long want_blocks = (long long)ts_sm_count() * 8;
+  const int chunks = (int)std::max(1LL, std::min<long long>(p->V, want_blocks / std::max(1LL, face_blocks)));
+  const int per = (p->V + chunks - 1) / chunks;
+  k_project<<<dim3((unsigned)face_blocks, (unsigned)((p->V + per - 1) / per)), 256, 0, s>>>(a, per);
   return cudaGetLastError();
 }

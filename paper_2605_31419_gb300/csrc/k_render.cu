@@ -330,7 +330,7 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, fl
           if (lane == (j & 31)) lm = bl;
           if (bl && lane == 0 && a.cov) atomicAdd(&fm.cv[b][j], (unsigned)__popc(bl));
         }
-        if (jq < cnt) a.lmask[(size_t)(rg.x + (uint32_t)(st * S + jq)) * (TW * TH / 32) + warp] = lm;
+        if (a.lmask && jq < cnt) a.lmask[(size_t)(rg.x + (uint32_t)(st * S + jq)) * (TW * TH / 32) + warp] = lm;
       }
       const int alive = __syncthreads_count(!done);
       if (a.cov) {

@@ -111,7 +111,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   if (!(prm->sigma > 0.0f) || !(prm->alpha_max > 0.0f && prm->alpha_max < 1.0f) || !(prm->alpha_min >= 0.0f) ||
       !(prm->T_min >= 0.0f && prm->T_min < 1.0f) || !(prm->z_near > 0.0f) || !(prm->r_min >= 0.0f) ||
       (prm->flags & ~(TS_FLAG_PERSISTENT | TS_FLAG_NORMALS | TS_FLAG_STATS | TS_FLAG_MIN_OPACITY |
-                       TS_FLAG_FACE_SIGMA)) != 0)
+                       TS_FLAG_FACE_SIGMA | TS_FLAG_FORWARD_ONLY)) != 0)
     return TS_ERR_INVALID_ARG;
   if (pair_capacity < 0) return TS_ERR_INVALID_ARG;
   memset(plan, 0, sizeof(ts_plan));
@@ -157,6 +157,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->stats = (prm->flags & TS_FLAG_STATS) != 0;
   p->min_opacity = (prm->flags & TS_FLAG_MIN_OPACITY) != 0;
   p->face_sigma = (prm->flags & TS_FLAG_FACE_SIGMA) != 0;
+  p->fwd_only = (prm->flags & TS_FLAG_FORWARD_ONLY) != 0;
   // layout
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -178,10 +179,10 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_ranges = take((size_t)toff * 8);
   p->o_tfin = take((size_t)poff * 4);
   p->o_nlast = take((size_t)poff * 4);
-  p->o_grad = take((size_t)VM * TS_GRAD_WORDS * 4);
+  p->o_grad = take(p->fwd_only ? 0 : (size_t)VM * TS_GRAD_WORDS * 4);
   p->o_pose = take((size_t)n_views * p->n_pose_blocks * 6 * 4);
   p->o_loss = take((size_t)n_views * p->n_loss_blocks * 2 * 4);
-  p->o_lmask = take((size_t)cap * (size_t)(prm->tile_w * prm->tile_h / 32) * 4);
+  p->o_lmask = take(p->fwd_only ? 0 : (size_t)cap * (size_t)(prm->tile_w * prm->tile_h / 32) * 4);
   p->o_pho = take((size_t)n_views * p->n_pho_blocks * 3 * 4);
   p->o_equi = take((size_t)ts_equi_blocks(n_faces) * 4);
   p->o_aux = take((p->normals || p->face_sigma) ? (size_t)VM * 16 : 0);
@@ -289,7 +290,7 @@ ts_status ts_render_bwd(const ts_plan* plan, void* ws, const float* dC, const fl
 ts_status ts_render_bwd_n(const ts_plan* plan, void* ws, const float* dC, const float* dD, const float* dA,
                           const float* dN, const ts_map_grad* grad, ts_stream stream) {
   const TsPlanImpl* p = impl(plan);
-  if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) || !dC) return TS_ERR_INVALID_ARG;
+  if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) || !dC || p->fwd_only) return TS_ERR_INVALID_ARG;
   if (dN && !p->normals) return TS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   TsWs w = ts_ws(p, ws);
@@ -309,7 +310,8 @@ ts_status ts_render_step_l1(const ts_plan* plan, void* ws, const float* tgt_colo
                            float lambda_dep, float* color, float* depth, float* alpha, float* loss, float* dC,
                            float* dD, const ts_map_grad* grad, ts_stream stream) {
   const TsPlanImpl* p = impl(plan);
-  if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) || !tgt_color || !tgt_depth || !color || !loss)
+  if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) || !tgt_color || !tgt_depth || !color || !loss ||
+      p->fwd_only)
     return TS_ERR_INVALID_ARG;
   if (!(lambda_dep >= 0.0f) || !std::isfinite(lambda_dep)) return TS_ERR_INVALID_ARG;
   if (p->normals || p->face_sigma) return TS_ERR_INVALID_ARG;
@@ -329,7 +331,7 @@ ts_status ts_render_step_l1(const ts_plan* plan, void* ws, const float* tgt_colo
 
 ts_status ts_pose_grad(const ts_plan* plan, void* ws, float* dtau, ts_stream stream) {
   const TsPlanImpl* p = impl(plan);
-  if (!p || !ws || !dtau || (reinterpret_cast<uintptr_t>(ws) & 255)) return TS_ERR_INVALID_ARG;
+  if (!p || !ws || !dtau || (reinterpret_cast<uintptr_t>(ws) & 255) || p->fwd_only) return TS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   StageTimer t(p, TS_STAGE_POSE, s);
   return cuda_status(ts_launch_pose_reduce(p, ts_ws(p, ws), dtau, s));

@@ -91,6 +91,7 @@ struct TsPlanImpl {
   bool stats;    // TS_FLAG_STATS
   bool min_opacity;  // TS_FLAG_MIN_OPACITY
   bool face_sigma;   // TS_FLAG_FACE_SIGMA
+  bool fwd_only;     // TS_FLAG_FORWARD_ONLY: no gradient slots, no lane masks
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_tcnt, o_bsums, o_tlarge, o_tmat, o_tloss, o_keys0, o_keys1,
       o_vals0, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_lmask, o_pho, o_equi, o_aux, o_nloss,
@@ -153,7 +154,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.ranges = (uint2*)(b + p->o_ranges);
   w.tfin = (float*)(b + p->o_tfin);
   w.nlast = (int32_t*)(b + p->o_nlast);
-  w.grad = (float*)(b + p->o_grad);
+  w.grad = p->fwd_only ? nullptr : (float*)(b + p->o_grad);
   w.pose = (float*)(b + p->o_pose);
   w.loss = (float*)(b + p->o_loss);
   w.pho = (float*)(b + p->o_pho);
@@ -161,7 +162,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.aux = (p->normals || p->face_sigma) ? (float4*)(b + p->o_aux) : nullptr;
   w.nloss = (float*)(b + p->o_nloss);
   w.cov = p->stats ? (uint32_t*)(b + p->o_cov) : nullptr;
-  w.lmask = (uint32_t*)(b + p->o_lmask);
+  w.lmask = p->fwd_only ? nullptr : (uint32_t*)(b + p->o_lmask);
   return w;
 }
 

@@ -10,6 +10,12 @@ and leaves, new ones join at the next step.  The two streams let a step's render
 overlap on the device, and the host prepares the next step while the device works.  Latency is
 arrival to completion (the completion event observed by the host).
 
+Render requests run on forward-only plans (TS_FLAG_FORWARD_ONLY): no gradient slots are cleared
+and no lane masks are stored for them, and their workspace is smaller.  ``serve_plain`` is the
+baseline without batching: the same requests, one at a time in arrival order, each on its own
+single-view plan.  A run ends ``drain_seconds`` after the last arrival; requests not finished by
+then are reported as not served.
+
 All arithmetic runs in libts kernels; torch moves pose rows, targets and results between request
 slots and the batch buffers.
 """
@@ -68,6 +74,9 @@ class Server:
                  lr_rot: float = 0.003, lr_trans: float = 0.001, lambda_dep: float = 0.05,
                  lambda_ssim: float = 0.2, hbm_fraction: float = 0.5, device="cuda"):
         self.map, self.params = m, (params if params is not None else B.ts_default_params())
+        # render requests: the same launch shape on forward-only plans
+        self.render_params = B.TsRasterParams.from_buffer_copy(self.params)
+        self.render_params.flags |= B.TS_FLAG_FORWARD_ONLY
         self.max_views, self.max_pixels = int(max_views), int(max_pixels)
         self.track_iters, self.lambda_dep = int(track_iters), float(lambda_dep)
         self.lambda_ssim = float(lambda_ssim)
@@ -127,14 +136,14 @@ class Server:
         self.stats = dict(steps=0, pixels=0, rejected_for_memory=0)
 
     # ---------------------------------------------------------------- admission
-    def _fits(self, cams: List[np.ndarray]) -> bool:
+    def _fits(self, cams: List[np.ndarray], render: bool = False) -> bool:
         if len(cams) > self.max_views or sum(int(c[4]) * int(c[5]) for c in cams) > self.max_pixels:
             return False
-        plan = B.ts_plan_init(np.stack(cams), self.map.n_faces, self.params, self.pair_capacity)
-        return B.ts_workspace_size(plan) <= self.ws_bytes
+        return B.ts_workspace_size(self._plan(cams, render)) <= self.ws_bytes
 
-    def _plan(self, cams: List[np.ndarray]):
-        return B.ts_plan_init(np.stack(cams), self.map.n_faces, self.params, self.pair_capacity)
+    def _plan(self, cams: List[np.ndarray], render: bool = False):
+        return B.ts_plan_init(np.stack(cams), self.map.n_faces, self.render_params if render else self.params,
+                              self.pair_capacity)
 
     # ---------------------------------------------------------------- one scheduler step
     def _launch_renders(self, reqs: List[Request]):
@@ -142,7 +151,7 @@ class Server:
             return
         lane = self.render_lane
         cams = [r.cam for r in reqs]
-        plan = self._plan(cams)
+        plan = self._plan(cams, render=True)
         with torch.cuda.stream(lane.stream):
             s = lane.stream
             poses = torch.as_tensor(np.stack([r.pose for r in reqs]).astype(np.float32), device=self.device)
@@ -216,9 +225,14 @@ class Server:
             lane.pending = keep
 
     # ---------------------------------------------------------------- driver
-    def run(self, requests: List[Request], realtime: bool = True, max_seconds: float = 120.0):
-        """Serve ``requests`` (sorted by t_arrival).  Returns the requests with results and times."""
+    def run(self, requests: List[Request], realtime: bool = True, max_seconds: Optional[float] = None,
+            drain_seconds: float = 5.0):
+        """Serve ``requests`` (sorted by t_arrival) until all are done or until ``drain_seconds`` after
+        the last arrival (``max_seconds``, if given, caps the run).  Returns the requests with results
+        and times; unfinished ones keep t_done < 0."""
         queue = deque(sorted(requests, key=lambda r: r.t_arrival))
+        if max_seconds is None:
+            max_seconds = (queue[-1].t_arrival if queue else 0.0) + drain_seconds
         active: List[Request] = []
         self._t0 = time.perf_counter()
         while (queue or active) and time.perf_counter() - self._t0 < max_seconds:
@@ -231,7 +245,7 @@ class Server:
                 r = queue[0]
                 cams_r = [x.cam for x in renders] + [r.cam] if r.kind == "render" else None
                 cams_t = [x.cam for x in tracks] + [r.cam] if r.kind == "track" else None
-                ok = self._fits(cams_r) if r.kind == "render" else (self._fits(cams_t) and bool(self.free_slots))
+                ok = self._fits(cams_r, True) if r.kind == "render" else (self._fits(cams_t) and bool(self.free_slots))
                 if not ok:
                     self.stats["rejected_for_memory"] += 1
                     break  # wait for the running work to leave room
@@ -274,15 +288,86 @@ class Server:
 
 
 def latency_stats(requests: List[Request], seconds: float):
+    """Per request kind: completed and not-served counts, and p50/p99 latency over ALL submitted
+    requests of the kind, a request that was not served counting as infinitely late (a percentile
+    that falls on one is reported as null with ``..._not_served`` true).  Mpix/s counts the pixels
+    of completed requests (a track request: pixels x iterations) over the run's wall time."""
     out = {}
     for kind in ("render", "track"):
-        lat = np.array([r.t_done - r.t_arrival for r in requests if r.kind == kind and r.t_done >= 0])
-        if len(lat):
-            out[kind] = {"n": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                         "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+        ks = [r for r in requests if r.kind == kind]
+        if not ks:
+            continue
+        lat = np.array([(r.t_done - r.t_arrival) if r.t_done >= 0 else np.inf for r in ks])
+        d = {"n": int(np.isfinite(lat).sum()), "not_served": int((~np.isfinite(lat)).sum()), "submitted": len(ks)}
+        for q in (50, 99):
+            v = float(np.percentile(lat, q, method="higher"))
+            d[f"p{q}_ms"] = v * 1e3 if np.isfinite(v) else None
+            if not np.isfinite(v):
+                d[f"p{q}_not_served"] = True
+        out[kind] = d
     done = [r for r in requests if r.t_done >= 0]
     px = sum(r.pixels * (1 if r.kind == "render" else max(r.iters_done, 1)) for r in done)
     out["mpix_s"] = px / max(seconds, 1e-9) / 1e6
     out["completed"] = len(done)
+    out["not_served"] = len(requests) - len(done)
     out["submitted"] = len(requests)
+    out["seconds"] = seconds
     return out
+
+
+def serve_plain(m: Map, requests: List[Request], params: Optional[B.TsRasterParams] = None, track_iters: int = 10,
+                lr_rot: float = 0.003, lr_trans: float = 0.001, lambda_dep: float = 0.05, lambda_ssim: float = 0.2,
+                realtime: bool = True, drain_seconds: float = 5.0, device="cuda") -> float:
+    """The baseline without batching: each request alone, in arrival order, on a single-view plan
+    (one per resolution, reused): a render is one forward on a forward-only plan, a track request
+    its ``track_iters`` gradient iterations back to back.  Same losses and optimiser as ``Server``.
+    Returns the run's wall seconds; each request gets t_done (or keeps -1 if not served)."""
+    from .rasterizer import Rasterizer
+    params = params if params is not None else B.ts_default_params()
+    rparams = B.TsRasterParams.from_buffer_copy(params)
+    rparams.flags |= B.TS_FLAG_FORWARD_ONLY
+    dev = torch.device(device)
+    rasts = {}
+
+    def rast(cam, render):
+        key = (int(cam[4]), int(cam[5]), float(cam[0]), render)
+        if key not in rasts:
+            rasts[key] = Rasterizer(cam[None, :], m.n_faces, rparams if render else params, device=dev)
+        return rasts[key]
+
+    pose = torch.empty(1, 12, device=dev)
+    adam = torch.empty(1, 13, device=dev)
+    order = sorted(requests, key=lambda r: r.t_arrival)
+    end = (order[-1].t_arrival if order else 0.0) + drain_seconds
+    for r in order:  # plans and workspaces before the clock starts
+        rast(r.cam, r.kind == "render")
+    t0 = time.perf_counter()
+    for r in order:
+        now = time.perf_counter() - t0
+        if now > end:
+            break
+        if realtime and r.t_arrival > now:
+            time.sleep(r.t_arrival - now)
+        R = rast(r.cam, r.kind == "render")
+        pose.copy_(torch.as_tensor(np.asarray(r.pose, np.float32).reshape(1, 12)))
+        if r.kind == "render":
+            C, D, A = R.forward(m, pose)
+            H, W = int(r.cam[5]), int(r.cam[4])
+            r.color, r.depth, r.alpha = C.view(3, H, W).clone(), D.view(H, W).clone(), A.view(H, W).clone()
+        else:
+            adam.zero_()
+            tc, td = r.target_color.reshape(-1), r.target_depth.reshape(-1)
+            for _ in range(track_iters):
+                R.forward(m, pose)
+                if lambda_ssim > 0:
+                    R.pho_loss(tc, td, lambda_ssim, lambda_dep)
+                else:
+                    R.l1_loss(tc, td, lambda_dep)
+                R.backward(R.dC, R.dD, None, None)
+                R.pose_grad()
+                B.ts_pose_adam(R.plan, pose, R.dtau, adam, lr_trans, lr_rot)
+            r.iters_done = track_iters
+            r.pose_out = pose[0].clone()
+        torch.cuda.synchronize(dev)
+        r.t_done = time.perf_counter() - t0
+    return time.perf_counter() - t0

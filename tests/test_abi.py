@@ -150,3 +150,24 @@ def test_noalloc_binding_checks_tensors_before_any_launch(ts):
         ts.binding.check_noalloc_args(cams, **bad)
     with pytest.raises(ValueError, match="CUDA"):  # right sizes, but host memory
         ts.binding.check_noalloc_args(cams, **ok)
+
+
+def test_forward_only_plan_is_smaller_and_refuses_backward(ts):
+    """A TS_FLAG_FORWARD_ONLY plan lays out no gradient slots and no lane masks, and the calls that
+    need them return TS_ERR_INVALID_ARG before launching anything (checked with placeholder
+    pointers that are never dereferenced)."""
+    import ctypes as C
+    cams = np.array([[600.0, 600.0, 600.0, 340.0, 1200, 680]] * 2)
+    full = ts.ts_plan_init(cams, 50_000, ts.ts_default_params())
+    fwd = ts.ts_plan_init(cams, 50_000, ts.ts_default_params(flags=ts.TS_FLAG_FORWARD_ONLY))
+    saved = ts.ts_workspace_size(full) - ts.ts_workspace_size(fwd)
+    # gradient slots (128 B per (view, face)) and lane masks (16 B per pair of the capacity)
+    assert saved >= 2 * 50_000 * 128 + 4 * 2 * 50_000 * 16 - 4096, saved
+    L = ts.binding.lib()
+    fake = C.c_void_p(1 << 20)  # 256-byte aligned, never touched
+    g = ts.binding.TsMapGrad()
+    assert L.ts_render_bwd(C.byref(fwd), fake, fake, None, None, C.byref(g), None) == 1
+    assert L.ts_render_bwd_n(C.byref(fwd), fake, fake, None, None, None, C.byref(g), None) == 1
+    assert L.ts_pose_grad(C.byref(fwd), fake, fake, None) == 1
+    assert L.ts_render_step_l1(C.byref(fwd), fake, fake, fake, 0.05, fake, None, None, fake, None, None,
+                               C.byref(g), None) == 1

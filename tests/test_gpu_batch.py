@@ -117,3 +117,32 @@ def test_mapping_loss_step_composes_the_terms():
     ts.MultiViewStep(m, sc.cams, poses, tc, td, None, g_pho, lambda_ssim=0.2).run(1)
     torch.cuda.synchronize()
     assert np.abs(g_pho.pos.cpu().numpy() - g_full.pos.cpu().numpy()).max() > 1e-3 * np.abs(g_full.pos.cpu().numpy()).max()
+
+
+def test_fused_window_step_equals_separate_calls():
+    """With the plain L1 loss MultiViewStep runs the fused ts_render_step_l1 pass: on mixed
+    resolutions it gives the images, the loss and (to atomic order) the map and pose gradients of
+    the separate forward, loss and backward calls."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    sc = _window()
+    p = ts.ts_default_params()
+    st, g = _step(sc, p)
+    assert st.fused
+    m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa)
+    g2 = m.zeros_like()
+    r = ts.Rasterizer(sc.cams, sc.n_faces, p)
+    tc = torch.as_tensor(np.concatenate([t.reshape(-1) for t in sc.tgt_color]), device="cuda")
+    td = torch.as_tensor(np.concatenate([t.reshape(-1) for t in sc.tgt_depth]), device="cuda")
+    r.forward(m, ts.poses_tensor(sc.poses))
+    r.l1_loss(tc, td, 0.05)
+    r.backward(r.dC, r.dD, None, g2)
+    r.pose_grad()
+    torch.cuda.synchronize()
+    for k in ("color", "depth", "alpha"):
+        assert torch.equal(getattr(st.rast, k), getattr(r, k)), k
+    assert np.allclose(st.rast.loss_v.cpu().numpy(), r.loss_v.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    for k in ("pos", "col", "opa"):
+        assert_grad(getattr(g, k).cpu().numpy(), getattr(g2, k).cpu().numpy(), f"d{k} fused vs separate", rtol=1e-4)
+    assert np.allclose(st.rast.dtau.cpu().numpy(), r.dtau.cpu().numpy(), rtol=1e-4,
+                       atol=1e-4 * np.abs(r.dtau.cpu().numpy()).max())

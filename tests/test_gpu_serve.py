@@ -78,3 +78,59 @@ def test_admission_waits_for_memory():
     assert srv.stats["steps"] >= 3 and srv.stats["rejected_for_memory"] >= 2
     st = ts.latency_stats(out, srv.stats["seconds"])
     assert st["completed"] == 6 and st["render"]["p99_ms"] >= st["render"]["p50_ms"]
+
+
+def test_forward_only_plan_renders_the_same_images():
+    """TS_FLAG_FORWARD_ONLY (the server's render plans) changes what is stored, not what is
+    rendered: colour, depth and opacity bit for bit against a full plan, on one view and on three
+    views of uneven size."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    from ts_synth.scenes import random_triangles_scene
+    pos, col, opa = room_map(3, 20000)
+    cams = np.array([[70.0, 70.0, 50.0, 37.5, 100, 75], [40.0, 40.0, 28.5, 16.5, 57, 33],
+                     [90.0, 90.0, 61.0, 40.0, 123, 81]])
+    sc1 = random_triangles_scene(seed=1)
+    cases = [(ts.Map.from_numpy(sc1.pos, sc1.col, sc1.opa), sc1.cams, sc1.poses),
+             (ts.Map.from_numpy(pos, col, opa), cams, trajectory_poses(1003, 3))]
+    for m, cm, ps in cases:
+        full = ts.Rasterizer(cm, m.n_faces)
+        fwd = ts.Rasterizer(cm, m.n_faces, ts.ts_default_params(flags=ts.TS_FLAG_FORWARD_ONLY))
+        assert fwd.ws_bytes < full.ws_bytes
+        a = [t.clone() for t in full.forward(m, ts.poses_tensor(ps))]
+        b = fwd.forward(m, ts.poses_tensor(ps))
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+        assert fwd.counters()["status"] == "TS_OK"
+
+
+def test_plain_baseline_gives_the_served_results():
+    """serve_plain (one request at a time, single-view plans) returns the renders of the batching
+    server bit for bit and its tracked poses within 1e-4."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    pos, col, opa = room_map(11, 40000, side_lo=0.05, side_hi=0.12)
+    m = ts.Map.from_numpy(pos, col, opa)
+    n_poses = 6
+    gts = trajectory_poses(2000 + 5, n_poses)
+    targets = {}
+    for (W, H, f) in RES:
+        r = ts.Rasterizer(np.array([[f, f, W / 2, H / 2, W, H]]), m.n_faces)
+        for k in range(n_poses):
+            C, D, _ = r.forward(m, ts.poses_tensor(gts[k][None, :]))
+            targets[(W, H, k)] = (C.clone().view(3, H, W), D.clone().view(H, W))
+    a = _requests(5, n_poses, targets)
+    b = _requests(5, n_poses, targets)
+    srv = ts.Server(m, max_views=16, max_pixels=16 * 120 * 68, track_iters=10)
+    srv.run(a, realtime=False)
+    secs = ts.serve_plain(m, b, track_iters=10, realtime=False)
+    torch.cuda.synchronize()
+    st = ts.latency_stats(b, secs)
+    assert st["not_served"] == 0 and st["completed"] == len(b)
+    for x, y in zip(a, b):
+        if x.kind == "render":
+            assert torch.equal(x.color, y.color) and torch.equal(x.depth, y.depth)
+        else:
+            assert y.iters_done == 10
+            assert np.allclose(x.pose_out.cpu().numpy(), y.pose_out.cpu().numpy(), atol=1e-4)
