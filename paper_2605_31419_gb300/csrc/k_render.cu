@@ -18,10 +18,11 @@
 // dL/dalpha_n = T_n v_n - S / (1 - alpha_n) with v_n = gC . c_n + gD z_n + gA, and chain into 23
 // per-face sums (barycentric-weighted gradients of the edge, colour and depth interpolants, of
 // o_F, and the contribution count).  The forward stores, per sorted pair and warp, the 32-bit
-// mask of the warp's pixels that blended the face; the backward queues those (face, pixel)
-// entries back to front and processes them 32 at a time, one per lane, so that no lane idles on
-// a pixel the face does not cover.  Lanes holding entries of the same pixel replay its recurrence
-// in queue order (the same products and sums, in the same order, as a per-pixel loop).  Every
+// mask of the warp's pixels that blended the face; the backward numbers those (face, pixel)
+// entries back to front (a warp-wide scan of the masks' bit counts) and processes them 32 at a
+// time, one per lane, so that no lane idles on a pixel the face does not cover.  Lanes holding
+// entries of the same pixel replay its recurrence in entry order (the same products and sums, in
+// the same order, as a per-pixel loop).  Every
 // per-face sum is over products of two per-entry factors (a weighted gradient times a
 // barycentric coordinate, or a scalar times one); each lane writes its factors to a ring row in
 // shared memory, and lane L then sums word L's products over each face's run of rows and adds it
@@ -121,17 +122,15 @@ struct PixIn {
   int nmax;  // the same in every thread: the tile's largest nl
 };
 
-// Backward scratch per warp: a queue of contributing (face, pixel) entries found by the visits,
-// the pixels' back-to-front state, and the ring of one batch's rows.  A ring row holds the
+// Backward scratch per warp: the pixels' back-to-front state and the ring of one batch's rows.  A ring row holds the
 // factors of one entry; row words: 0-2 barycentrics l_k; 3-5 w gC_c; 6 w gD; 7-9 dm routed to
 // the nearest edge (zero for the other two); 10 dL/do_F; 11 one; with the side array 12-14 w gN_c
 // and 15 dL/dsigma_F.
 constexpr int RING_CAP = 32;   // rows: one batch of entries, one per lane
-constexpr int QUEUE_CAP = 64;  // entries: under 32 waiting plus one visit's up to 32
 template <bool AUX>
 struct Ring {
   static constexpr int EW = AUX ? 16 : 12;
-  static constexpr int BYTES_PER_WARP = RING_CAP * EW * 4 + 32 * 8 + QUEUE_CAP * 2;
+  static constexpr int BYTES_PER_WARP = RING_CAP * EW * 4 + 32 * 8;
 };
 
 template <int TW, int TH>
@@ -505,24 +504,24 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
                            (size_t)warp * Ring<AUX>::BYTES_PER_WARP;
     float* ring = reinterpret_cast<float*>(wbase);
     float2* pst = reinterpret_cast<float2*>(wbase + RING_CAP * EW * 4);  // per pixel lane: (T, S)
-    uint16_t* queue = reinterpret_cast<uint16_t*>(wbase + RING_CAP * EW * 4 + 32 * 8);  // face << 5 | pixel
     pst[lane] = make_float2(T, Sacc);
     int ia, ib;
     const bool has = ring_word<AUX>(lane, ia, ib);
-    const unsigned below = (1u << lane) - 1u;
     const int xw = g.x - (lane & 7), yw = g.y - (lane >> 3);  // the warp's first pixel
-    int head = 0, fill = 0;  // the queue's entries (the same in every lane)
     for (int k = 0; k < nst; ++k) {
       const int st = nst - 1 - k;
       int b = seq & 1;
       const int cnt = min(S, n - st * S);
       // The forward's lane masks (positions below the tile's largest list position after a
       // contribution were all written by it) give, per face, the pixels of this warp that blended
-      // it.  Visits back to front queue them; every 32 entries, and at the end of the stage, the
-      // lanes take one entry each.  The last chunk's masks load while the stage's copies land.
-      const uint32_t* lmrow = a.lmask + (size_t)(rg.x + (uint32_t)(st * S)) * (TW * TH / 32) + warp;
+      // it.  A chunk of 32 faces at a time, lane L holding face qq * 32 + 31 - L (back to front),
+      // the chunk's (face, pixel) entries are numbered face by face, pixels in lane order, and
+      // each batch of 32 consecutive entries gives every lane one.  The last chunk's masks load
+      // while the stage's copies land.
+      constexpr int NW = TW * TH / 32;
+      const uint32_t* lmrow = a.lmask + (size_t)(rg.x + (uint32_t)(st * S)) * NW + warp;
       int qq = (cnt - 1) >> 5;
-      unsigned lmc = qq * 32 + lane < cnt ? lmrow[(size_t)(qq * 32 + lane) * (TW * TH / 32)] : 0u;
+      unsigned lmc = qq * 32 + 31 - lane < cnt ? lmrow[(size_t)(qq * 32 + 31 - lane) * NW] : 0u;
       if (FUSED) {
         // the forward's last stage, and the one before it unless a prefetch replaced it, are
         // still staged; other stages are staged again (all warps are done with both buffers)
@@ -543,30 +542,44 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
       }
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
-      unsigned bits = __ballot_sync(FULL, lmc != 0u);
       for (;;) {
-        while (!bits && qq > 0) {
-          --qq;
-          lmc = lmrow[(size_t)(qq * 32 + lane) * (TW * TH / 32)];
-          bits = __ballot_sync(FULL, lmc != 0u);
+        // lane L's face has popc(lmc) entries; their numbers start at the exclusive scan
+        const int c = __popc(lmc);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += t;
         }
-        const bool more = bits != 0;
-        if (more) {
-          const int hb = 31 - __clz(bits);
-          bits &= ~(1u << hb);
-          const int j = qq * 32 + hb;
-          const unsigned cbm = __shfl_sync(FULL, lmc, hb);
-          if ((cbm >> lane) & 1u) queue[(head + fill + __popc(cbm & below)) & (QUEUE_CAP - 1)] = (uint16_t)((j << 5) | lane);
-          fill += __popc(cbm);
-        }
-        if (fill >= 32 || (!more && fill > 0)) {
-          const int ne = min(fill, 32);
-          __syncwarp();
-          // -- one entry per lane: face j at pixel lane p ---------------------------------------
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - c;
+        for (int e0 = 0; e0 < total; e0 += 32) {
+          const int ne = min(total - e0, 32);
           const bool act = lane < ne;
-          const unsigned ent = queue[(head + lane) & (QUEUE_CAP - 1)];
-          const int j = act ? (int)(ent >> 5) : 0;
-          const int p = act ? (int)(ent & 31u) : lane;
+          const int ee = e0 + lane;
+          // the entry's face: the last lane whose first number is at most ee (binary search)
+          int ow = 0;
+#pragma unroll
+          for (int w = 16; w > 0; w >>= 1) {
+            const int ex = __shfl_sync(FULL, excl, (ow + w) & 31);
+            if (ow + w < 32 && ex <= ee) ow += w;
+          }
+          const unsigned om = __shfl_sync(FULL, lmc, ow);
+          int kk = ee - __shfl_sync(FULL, excl, ow);  // the entry's rank among the face's pixels
+          int pb = 0;  // its pixel: the kk-th set bit of om
+          unsigned mm = om;
+#pragma unroll
+          for (int w = 16; w > 0; w >>= 1) {
+            const int cl = __popc(mm & ((1u << w) - 1u));
+            if (kk >= cl) {
+              kk -= cl;
+              pb += w;
+              mm >>= w;
+            }
+          }
+          const int j = act ? qq * 32 + 31 - ow : 0;
+          const int p = act ? pb : lane;
+          // -- one entry per lane: face j at pixel lane p ---------------------------------------
           const float4* r4 = reinterpret_cast<const float4*>(rb + j * TS_REC_WORDS);
           const float px = (float)(xw + (p & 7)) + 0.5f, py = (float)(yw + (p >> 3)) + 0.5f;
           const float sig = (AUX && a.face_sigma) ? nb[j].w : a.sigma;
@@ -577,7 +590,7 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
           const float I = act ? ts_window(e.m, sig) : 0.f;
           const float al = fminf(oF * I, a.alpha_max);
           const float ro = ts_rcp_approx(1.f - al);  // 1 - al >= 1 - alpha_max
-          // entries of the same pixel, in queue (back-to-front) order; each lane replays its
+          // entries of the same pixel, in entry (back-to-front) order; each lane replays its
           // pixel's recurrence T <- T / (1 - alpha) over the earlier ones and itself, in order
           const unsigned peers = __match_any_sync(FULL, act ? p : 32 + lane);
           const int K = (int)__reduce_max_sync(FULL, (unsigned)__popc(peers));
@@ -673,10 +686,9 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
             }
           }
           __syncwarp();
-          head += ne;
-          fill -= ne;
         }
-        if (!more && fill == 0) break;
+        if (--qq < 0) break;
+        lmc = lmrow[(size_t)(qq * 32 + 31 - lane) * NW];  // a full chunk below the last one
       }
     }
   }
