@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--views", type=int, default=N_VIEWS)
     ap.add_argument("--tile", default="16x8")
     ap.add_argument("--stage", type=int, default=64)
+    ap.add_argument("--eager", action="store_true",
+                    help="time the launches one by one instead of replaying the step from a CUDA graph")
     ap.add_argument("--separate", action="store_true",
                     help="time ts_render_fwd + ts_l1_loss + ts_render_bwd instead of the fused ts_render_step_l1")
     return ap.parse_args()
@@ -654,30 +656,57 @@ def main():
         step()
     torch.cuda.synchronize()
     cnt = rast.counters()
-    ts.ts_set_stage_events(rast.plan, ev)
-    stage_ms = np.zeros(len(ts.binding.STAGES))
+    # the step's launches captured once into a CUDA graph, replayed for the timed steps (the launch
+    # gaps of an eager sequence of ~15 kernels go); --eager times the launches one by one
+    graph = None
+    if not args.eager:
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                step()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+
+    def timed_steps(k, run, with_stages):
+        ms, st_ms = [], np.zeros(len(ts.binding.STAGES))
+        if with_stages:
+            ts.ts_set_stage_events(rast.plan, ev)
+        for _ in range(k):
+            flush.fill_(1.0)
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            run()
+            s1.record(stream)
+            s1.synchronize()
+            ms.append(s0.elapsed_time(s1))
+            if with_stages:
+                st_ms += [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(len(ts.binding.STAGES))]
+        if with_stages:
+            ts.ts_set_stage_events(rast.plan, None)
+        return ms, st_ms / max(k, 1)
+
     sampler = ClockSampler(dev.index or 0)
-    step_ms = []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        step()
-        s1.record(stream)
-        s1.synchronize()
-        step_ms.append(s0.elapsed_time(s1))
-        for k in range(len(ts.binding.STAGES)):
-            stage_ms[k] += ev[2 * k].elapsed_time(ev[2 * k + 1])
+    step_ms, stage_ms = timed_steps(args.steps, graph.replay if graph is not None else step, graph is None)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ts.ts_set_stage_events(rast.plan, None)
     t_step = max_over_ranks(float(np.sum(step_ms)) / args.steps / 1e3, dev if world > 1 else None)
-    stage_ms /= args.steps
+    # stage times (CUDA events recorded by libts around each stage) from eager steps outside the
+    # timed region when the timed steps are graph replays
+    eager_ms = None
+    if graph is not None:
+        e_ms, stage_ms = timed_steps(max(3, args.steps // 2), step, True)
+        eager_ms = float(np.mean(e_ms))
     pixels = sc.pixels()
     value = job_value(pixels, world, t_step)
 
@@ -747,6 +776,8 @@ def main():
                        "path": ("ts_render_fwd + ts_l1_loss + ts_render_bwd" if args.separate
                                 else "ts_render_step_l1 (forward, L1 loss and backward in one pass per tile)"),
                        "tile": args.tile, "tris_per_stage": args.stage, "l2": "flushed (256 MB write) between steps",
+                       "launch": "eager" if graph is None else "CUDA graph replay of the step's launches",
+                       "eager_ms_per_step": eager_ms,
                        "parallelism": f"replicas x{world}"},
             "plain_per_view": {"value": pixels / (plain_ms / 1e3) / 1e6 if plain_ms else None, "unit": "Mpix/s",
                                "ms_per_step": plain_ms},

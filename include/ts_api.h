@@ -257,7 +257,9 @@ ts_status ts_normal_loss(const ts_plan* plan, void* ws, const float* normal, con
  *   loss: device float [n_views], overwritten (fixed-order sums of per-tile partials);
  *   dC, dD: NULL, or device images that also receive the loss gradients;
  *   grad: as in ts_render_bwd (map gradients added; pose partials for ts_pose_grad).
- * Calls on the workspace: ts_project -> ts_bin -> ts_render_step_l1 [-> ts_pose_grad].  A plan with
+ * Calls on the workspace: ts_project -> ts_bin -> ts_render_step_l1 [-> ts_pose_grad].  The fused
+ * step does not record the per-pixel T_final and last-contribution position (its backward keeps
+ * them on the chip), so ts_render_bwd cannot follow it without a new ts_render_fwd.  A plan with
  * TS_FLAG_NORMALS or TS_FLAG_FACE_SIGMA, a NULL required pointer, or a negative or non-finite
  * lambda_dep returns TS_ERR_INVALID_ARG. */
 ts_status ts_render_step_l1(const ts_plan* plan, void* ws, const float* tgt_color, const float* tgt_depth,

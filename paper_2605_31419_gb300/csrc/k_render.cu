@@ -127,6 +127,7 @@ struct PixIn {
 // the nearest edge (zero for the other two); 10 dL/do_F; 11 one; with the side array 12-14 w gN_c
 // and 15 dL/dsigma_F.
 constexpr int RING_CAP = 32;   // rows: one batch of entries, one per lane
+constexpr int FMAX = 4;        // faces per lane when the backward numbers a stage's entries (128 / 32)
 template <bool AUX>
 struct Ring {
   static constexpr int EW = AUX ? 16 : 12;
@@ -381,8 +382,10 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, fl
       q[HW] = N1;
       q[2 * HW] = N2;
     }
-    a.tfin[o] = T;
-    a.nlast[o] = nl;
+    if (!FUSED) {  // what ts_render_bwd needs; the fused step keeps them in registers
+      a.tfin[o] = T;
+      a.nlast[o] = nl;
+    }
   }
 }
 
@@ -514,14 +517,19 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
       const int cnt = min(S, n - st * S);
       // The forward's lane masks (positions below the tile's largest list position after a
       // contribution were all written by it) give, per face, the pixels of this warp that blended
-      // it.  A chunk of 32 faces at a time, lane L holding face qq * 32 + 31 - L (back to front),
-      // the chunk's (face, pixel) entries are numbered face by face, pixels in lane order, and
-      // each batch of 32 consecutive entries gives every lane one.  The last chunk's masks load
-      // while the stage's copies land.
+      // it.  Lane L holds the masks of F = ceil(cnt / 32) faces, lane 0 the backmost; the stage's
+      // (face, pixel) entries are numbered back to front, face by face, pixels in lane order, and
+      // each batch of 32 consecutive numbers gives every lane one entry.  The masks load while
+      // the stage's copies land.
       constexpr int NW = TW * TH / 32;
       const uint32_t* lmrow = a.lmask + (size_t)(rg.x + (uint32_t)(st * S)) * NW + warp;
-      int qq = (cnt - 1) >> 5;
-      unsigned lmc = qq * 32 + 31 - lane < cnt ? lmrow[(size_t)(qq * 32 + 31 - lane) * NW] : 0u;
+      const int F = (cnt + 31) >> 5;  // faces per lane: lane L holds faces F * (32 - L) - 1 - i, i < F
+      unsigned lmk[FMAX];
+#pragma unroll
+      for (int i = 0; i < FMAX; ++i) {
+        const int jf = F * (32 - lane) - 1 - i;
+        lmk[i] = (i < F && jf < cnt) ? lmrow[(size_t)jf * NW] : 0u;
+      }
       if (FUSED) {
         // the forward's last stage, and the one before it unless a prefetch replaced it, are
         // still staged; other stages are staged again (all warps are done with both buffers)
@@ -542,9 +550,12 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
       }
       const float* rb = reinterpret_cast<const float*>(smrec + (size_t)b * S * 8);
       const float4* nb = smrec + (size_t)2 * S * 8 + (size_t)b * S;
-      for (;;) {
-        // lane L's face has popc(lmc) entries; their numbers start at the exclusive scan
-        const int c = __popc(lmc);
+      {
+        // lane L's faces have popc of their masks entries; their numbers start at the exclusive
+        // scan over the lanes, face by face within a lane
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < FMAX; ++i) c += __popc(lmk[i]);
         int incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -557,16 +568,33 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
           const int ne = min(total - e0, 32);
           const bool act = lane < ne;
           const int ee = e0 + lane;
-          // the entry's face: the last lane whose first number is at most ee (binary search)
+          // the entry's lane: the last lane whose first number is at most ee (binary search)
           int ow = 0;
 #pragma unroll
           for (int w = 16; w > 0; w >>= 1) {
             const int ex = __shfl_sync(FULL, excl, (ow + w) & 31);
             if (ow + w < 32 && ex <= ee) ow += w;
           }
-          const unsigned om = __shfl_sync(FULL, lmc, ow);
-          int kk = ee - __shfl_sync(FULL, excl, ow);  // the entry's rank among the face's pixels
-          int pb = 0;  // its pixel: the kk-th set bit of om
+          int kk = ee - __shfl_sync(FULL, excl, ow);  // the entry's rank among that lane's pixels
+          // the face among the lane's F faces, then its pixel: the kk-th set bit of its mask
+          unsigned om = 0u;
+          int fi = 0;
+          bool found = false;
+#pragma unroll
+          for (int i = 0; i < FMAX; ++i) {
+            const unsigned mi = __shfl_sync(FULL, lmk[i], ow);
+            const int ci = __popc(mi);
+            if (!found && i < F) {
+              if (kk < ci) {
+                om = mi;
+                fi = i;
+                found = true;
+              } else {
+                kk -= ci;
+              }
+            }
+          }
+          int pb = 0;
           unsigned mm = om;
 #pragma unroll
           for (int w = 16; w > 0; w >>= 1) {
@@ -577,7 +605,7 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
               mm >>= w;
             }
           }
-          const int j = act ? qq * 32 + 31 - ow : 0;
+          const int j = act ? F * (32 - ow) - 1 - fi : 0;
           const int p = act ? pb : lane;
           // -- one entry per lane: face j at pixel lane p ---------------------------------------
           const float4* r4 = reinterpret_cast<const float4*>(rb + j * TS_REC_WORDS);
@@ -687,8 +715,6 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
           }
           __syncwarp();
         }
-        if (--qq < 0) break;
-        lmc = lmrow[(size_t)(qq * 32 + 31 - lane) * NW];  // a full chunk below the last one
       }
     }
   }
