@@ -20,12 +20,13 @@ struct MapArgs {
 };
 
 __global__ void k_setup(TsViewTable tab, int V, MapArgs map, const ts_pose* __restrict__ poses, TsDevHeader* hdr,
-                        TsView* views, ts_pose* ws_poses) {
+                        TsView* views, ts_pose* ws_poses, unsigned long long* ctr) {
   const int t = threadIdx.x;
   for (int v = t; v < V; v += blockDim.x) {
     views[v] = tab.v[v];
     ws_poses[v] = poses[v];
   }
+  for (int i = t; i < TS_N_CTR * TS_CTR_SLOTS; i += blockDim.x) ctr[(size_t)i * TS_CTR_STRIDE] = 0ull;
   if (t == 0) {
     hdr->n_pairs = 0;
     hdr->n_visible = 0;
@@ -60,6 +61,7 @@ struct ProjArgs {
   uint32_t* zbits;
   uint32_t* count;
   TsDevHeader* hdr;
+  unsigned long long* ctr;
 };
 
 __global__ void __launch_bounds__(256, 3) k_project(ProjArgs a, int views_per_block) {
@@ -208,8 +210,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjArgs a, int views_per_bl
         a.count[idx] = 0u;
       }
     }
-    const unsigned ball = __ballot_sync(0xffffffffu, vis);
-    if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&a.hdr->n_visible, (unsigned long long)__popc(ball));
+    ts_count_add(a.ctr, TS_CTR_VISIBLE, vis ? 1u : 0u);
   }
 }
 
@@ -220,7 +221,7 @@ cudaError_t ts_launch_setup(const TsPlanImpl* p, const TsWs& w, const ts_map* ma
   TsViewTable local;  // passed by value: capture-safe, no host-to-device copy
   for (int v = 0; v < p->V; ++v) local.v[v] = p->views[v];
   MapArgs m{map->px, map->py, map->pz, map->cr, map->cg, map->cb, map->op, map->faces, map->n_vertices};
-  k_setup<<<1, 256, 0, s>>>(local, p->V, m, poses, w.hdr, w.views, w.poses);
+  k_setup<<<1, 256, 0, s>>>(local, p->V, m, poses, w.hdr, w.views, w.poses, w.ctr);
   return cudaGetLastError();
 }
 
@@ -250,10 +251,37 @@ cudaError_t ts_launch_project(const TsPlanImpl* p, const TsWs& w, const ts_map* 
   a.zbits = w.zbits;
   a.count = w.count;
   a.hdr = w.hdr;
+  a.ctr = w.ctr;
   // up to 4 views per thread: measured on the 300k-face, 20-view room and the 1M-face, 12-view
   // mapping window against 1, 2 and all views per thread, it is within 0.01 ms of the best of both
   const long long face_blocks = (p->M + 255) / 256;
   const int per = std::min(p->V, 4);
   k_project<<<dim3((unsigned)face_blocks, (unsigned)((p->V + per - 1) / per)), 256, 0, s>>>(a, per);
+  return cudaGetLastError();
+}
+
+// The counters' slots summed into the header (read by ts_sync_status).
+__global__ void __launch_bounds__(256) k_sum_counters(const unsigned long long* __restrict__ ctr, TsDevHeader* hdr) {
+  __shared__ unsigned long long red[TS_N_CTR][256];
+  for (int c = 0; c < TS_N_CTR; ++c) {
+    unsigned long long s = 0;
+    for (int i = threadIdx.x; i < TS_CTR_SLOTS; i += 256) s += ctr[((size_t)c * TS_CTR_SLOTS + i) * TS_CTR_STRIDE];
+    red[c][threadIdx.x] = s;
+  }
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int c = 0; c < TS_N_CTR; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    hdr->n_visible = red[TS_CTR_VISIBLE][0];
+    hdr->fwd_contrib = red[TS_CTR_FWD][0];
+    hdr->bwd_contrib = red[TS_CTR_BWD][0];
+  }
+}
+
+cudaError_t ts_launch_sum_counters(const TsWs& w, cudaStream_t s) {
+  k_sum_counters<<<1, 256, 0, s>>>(w.ctr, w.hdr);
   return cudaGetLastError();
 }

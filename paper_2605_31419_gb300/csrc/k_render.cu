@@ -74,6 +74,7 @@ struct RenderArgs {
   float* dD_out;
   float* tloss;
   TsDevHeader* hdr;
+  unsigned long long* ctr;  // counter slots (contributions)
 };
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -237,10 +238,6 @@ __device__ __forceinline__ void stage_masks(const float* rb, uint16_t* smask, in
   }
 }
 
-__device__ __forceinline__ void count_add(unsigned long long* ctr, unsigned v) {
-  const unsigned s = __reduce_add_sync(FULL, v);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
-}
 
 // Wait for the stage issued last: each thread's copies (they always complete), then a barrier.
 __device__ __forceinline__ void wait_stage() {
@@ -352,7 +349,7 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, fl
       }
     }
   }
-  count_add(&a.hdr->fwd_contrib, contrib);
+  ts_count_add(a.ctr, TS_CTR_FWD, contrib);
   if constexpr (FUSED) {
     carry->T = T;
     carry->C0 = C0;
@@ -718,7 +715,7 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs& a, long long tile, fl
       }
     }
   }
-  count_add(&a.hdr->bwd_contrib, contrib);
+  ts_count_add(a.ctr, TS_CTR_BWD, contrib);
 }
 
 // The fused L1 step of one tile: the forward, the mean-L1 loss of its pixels (Eq. 8 L1 part with
@@ -954,6 +951,7 @@ RenderArgs base_args(const TsPlanImpl* p, const TsWs& w) {
   a.bg2 = p->prm.bg[2];
   a.S = p->prm.tris_per_stage;
   a.hdr = w.hdr;
+  a.ctr = w.ctr;
   a.counter = &w.hdr->tile_counter;
   a.lmask = w.lmask;
   a.aux = w.aux;

@@ -188,6 +188,7 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_aux = take((p->normals || p->face_sigma) ? (size_t)VM * 16 : 0);
   p->o_nloss = take((size_t)n_views * p->n_loss_blocks * 4);
   p->o_cov = take(p->stats ? (size_t)VM * 4 : 0);
+  p->o_ctr = take((size_t)TS_N_CTR * TS_CTR_SLOTS * TS_CTR_STRIDE * 8);
   p->total = o;
   p->magic = TS_PLAN_MAGIC;
   return TS_OK;
@@ -235,6 +236,7 @@ ts_status ts_workspace_init(const ts_plan* plan, void* ws, size_t ws_bytes, ts_s
   // gradient slots of the visible faces)
   cudaError_t e = cudaMemsetAsync((char*)ws + p->o_hdr, 0, sizeof(TsDevHeader), s);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)ws + p->o_tfin, 0, p->o_grad - p->o_tfin, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync((char*)ws + p->o_ctr, 0, (size_t)TS_N_CTR * TS_CTR_SLOTS * TS_CTR_STRIDE * 8, s);
   return cuda_status(e);
 }
 
@@ -417,7 +419,9 @@ ts_status ts_sync_status(const ts_plan* plan, void* ws, ts_stream stream, ts_cou
   const TsPlanImpl* p = impl(plan);
   if (!p || !ws) return TS_ERR_INVALID_ARG;
   TsDevHeader h;
-  cudaError_t e = cudaMemcpyAsync(&h, (char*)ws + p->o_hdr, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  cudaError_t e = ts_launch_sum_counters(ts_ws(p, ws), (cudaStream_t)stream);  // the slots into the header
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h, (char*)ws + p->o_hdr, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return TS_ERR_CUDA;
   if (out) {

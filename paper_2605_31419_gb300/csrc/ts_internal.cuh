@@ -20,6 +20,12 @@
 #define TS_ERRBIT_CAPACITY 1u
 #define TS_ERRBIT_TIMEOUT 2u
 #define TS_ERRBIT_BOUNDS 4u  // an index failed its bounds check (the access was skipped)
+// Device counters (visible records, forward and backward contributions) are kept in TS_CTR_SLOTS
+// slots each, one 32-byte sector apart, chosen by the adding warp, so that the adds of all warps
+// do not queue on one address; ts_sync_status sums the slots.
+#define TS_CTR_SLOTS 1024
+#define TS_CTR_STRIDE 4  // unsigned long long words between slots (32 bytes)
+enum { TS_CTR_VISIBLE = 0, TS_CTR_FWD = 1, TS_CTR_BWD = 2, TS_N_CTR = 3 };
 
 // Record word indices.  u, v: projected vertices (pixels, FP32 as produced by Eq. 1 in the fixed
 // op order); e_i = q_{i+1} - q_i; k_i = s_i / D2 with s_i = perimeter / |e_i| and D2 twice the
@@ -95,7 +101,7 @@ struct TsPlanImpl {
   // workspace layout (byte offsets)
   size_t o_hdr, o_views, o_poses, o_frec, o_rect, o_zbits, o_count, o_tcnt, o_bsums, o_tlarge, o_tmat, o_tloss, o_keys0, o_keys1,
       o_vals0, o_ranges, o_tfin, o_nlast, o_grad, o_pose, o_loss, o_lmask, o_pho, o_equi, o_aux, o_nloss,
-      o_cov, total;
+      o_cov, o_ctr, total;
   void* events[2 * TS_N_STAGES];
   int32_t timing;
   TsView views[TS_MAX_VIEWS];
@@ -131,6 +137,7 @@ struct TsWs {
   float* nloss;  // per (view, 2048-pixel block): partial sums of the normal loss
   uint32_t* cov;  // per (view, face): pixels blended by the forward (TS_FLAG_STATS), else null
   uint32_t* lmask;  // per sorted pair and warp of its tile: the lanes (pixels) that blended the face in the forward
+  unsigned long long* ctr;  // [TS_N_CTR][TS_CTR_SLOTS] counters, TS_CTR_STRIDE words apart
 };
 
 inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
@@ -163,6 +170,7 @@ inline TsWs ts_ws(const TsPlanImpl* p, void* ws) {
   w.nloss = (float*)(b + p->o_nloss);
   w.cov = p->stats ? (uint32_t*)(b + p->o_cov) : nullptr;
   w.lmask = p->fwd_only ? nullptr : (uint32_t*)(b + p->o_lmask);
+  w.ctr = (unsigned long long*)(b + p->o_ctr);
   return w;
 }
 
@@ -217,11 +225,21 @@ cudaError_t ts_launch_timeout_probe(const TsWs& w, unsigned long long limit_ns, 
 int ts_pose_blocks(long long M);                 // blocks of the projection-backward kernel
 // Streaming multiprocessors of the current device (queried once per device; 1 if the query fails).
 int ts_sm_count();
+cudaError_t ts_launch_sum_counters(const TsWs& w, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Device helpers
 // ------------------------------------------------------------------------------------------
 #ifdef __CUDACC__
+
+// Add v (summed over the calling warp) to counter c: one add by lane 0 into the slot of the warp.
+__device__ __forceinline__ void ts_count_add(unsigned long long* ctr, int c, unsigned v) {
+  const unsigned s = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0 && s) {
+    const unsigned slot = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (TS_CTR_SLOTS - 1);
+    atomicAdd(ctr + ((size_t)c * TS_CTR_SLOTS + slot) * TS_CTR_STRIDE, (unsigned long long)s);
+  }
+}
 
 __device__ __forceinline__ int ts_find_view(const TsView* views, int V, long long tile) {
   int lo = 0, hi = V - 1;
