@@ -34,12 +34,10 @@ FLOPS_BWD = 90.0   # per differentiated contribution, backward raster
 # sums (FMA = 2 flops: 220) and their 3 products, SSIM with its 3 partials (~30), the adjoint as 3
 # separable window sums (132), and the gradient and L1 terms (~9)
 FLOPS_PHO = 394.0
-# DRAM bytes (read + write) per view of one k_render_bwd launch of this workload, from the ncu
-# capture in profiles/render_kernels_room_4views_full.md (4 views, tile 16x8, 64 faces per stage),
-# scaled by the views of the launch; reported only for that launch configuration
-BWD_TRAFFIC_PER_VIEW = (188.842752e6 + 23.260928e6) / 4
-# DRAM bytes per view of one k_render_step launch (ncu capture of the 4-view case)
-STEP_TRAFFIC_PER_VIEW = (150.714112e6 + 99.946240e6) / 4
+# DRAM bytes (read + write) per view of one k_render_step launch of this workload, from the
+# one-kernel ncu capture in profiles/k_render_step_room_4views_full.md (4 views, tile 16x8, 64 faces
+# per stage), scaled by the views of the launch; reported only for that launch configuration
+STEP_TRAFFIC_PER_VIEW = (150.826240e6 + 76.013824e6) / 4
 W, H, F, N_FACES, N_VIEWS = 1200, 680, 600.0, 300_000, 20
 WORKLOAD = "room 1200x680 f=600, 300k faces, 20 poses, fwd+bwd (L1 colour+depth), batched"
 
@@ -748,7 +746,7 @@ def main():
             flops = per * contrib
             ach = flops / (stage_ms[dom] / 1e3) / 1e12
             kernel = "k_render_step" if fused else f"k_render_{'bwd' if names[dom] == 'bwd_raster' else 'fwd'}"
-            per_view = {"k_render_step": STEP_TRAFFIC_PER_VIEW, "k_render_bwd": BWD_TRAFFIC_PER_VIEW}.get(kernel)
+            per_view = {"k_render_step": STEP_TRAFFIC_PER_VIEW}.get(kernel)
             traffic = (per_view * sc.n_views if per_view is not None and args.tile == "16x8"
                        and args.stage == 64 else None)
             roof = {"kernel": kernel, "bound": "alu",

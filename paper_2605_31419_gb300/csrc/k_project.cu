@@ -171,9 +171,11 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjArgs a, int views_per_bl
         rec[7] = make_float4(z[2], __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
                              __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)slot));
         if (a.grad) {  // null for a forward-only plan
+          // the raster backward adds into words 0..22, and with the side array (normals, sigma_F)
+          // also into 23, 24, 30, 31; the chain pass writes the rest
           float4* gs = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
-#pragma unroll
-          for (int i = 0; i < TS_GRAD_WORDS / 4; ++i) gs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          const int nz = a.aux ? TS_GRAD_WORDS / 4 : 6;
+          for (int i = 0; i < nz; ++i) gs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const int tx0 = x0 / a.tile_w, tx1 = x1 / a.tile_w, ty0 = y0 / a.tile_h, ty1 = y1 / a.tile_h;
         a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
