@@ -289,3 +289,21 @@ def test_persistent_launch_matches_oracle(name):
     _, _, _, g1, _ = run(name, (16, 8), 64)
     for k in ("color", "depth", "alpha"):
         assert np.array_equal(g[k], g1[k])
+
+
+@pytest.mark.parametrize("name", ["c1", "ragged_room"])
+def test_counters_match_oracle(oracle, name):
+    """The device counters (summed from their slots by ts_sync_status) against the oracle: visible
+    (view, face) records, (tile, face) pairs, and blended contributions of the forward and backward."""
+    from oracle.oracle import SceneArrays
+    sc = random_triangles_scene(seed=1) if name == "c1" else _ragged_room()
+    p, po = params_pair()
+    g = gpu_run(sc, p)
+    c = g["counters"]
+    sa = SceneArrays.of(sc)
+    pr = oracle.project(sa, po)
+    b = oracle.bin(sa, po)
+    st = oracle.face_stats(sa, po)
+    assert c["n_visible"] == int((pr["count"] > 0).sum())
+    assert c["n_pairs"] == len(b["ids"])
+    assert c["fwd_contrib"] == c["bwd_contrib"] == int(st["coverage"].sum()) > 0

@@ -233,3 +233,22 @@ def test_step_full_size_room(oracle):
     assert_grad(s["dpos"], r["dpos"], "dpos")
     assert_grad(s["dcol"], r["dcol"], "dcol")
     assert_grad(s["dopa"], r["dopa"], "dopa")
+
+
+@pytest.mark.parametrize("stage", [32, 128])
+def test_step_stage_sizes(oracle, stage):
+    """32- and 128-face stages (the backward numbers one and four faces per lane): the fused step on
+    long lists that span several stages equals the separate calls and the oracle."""
+    sc = SCENES["long_lists"]()
+    p, po = params_pair(tris_per_stage=stage)
+    s = step_run(sc, p, pair_capacity=1_000_000)
+    g = gpu_run(sc, p, pair_capacity=1_000_000)
+    for k in ("color", "depth", "alpha", "dC", "dD"):
+        assert np.array_equal(s[k], g[k]), k
+    assert s["counters"]["fwd_contrib"] == s["counters"]["bwd_contrib"] == g["counters"]["bwd_contrib"] > 0
+    r = oracle_run(oracle, sc, po)
+    assert_images(s["loss_v"], r["loss_v"], "loss", atol=1e-6, rtol=1e-5)
+    assert_grad(s["dpos"], r["dpos"], "dpos")
+    assert_grad(s["dcol"], r["dcol"], "dcol")
+    assert_grad(s["dopa"], r["dopa"], "dopa")
+    assert_pose_grad(s["dtau"], r["dtau"], r["dtau_abs"])
