@@ -286,13 +286,25 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, fl
         unsigned lm = 0;  // lane L: this warp's pixels that blended face q * 32 + L
         unsigned bits = __ballot_sync(FULL, jq < cnt && ((sm.smask[b][min(jq, cnt - 1)] >> warp) & 1u));
         while (bits) {
-          const int j = q * 32 + __ffs(bits) - 1;
+          const int j0 = q * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          bool blended = false;
-          if (!done) {
-            const float* r = rb + j * TS_REC_WORDS;
-            const TsPix e = ts_eval_edges(r, g.px, g.py);
-            if (e.m > 0.f) {
+          const bool two = bits != 0;
+          const int j1 = two ? q * 32 + __ffs(bits) - 1 : j0;
+          if (two) bits &= bits - 1;
+          // two faces per pass: both edge functions first (independent work the scheduler can overlap),
+          // then the compositing in list order, exactly as one face at a time
+          const float* r0 = rb + j0 * TS_REC_WORDS;
+          const float* r1 = rb + j1 * TS_REC_WORDS;
+          const TsPix e0 = ts_eval_edges(r0, g.px, g.py);
+          const TsPix e1 = ts_eval_edges(r1, g.px, g.py);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            const int j = h ? j1 : j0;
+            const float* r = h ? r1 : r0;
+            const TsPix e = h ? e1 : e0;
+            bool blended = false;
+            if (!done && e.m > 0.f) {
               const float sig = (AUX && a.face_sigma) ? nb[j].w : a.sigma;
               const float I = ts_window(e.m, sig);
               const float al = fminf(r[R_OF] * I, a.alpha_max);
@@ -321,11 +333,11 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs& a, long long tile, fl
                 }
               }
             }
+            // the backward takes exactly these (face, pixel) contributions
+            const unsigned bl = __ballot_sync(FULL, blended);
+            if (lane == (j & 31)) lm = bl;
+            if (bl && lane == 0 && a.cov) atomicAdd(&fm.cv[b][j], (unsigned)__popc(bl));
           }
-          // the backward takes exactly these (face, pixel) contributions
-          const unsigned bl = __ballot_sync(FULL, blended);
-          if (lane == (j & 31)) lm = bl;
-          if (bl && lane == 0 && a.cov) atomicAdd(&fm.cv[b][j], (unsigned)__popc(bl));
         }
         if (a.lmask && jq < cnt) a.lmask[(size_t)(rg.x + (uint32_t)(st * S + jq)) * (TW * TH / 32) + warp] = lm;
       }
