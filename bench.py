@@ -764,8 +764,8 @@ def main():
                     "frac": None, "traffic": None}
         # setup + project, binning (tile counts, scan (3), places, ranges, warp and CTA segment
         # sorts), then either forward, loss (2) and raster backward, or the fused step and its loss
-        # reduction; chain rule + gather, pose reduction
-        launches = 2 + 8 + (1 + 2 + 1 if args.separate else 2) + 2 + 1
+        # reduction; the chain-rule pass, pose reduction
+        launches = 2 + 8 + (1 + 2 + 1 if args.separate else 2) + 1 + 1
         line = {
             "metric": "Mpix/s fwd+bwd raster", "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,

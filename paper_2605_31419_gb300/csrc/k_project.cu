@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjArgs a, int views_per_bl
                              __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)slot));
         if (a.grad) {  // null for a forward-only plan
           // the raster backward adds into words 0..22, and with the side array (normals, sigma_F)
-          // also into 23, 24, 30, 31; the chain pass writes the rest
+          // also into 23, 24, 30, 31; words 25..29 are not used
           float4* gs = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
           const int nz = a.aux ? TS_GRAD_WORDS / 4 : 6;
           for (int i = 0; i < nz; ++i) gs[i] = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -8,21 +8,22 @@
 //   * o_F = (o_i + o_j + o_k) / 3 (Sec. 3.1): each vertex opacity gets a third;
 //   * with TS_FLAG_NORMALS, the face normal of the normal map (Eq. 12) through the cross product
 //     of the camera-space edge vectors; with TS_FLAG_FACE_SIGMA, dL/dsigma_F (a sum the raster
-//     backward already formed) is moved to word 23 and summed over views by the gather;
+//     backward already formed, word 24) is summed over views;
 //   * the pinhole (Eq. 1) to camera space, R^T to world space, and the left-perturbation pose
 //     Jacobian [I, -[v_C]x] (Eq. 7): dL/dtau += [g_C ; v_C x g_C].
 //
 // Gradient slots are face-major (slot = face * V + view) and cleared by the projection pass for
-// the visible ones.  Two passes keep every lane busy and the result deterministic:
-//   A. persistent warps scan the visibility counts, queue the visible slots with ballots, and run
-//      the chain rule on full warps of visible slots, writing each slot's world-space position
-//      gradient (words 0..8) and pose terms (words 24..29) back into it;
-//   B. persistent warps take 4 faces at a time: one ballot round trip gives each face's visible
-//      views, every lane then sums one output word (3 positions x 3 vertices, 3 colours x 3
-//      vertices, the opacity) over those views in view order with up to 8 loads in flight, and
-//      adds it to the map gradient; the lane that owns a view adds the face's pose terms to the
-//      warp's per-view sums in shared memory.  At the end the warps' sums are added in a fixed
-//      order into per-block partials, which a last kernel adds in a fixed order.
+// the visible ones.  One pass, face-major, deterministic: persistent warps take 4 faces at a time.
+// One ballot per face and 32 views gives the face's visible views; the (face, view) entries,
+// numbered face by face with views in order, run the chain rule one per lane (batches of 32), each
+// lane leaving its entry's 20 map words in a shared-memory row.  Lanes 0..20 then each own one
+// output word (3 positions x 3 vertices, 3 colours x 3 vertices, the opacity; lane 21 sigma_F),
+// sum it over the face's rows in view order and add it to the map gradient.  The entry's lane adds
+// its pose terms to the warp's per-view sums in shared memory, face by face, so every view's sum
+// runs in face order.  At the end the warps' sums are added in a fixed order into per-block
+// partials, which a last kernel adds in a fixed order.  Each slot is read once and nothing is
+// written back to it.
+
 #include <algorithm>
 
 #include "ts_internal.cuh"
@@ -51,18 +52,28 @@ __device__ __forceinline__ long long face_vertex(const TsDevHeader* h, long long
   return (j >= 0 && j < h->n_vertices) ? j : 0;
 }
 
-// Pass A body: the chain rule of one visible (view, face).
-__device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) {
+// What the chain rule of one visible (view, face) gives: the world-space vertex-position
+// gradients, the pose terms, and the slot's colour, opacity and sigma_F sums passed through.
+struct SlotTerms {
+  float out[9];  // dL/dp of vertex k, coordinate c at 3k + c
+  float tau[6];  // [g_C ; v_C x g_C] summed over the vertices
+  float gc[9];   // dL/dc of vertex k, channel ch at 3 ch + k (the raster sums)
+  float go;      // dL/do_F
+  float gsig;    // dL/dsigma_F (TS_FLAG_FACE_SIGMA)
+};
+
+// The chain rule of one visible (view, face).
+__device__ __forceinline__ void chain_terms(const PBArgs& a, int v, long long m, SlotTerms& t) {
   const TsDevHeader* h = a.hdr;
   const long long slot = m * a.V + v;
-  float4* gp = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
+  const float4* gp = reinterpret_cast<const float4*>(a.grad + slot * TS_GRAD_WORDS);
   float G[24];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     const float4 q = gp[i];
     G[4 * i] = q.x; G[4 * i + 1] = q.y; G[4 * i + 2] = q.z; G[4 * i + 3] = q.w;
   }
-  const float gsig = a.face_sigma ? gp[6].x : 0.f;  // word 24, before the pose terms overwrite it
+  const float gsig = a.face_sigma ? gp[6].x : 0.f;  // word 24
   const TsView vw = a.views[v];
   const ts_pose P = a.poses[v];
   // The projection, edge vectors, lengths and area are recomputed in the forward record's fixed
@@ -166,8 +177,10 @@ __device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) 
       }
     }
   }
-  float out[9];
-  float tau[6] = {0, 0, 0, 0, 0, 0};
+  float* out = t.out;
+  float* tau = t.tau;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) tau[i] = 0.f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float iz = 1.0f / zc[k];
@@ -183,119 +196,144 @@ __device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) 
     tau[4] += zc[k] * gx - xc[k] * gz;
     tau[5] += xc[k] * gy - yc[k] * gx;
   }
-  // write back: positions into words 0..8 (edge sums, now consumed), pose terms into 24..29
-  float* gs = a.grad + slot * TS_GRAD_WORDS;
-  gp[0] = make_float4(out[0], out[1], out[2], out[3]);
-  gp[1] = make_float4(out[4], out[5], out[6], out[7]);
-  gs[8] = out[8];
-  gp[6] = make_float4(tau[0], tau[1], tau[2], tau[3]);
-  gs[28] = tau[4];
-  gs[29] = tau[5];
-  if (a.face_sigma) gs[23] = gsig;  // (the normal's word 23 is consumed above)
-}
-
-constexpr int PA_T = 256;
-constexpr int PA_WARPS = PA_T / 32;
-
-__global__ void __launch_bounds__(PA_T) k_pbwd_chain(PBArgs a) {
-  __shared__ long long q[PA_WARPS][64];  // queued view-major indices v * M + m
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * PA_WARPS + warp, nw = (long long)gridDim.x * PA_WARPS;
-  const unsigned lt = (1u << lane) - 1u;
-  int qn = 0;
-  for (long long c = gw; c * 32 < a.VM; c += nw) {
-    const long long idx = c * 32 + lane;
-    const bool vis = idx < a.VM && a.count[idx] > 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, vis);
-    if (vis) q[warp][qn + __popc(bal & lt)] = idx;
-    qn += __popc(bal);
-    __syncwarp();
-    if (qn >= 32) {
-      const long long e = q[warp][lane];
-      const int v = (int)(e / a.M);
-      chain_slot(a, v, e - (long long)v * a.M);
-      __syncwarp();
-      if (lane < qn - 32) q[warp][lane] = q[warp][lane + 32];
-      qn -= 32;
-      __syncwarp();
-    }
-  }
-  if (lane < qn) {
-    const long long e = q[warp][lane];
-    const int v = (int)(e / a.M);
-    chain_slot(a, v, e - (long long)v * a.M);
-  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) t.gc[i] = G[G_C + i];
+  t.go = G[G_O];
+  t.gsig = gsig;
 }
 
 constexpr int PG_WARPS = 4;
 constexpr int PG_T = 32 * PG_WARPS;
-constexpr int PG_F = 4;  // faces per warp iteration
+constexpr int PG_F = 4;    // faces per warp iteration
+constexpr int PG_RS = 21;  // floats per entry row (out 9, colour 9, opacity, sigma; odd: no bank conflicts)
+constexpr int PG_RMAX = (TS_MAX_VIEWS + 31) / 32;
 
-__global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
-  extern __shared__ float pv[];  // [PG_WARPS][V][8] per-warp per-view pose sums
+// Shared memory of one block: per-warp per-view pose sums, per-warp entry rows, per-warp view masks.
+size_t pbwd_smem(int V) {
+  return (size_t)PG_WARPS * V * 8 * sizeof(float) + (size_t)PG_WARPS * 32 * PG_RS * sizeof(float) +
+         (size_t)PG_WARPS * PG_F * PG_RMAX * sizeof(uint32_t);
+}
+
+__global__ void __launch_bounds__(PG_T) k_pbwd_face(PBArgs a) {
+  extern __shared__ float pv[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TsDevHeader* h = a.hdr;
-  float* my = pv + (size_t)warp * a.V * 8;
+  float* my = pv + (size_t)warp * a.V * 8;  // this warp's pose sums [V][8]
+  float* rows = pv + (size_t)PG_WARPS * a.V * 8 + (size_t)warp * 32 * PG_RS;
+  uint32_t* vm = reinterpret_cast<uint32_t*>(pv + (size_t)PG_WARPS * a.V * 8 + (size_t)PG_WARPS * 32 * PG_RS) +
+                 warp * PG_F * PG_RMAX;  // [f][r]: the face's visible views r * 32 + bit
   for (int i = lane; i < a.V * 8; i += 32) my[i] = 0.f;
   __syncwarp();
   // lanes 0..20 each own one output word: array c (gpx..gop), vertex k; with per-face sigma,
-  // lane 21 owns the face's dL/dsigma_F (word 23 after the chain pass)
+  // lane 21 owns the face's dL/dsigma_F
   const int c = lane / 3, k = lane - 3 * (lane / 3);
   const bool face_word = lane == 21;
   const bool owner = lane < 21 || (face_word && a.face_sigma);
-  const int word = c < 3 ? G_DPOS + 3 * k + c : (c < 6 ? G_C + 3 * (c - 3) + k : (c == 6 ? G_O : 23));
+  const int ridx = c < 3 ? 3 * k + c : (c < 6 ? 9 + 3 * (c - 3) + k : (c == 6 ? 18 : 19));
   const float mean_scale = c == 6 ? (1.0f / 3.0f) : 1.0f;
   float* dst = owner ? (face_word ? a.dst_sigma : a.dst[c]) : nullptr;
   const bool indexed = h->faces != nullptr;
+  const int R = (a.V + 31) >> 5;
   const long long stride = (long long)gridDim.x * PG_WARPS * PG_F;
   for (long long m0 = ((long long)blockIdx.x * PG_WARPS + warp) * PG_F; m0 < a.M; m0 += stride) {
     long long j[PG_F];
     float old[PG_F], s[PG_F];
+    int nf[PG_F];
 #pragma unroll
     for (int f = 0; f < PG_F; ++f) {
       const long long m = m0 + f;
       j[f] = (m < a.M && dst) ? (face_word ? m : face_vertex(h, m, k)) : 0;
       old[f] = (m < a.M && dst && (!indexed || face_word)) ? dst[j[f]] : 0.f;  // issued early
       s[f] = 0.f;
+      nf[f] = 0;
     }
-    for (int r = 0; r * 32 < a.V; ++r) {
+    // the faces' visible views, 32 at a time
+    for (int r = 0; r < R; ++r) {
       const int vl = r * 32 + lane;
-      unsigned msk[PG_F];
+      uint32_t cnt[PG_F];
 #pragma unroll
       for (int f = 0; f < PG_F; ++f) {
         const long long m = m0 + f;
-        const uint32_t cnt = (m < a.M && vl < a.V) ? a.count[(long long)vl * a.M + m] : 0u;
-        msk[f] = __ballot_sync(0xffffffffu, cnt > 0);
+        cnt[f] = (m < a.M && vl < a.V) ? a.count[(long long)vl * a.M + m] : 0u;
       }
-      // pose terms: the lane owning view vl adds each face's terms to the warp's sums (face order)
 #pragma unroll
       for (int f = 0; f < PG_F; ++f) {
-        if ((msk[f] >> lane) & 1u) {
-          const float* t = a.grad + ((m0 + f) * a.V + vl) * TS_GRAD_WORDS + G_TAU;
-#pragma unroll
-          for (int i = 0; i < 6; ++i) my[vl * 8 + i] += t[i];
-        }
+        const unsigned msk = __ballot_sync(0xffffffffu, cnt[f] > 0);
+        if (lane == 0) vm[f * PG_RMAX + r] = msk;
+        nf[f] += __popc(msk);
       }
-      // output words: sum over the visible views in view order, up to 8 loads in flight
+    }
+    __syncwarp();
+    int total = 0, st[PG_F];
+#pragma unroll
+    for (int f = 0; f < PG_F; ++f) {
+      st[f] = total;
+      total += nf[f];
+    }
+    // the (face, view) entries, face by face and views in order, one per lane
+    for (int b0 = 0; b0 < total; b0 += 32) {
+      const int ee = b0 + lane;
+      const bool act = ee < total;
+      int fe = 0, kk = ee;
+      bool found = false;
 #pragma unroll
       for (int f = 0; f < PG_F; ++f) {
-        unsigned bits = msk[f];
-        const float* base = a.grad + (m0 + f) * a.V * TS_GRAD_WORDS + word;
-        while (bits) {
-          float vals[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            vals[u] = 0.f;
-            if (bits) {
-              const int v = r * 32 + __ffs(bits) - 1;
-              bits &= bits - 1;
-              if (dst) vals[u] = base[(long long)v * TS_GRAD_WORDS];  // only for a requested output
-            }
+        if (!found) {
+          if (kk < nf[f]) {
+            fe = f;
+            found = true;
+          } else {
+            kk -= nf[f];
           }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) s[f] += vals[u];
         }
       }
+      int v = 0;
+      SlotTerms t;
+      if (act) {
+        int r = 0;
+        uint32_t mr = vm[fe * PG_RMAX];
+        while (kk >= __popc(mr)) {  // the entry is in a later round of the face's views
+          kk -= __popc(mr);
+          mr = vm[fe * PG_RMAX + ++r];
+        }
+        int pb = 0;
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) {  // the kk-th set bit of mr
+          const int cl = __popc(mr & ((1u << w) - 1u));
+          if (kk >= cl) {
+            kk -= cl;
+            pb += w;
+            mr >>= w;
+          }
+        }
+        v = r * 32 + pb;
+        chain_terms(a, v, m0 + fe, t);
+        float* row = rows + lane * PG_RS;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) row[i] = t.out[i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) row[9 + i] = t.gc[i];
+        row[18] = t.go;
+        row[19] = t.gsig;
+      }
+      // pose terms: face by face (a face's views are distinct), so each view's sum runs in face order
+#pragma unroll
+      for (int f = 0; f < PG_F; ++f) {
+        if (act && fe == f) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) my[v * 8 + i] += t.tau[i];
+        }
+        __syncwarp();
+      }
+      // output words: each face's entries of this batch, views in order
+      if (dst) {
+#pragma unroll
+        for (int f = 0; f < PG_F; ++f) {
+          const int lo = max(st[f] - b0, 0), hi = min(st[f] + nf[f] - b0, 32);
+          for (int e = lo; e < hi; ++e) s[f] += rows[e * PG_RS + ridx];
+        }
+      }
+      __syncwarp();  // every lane has read the rows before the next batch writes them
     }
 #pragma unroll
     for (int f = 0; f < PG_F; ++f) {
@@ -347,7 +385,7 @@ __global__ void __launch_bounds__(256) k_pose_reduce(const float* __restrict__ p
 
 }  // namespace
 
-// The gather's block count fixes the partial-sum layout of the pose gradient and so its summation
+// The chain-rule pass's block count fixes the partial-sum layout of the pose gradient and so its summation
 // order: a constant cap (not the device's SM count) keeps dtau's rounding the same on every GPU.
 constexpr long long POSE_BLOCKS_MAX = 2432;
 int ts_pose_blocks(long long M) {
@@ -378,11 +416,7 @@ cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_m
   a.min_opacity = p->min_opacity;
   a.part = w.pose;
   a.nblocks = (int)p->n_pose_blocks;
-  const long long chunks = (a.VM + 31) / 32;
-  const long long grid_a = std::min<long long>((chunks + PA_WARPS - 1) / PA_WARPS, (long long)ts_sm_count() * 8);
-  k_pbwd_chain<<<(unsigned)grid_a, PA_T, 0, s>>>(a);
-  const size_t smem = (size_t)PG_WARPS * p->V * 8 * sizeof(float);  // <= 32 KiB for 256 views
-  k_pbwd_gather<<<(unsigned)p->n_pose_blocks, PG_T, smem, s>>>(a);
+  k_pbwd_face<<<(unsigned)p->n_pose_blocks, PG_T, pbwd_smem(p->V), s>>>(a);  // < 44 KiB for 256 views
   return cudaGetLastError();
 }
 
