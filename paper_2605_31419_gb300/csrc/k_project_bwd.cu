@@ -13,16 +13,21 @@
 //     Jacobian [I, -[v_C]x] (Eq. 7): dL/dtau += [g_C ; v_C x g_C].
 //
 // Gradient slots are face-major (slot = face * V + view) and cleared by the projection pass for
-// the visible ones.  One pass, face-major, deterministic: persistent warps take 4 faces at a time.
-// One ballot per face and 32 views gives the face's visible views; the (face, view) entries,
-// numbered face by face with views in order, run the chain rule one per lane (batches of 32), each
-// lane leaving its entry's 20 map words in a shared-memory row.  Lanes 0..20 then each own one
-// output word (3 positions x 3 vertices, 3 colours x 3 vertices, the opacity; lane 21 sigma_F),
-// sum it over the face's rows in view order and add it to the map gradient.  The entry's lane adds
-// its pose terms to the warp's per-view sums in shared memory, face by face, so every view's sum
-// runs in face order.  At the end the warps' sums are added in a fixed order into per-block
-// partials, which a last kernel adds in a fixed order.  Each slot is read once and nothing is
-// written back to it.
+// the visible ones.  Persistent warps take 4 faces at a time; one ballot per face and 32 views
+// gives the face's visible views.  Lanes 0..20 each own one output word (3 positions x 3 vertices,
+// 3 colours x 3 vertices, the opacity; lane 21 sigma_F), sum it over the face's visible views in
+// view order and add it to the map gradient.  Each view's pose terms are added to the warp's
+// per-view sums in shared memory in face order; at the end the warps' sums are added in a fixed
+// order into per-block partials, which a last kernel adds in a fixed order.  Two forms, with the
+// same arithmetic and the same summation orders (so the same results):
+//   * one pass (8 or more views): the 4 faces' (face, view) entries, numbered face by face with
+//     views in order, run the chain rule one per lane (batches of 32), each lane leaving its
+//     entry's 20 map words in a shared-memory row that the word lanes sum; each slot is read
+//     once and nothing is written back;
+//   * two passes (fewer views, where 4 faces fill few lanes): A. persistent warps scan the
+//     visibility counts, queue the visible slots with ballots and run the chain rule on full warps,
+//     writing each slot's results back into it; B. the word lanes sum the written-back words,
+//     with up to 8 loads in flight.
 
 #include <algorithm>
 
@@ -202,11 +207,61 @@ __device__ __forceinline__ void chain_terms(const PBArgs& a, int v, long long m,
   t.gsig = gsig;
 }
 
+// Two-pass form, pass A: the chain rule of one visible (view, face), written back into its slot:
+// positions into words 0..8 (the edge sums, now consumed), pose terms into 24..29, sigma_F into 23.
+__device__ __forceinline__ void chain_slot(const PBArgs& a, int v, long long m) {
+  SlotTerms t;
+  chain_terms(a, v, m, t);
+  float* gs = a.grad + (m * a.V + v) * TS_GRAD_WORDS;
+  float4* gp = reinterpret_cast<float4*>(gs);
+  gp[0] = make_float4(t.out[0], t.out[1], t.out[2], t.out[3]);
+  gp[1] = make_float4(t.out[4], t.out[5], t.out[6], t.out[7]);
+  gs[8] = t.out[8];
+  gp[6] = make_float4(t.tau[0], t.tau[1], t.tau[2], t.tau[3]);
+  gs[28] = t.tau[4];
+  gs[29] = t.tau[5];
+  if (a.face_sigma) gs[23] = t.gsig;
+}
+
+constexpr int PA_T = 256;
+constexpr int PA_WARPS = PA_T / 32;
+
+__global__ void __launch_bounds__(PA_T) k_pbwd_chain(PBArgs a) {
+  __shared__ long long q[PA_WARPS][64];  // queued view-major indices v * M + m
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * PA_WARPS + warp, nw = (long long)gridDim.x * PA_WARPS;
+  const unsigned lt = (1u << lane) - 1u;
+  int qn = 0;
+  for (long long c = gw; c * 32 < a.VM; c += nw) {
+    const long long idx = c * 32 + lane;
+    const bool vis = idx < a.VM && a.count[idx] > 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, vis);
+    if (vis) q[warp][qn + __popc(bal & lt)] = idx;
+    qn += __popc(bal);
+    __syncwarp();
+    if (qn >= 32) {
+      const long long e = q[warp][lane];
+      const int v = (int)(e / a.M);
+      chain_slot(a, v, e - (long long)v * a.M);
+      __syncwarp();
+      if (lane < qn - 32) q[warp][lane] = q[warp][lane + 32];
+      qn -= 32;
+      __syncwarp();
+    }
+  }
+  if (lane < qn) {
+    const long long e = q[warp][lane];
+    const int v = (int)(e / a.M);
+    chain_slot(a, v, e - (long long)v * a.M);
+  }
+}
+
 constexpr int PG_WARPS = 4;
 constexpr int PG_T = 32 * PG_WARPS;
 constexpr int PG_F = 4;    // faces per warp iteration
 constexpr int PG_RS = 21;  // floats per entry row (out 9, colour 9, opacity, sigma; odd: no bank conflicts)
 constexpr int PG_RMAX = (TS_MAX_VIEWS + 31) / 32;
+constexpr int PBWD_ONE_PASS_VIEWS = 8;  // from here on the one-pass form is faster (room scene, 300k faces)
 
 // Shared memory of one block: per-warp per-view pose sums, per-warp entry rows, per-warp view masks.
 size_t pbwd_smem(int V) {
@@ -214,6 +269,100 @@ size_t pbwd_smem(int V) {
          (size_t)PG_WARPS * PG_F * PG_RMAX * sizeof(uint32_t);
 }
 
+// Two-pass form, pass B.
+__global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
+  extern __shared__ float pv[];  // [PG_WARPS][V][8] per-warp per-view pose sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const TsDevHeader* h = a.hdr;
+  float* my = pv + (size_t)warp * a.V * 8;
+  for (int i = lane; i < a.V * 8; i += 32) my[i] = 0.f;
+  __syncwarp();
+  // lanes 0..20 each own one output word: array c (gpx..gop), vertex k; with per-face sigma,
+  // lane 21 owns the face's dL/dsigma_F (word 23 after the chain pass)
+  const int c = lane / 3, k = lane - 3 * (lane / 3);
+  const bool face_word = lane == 21;
+  const bool owner = lane < 21 || (face_word && a.face_sigma);
+  const int word = c < 3 ? G_DPOS + 3 * k + c : (c < 6 ? G_C + 3 * (c - 3) + k : (c == 6 ? G_O : 23));
+  const float mean_scale = c == 6 ? (1.0f / 3.0f) : 1.0f;
+  float* dst = owner ? (face_word ? a.dst_sigma : a.dst[c]) : nullptr;
+  const bool indexed = h->faces != nullptr;
+  const long long stride = (long long)gridDim.x * PG_WARPS * PG_F;
+  for (long long m0 = ((long long)blockIdx.x * PG_WARPS + warp) * PG_F; m0 < a.M; m0 += stride) {
+    long long j[PG_F];
+    float old[PG_F], s[PG_F];
+#pragma unroll
+    for (int f = 0; f < PG_F; ++f) {
+      const long long m = m0 + f;
+      j[f] = (m < a.M && dst) ? (face_word ? m : face_vertex(h, m, k)) : 0;
+      old[f] = (m < a.M && dst && (!indexed || face_word)) ? dst[j[f]] : 0.f;  // issued early
+      s[f] = 0.f;
+    }
+    for (int r = 0; r * 32 < a.V; ++r) {
+      const int vl = r * 32 + lane;
+      unsigned msk[PG_F];
+#pragma unroll
+      for (int f = 0; f < PG_F; ++f) {
+        const long long m = m0 + f;
+        const uint32_t cnt = (m < a.M && vl < a.V) ? a.count[(long long)vl * a.M + m] : 0u;
+        msk[f] = __ballot_sync(0xffffffffu, cnt > 0);
+      }
+      // pose terms: the lane owning view vl adds each face's terms to the warp's sums (face order)
+#pragma unroll
+      for (int f = 0; f < PG_F; ++f) {
+        if ((msk[f] >> lane) & 1u) {
+          const float* t = a.grad + ((m0 + f) * a.V + vl) * TS_GRAD_WORDS + G_TAU;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) my[vl * 8 + i] += t[i];
+        }
+      }
+      // output words: sum over the visible views in view order, up to 8 loads in flight
+#pragma unroll
+      for (int f = 0; f < PG_F; ++f) {
+        unsigned bits = msk[f];
+        const float* base = a.grad + (m0 + f) * a.V * TS_GRAD_WORDS + word;
+        while (bits) {
+          float vals[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            vals[u] = 0.f;
+            if (bits) {
+              const int v = r * 32 + __ffs(bits) - 1;
+              bits &= bits - 1;
+              if (dst) vals[u] = base[(long long)v * TS_GRAD_WORDS];  // only for a requested output
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s[f] += vals[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < PG_F; ++f) {
+      if (m0 + f < a.M && dst) {
+        float scale = mean_scale;
+        if (c == 6 && a.min_opacity) {  // the first vertex, in face order, attaining the minimum
+          const long long m = m0 + f;
+          const float o0 = __ldg(h->op + face_vertex(h, m, 0)), o1 = __ldg(h->op + face_vertex(h, m, 1));
+          const float o2 = __ldg(h->op + face_vertex(h, m, 2));
+          const int km = (o0 <= o1 && o0 <= o2) ? 0 : (o1 <= o2 ? 1 : 2);
+          scale = k == km ? 1.0f : 0.0f;
+        }
+        if (indexed && !face_word) atomicAdd(dst + j[f], s[f] * scale);
+        else dst[j[f]] = old[f] + s[f] * scale;
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < a.V * 6; t += PG_T) {
+    const int v = t / 6, i = t - 6 * (t / 6);
+    float sum = 0.f;
+#pragma unroll
+    for (int w = 0; w < PG_WARPS; ++w) sum += pv[((size_t)w * a.V + v) * 8 + i];
+    a.part[((long long)v * a.nblocks + blockIdx.x) * 6 + i] = sum;
+  }
+}
+
+// One-pass form.
 __global__ void __launch_bounds__(PG_T) k_pbwd_face(PBArgs a) {
   extern __shared__ float pv[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -416,7 +565,14 @@ cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_m
   a.min_opacity = p->min_opacity;
   a.part = w.pose;
   a.nblocks = (int)p->n_pose_blocks;
-  k_pbwd_face<<<(unsigned)p->n_pose_blocks, PG_T, pbwd_smem(p->V), s>>>(a);  // < 44 KiB for 256 views
+  if (p->V >= PBWD_ONE_PASS_VIEWS) {
+    k_pbwd_face<<<(unsigned)p->n_pose_blocks, PG_T, pbwd_smem(p->V), s>>>(a);  // < 44 KiB for 256 views
+  } else {
+    const long long chunks = (a.VM + 31) / 32;
+    const long long grid_a = std::min<long long>((chunks + PA_WARPS - 1) / PA_WARPS, (long long)ts_sm_count() * 8);
+    k_pbwd_chain<<<(unsigned)grid_a, PA_T, 0, s>>>(a);
+    k_pbwd_gather<<<(unsigned)p->n_pose_blocks, PG_T, (size_t)PG_WARPS * p->V * 8 * sizeof(float), s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -21,11 +21,15 @@ def params_pair(**kw):
     return p, o
 
 
-def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, dN=None, lambda_dep=0.05, pair_capacity=0):
+def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, dN=None, lambda_dep=0.05, pair_capacity=0,
+            expect_error=False):
     """Forward (and backward of the L1 loss, or of the given image gradients) on the GPU.  With
-    TS_FLAG_NORMALS in p.flags the normal map is returned and dN (if given) joins the backward."""
+    TS_FLAG_NORMALS in p.flags the normal map is returned and dN (if given) joins the backward.
+    pair_capacity 0 takes the scene's own ``pair_capacity`` if it has one, else the plan default.
+    A run that latched a device error (a dropped pair, a timed-out wait) fails unless expect_error."""
     import torch
     import paper_2605_31419_gb300 as ts
+    pair_capacity = pair_capacity or getattr(scene, "pair_capacity", 0)
     rast = ts.Rasterizer(scene.cams, scene.n_faces, p, pair_capacity=pair_capacity)
     m = ts.Map.from_numpy(scene.pos, scene.col, scene.opa, scene.faces, sigma=getattr(scene, "sigma", None))
     poses = ts.poses_tensor(scene.poses)
@@ -61,6 +65,8 @@ def gpu_run(scene, p, *, backward=True, dC=None, dD=None, dA=None, dN=None, lamb
         if g.sigma is not None:
             out["dsigma"] = g.sigma.cpu().numpy().astype(np.float64)
         out["counters"] = rast.counters(raise_on_error=False)
+    if not expect_error:
+        assert out["counters"]["error_bits"] == 0, f"device error latched: {out['counters']}"
     out["rast"] = rast
     return out
 

@@ -16,8 +16,9 @@ pytestmark = pytest.mark.gpu
 
 
 def _scenes():
-    from test_gpu_parity import _indexed, _ragged_room
-    return {"c1": lambda: random_triangles_scene(seed=1), "ragged_room": _ragged_room, "indexed": _indexed}
+    from test_gpu_parity import _indexed, _indexed_9v, _ragged_room, _room_10v
+    return {"c1": lambda: random_triangles_scene(seed=1), "ragged_room": _ragged_room, "indexed": _indexed,
+            "room_10v": _room_10v, "indexed_9v": _indexed_9v}
 
 
 def _params(**kw):
@@ -25,7 +26,7 @@ def _params(**kw):
     return params_pair(flags=ts.TS_FLAG_NORMALS, **kw)
 
 
-@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed"])
+@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed", "room_10v", "indexed_9v"])
 def test_normal_map_matches_oracle(oracle, name):
     sc = _scenes()[name]()
     p, po = _params()
@@ -46,7 +47,7 @@ def test_normal_map_matches_oracle(oracle, name):
         assert np.array_equal(g[k], g0[k]), k
 
 
-@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed"])
+@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed", "room_10v", "indexed_9v"])
 def test_backward_with_normal_gradient(oracle, name):
     sc = _scenes()[name]()
     p, po = _params()

@@ -29,7 +29,33 @@ def _indexed():
     return sc
 
 
-SCENES = {"c1": lambda: random_triangles_scene(seed=1), "ragged_room": _ragged_room, "indexed": _indexed}
+def _room_10v():
+    # ten views: the chain rule takes its one-pass form from 8 views on
+    return room_scene(5, 20000, 10, 100, 75, 70.0, target_seed=6)
+
+
+def _indexed_9v():
+    # a regular shared-vertex strip (faces (m, m+1, m+2), 10 x 20 px, inradius ~3.6 px) seen from
+    # nine camera positions: the one-pass chain rule with atomic adds over shared vertices
+    rng = np.random.default_rng(39)
+    k = np.arange(42)
+    pos = np.stack([-2.0 + 0.1 * k, np.where(k % 2 == 0, -0.2, 0.2), 2.0 + 0.05 * np.sin(0.7 * k)], 1)
+    col = rng.uniform(0.1, 0.9, size=(42, 3))
+    opa = rng.uniform(0.3, 0.9, size=42)
+    faces = np.stack([k[:40], k[:40] + 1, k[:40] + 2], 1)
+    n = 9
+    poses = np.tile(np.array([[1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0]], np.float64), (n, 1))
+    poses[:, 9] = np.linspace(-0.3, 0.3, n)
+    poses[:, 10] = np.linspace(0.05, -0.05, n)
+    cams = np.tile(np.array([[100.0, 100.0, 40.0, 30.0, 80, 60]]), (n, 1))
+    out = Scene(pos.astype(np.float32), col.astype(np.float32), opa.astype(np.float32), faces.astype(np.int32),
+                cams, poses)
+    out.tgt_color, out.tgt_depth = noise_targets(38, cams)
+    return out
+
+
+SCENES = {"c1": lambda: random_triangles_scene(seed=1), "ragged_room": _ragged_room, "indexed": _indexed,
+          "room_10v": _room_10v, "indexed_9v": _indexed_9v}
 TILES = [(16, 8), (16, 16), (8, 8), (32, 8), (16, 32)]
 _cache = {}
 
@@ -211,7 +237,7 @@ def test_capacity_overflow_is_reported():
     import paper_2605_31419_gb300 as ts
     sc = random_triangles_scene(seed=1)
     p, _ = params_pair()
-    g = gpu_run(sc, p, backward=False, pair_capacity=1024)
+    g = gpu_run(sc, p, backward=False, pair_capacity=1024, expect_error=True)
     assert g["counters"]["status"] == "TS_ERR_CAPACITY"
     assert g["counters"]["n_pairs"] > 1024
     with pytest.raises(ts.TsError):

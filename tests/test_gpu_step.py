@@ -43,6 +43,7 @@ SCENES = {
 def step_run(sc, p, lambda_dep=0.05, pair_capacity=0):
     import torch
     import paper_2605_31419_gb300 as ts
+    pair_capacity = pair_capacity or getattr(sc, "pair_capacity", 0)
     rast = ts.Rasterizer(sc.cams, sc.n_faces, p, pair_capacity=pair_capacity)
     m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa, sc.faces)
     poses = ts.poses_tensor(sc.poses)
@@ -58,7 +59,7 @@ def step_run(sc, p, lambda_dep=0.05, pair_capacity=0):
     f = lambda t: t.cpu().numpy().astype(np.float64)  # noqa: E731
     return dict(color=f(rast.color), depth=f(rast.depth), alpha=f(rast.alpha), loss_v=f(loss), dC=f(rast.dC),
                 dD=f(rast.dD), dpos=f(g.pos).T, dcol=f(g.col).T, dopa=f(g.opa), dtau=f(dtau),
-                counters=rast.counters(raise_on_error=False))
+                counters=rast.counters())  # raises on a latched device error
 
 
 @pytest.mark.parametrize("name", list(SCENES))

@@ -12,11 +12,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _scenes():
-    from test_gpu_parity import _indexed, _ragged_room
-    return {"c1": lambda: random_triangles_scene(seed=1), "ragged_room": _ragged_room, "indexed": _indexed}
+    from test_gpu_parity import _indexed, _indexed_9v, _ragged_room, _room_10v
+    return {"c1": lambda: random_triangles_scene(seed=1), "ragged_room": _ragged_room, "indexed": _indexed,
+            "room_10v": _room_10v, "indexed_9v": _indexed_9v}
 
 
-@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed"])
+@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed", "room_10v", "indexed_9v"])
 def test_min_opacity_variant(oracle, name):
     import paper_2605_31419_gb300 as ts
     sc = _scenes()[name]()
@@ -41,7 +42,7 @@ def test_min_opacity_variant(oracle, name):
         assert nz.max() <= 1
 
 
-@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed"])
+@pytest.mark.parametrize("name", ["c1", "ragged_room", "indexed", "room_10v", "indexed_9v"])
 def test_face_sigma_variant(oracle, name):
     """Per-face window exponents sigma_F ~ U[0.5, 1.5] (float32), with dL/dsigma_F."""
     import paper_2605_31419_gb300 as ts
