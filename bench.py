@@ -34,10 +34,10 @@ FLOPS_BWD = 90.0   # per differentiated contribution, backward raster
 # sums (FMA = 2 flops: 220) and their 3 products, SSIM with its 3 partials (~30), the adjoint as 3
 # separable window sums (132), and the gradient and L1 terms (~9)
 FLOPS_PHO = 394.0
-# DRAM bytes (read + write) per view of one k_render_step launch of this workload, from the
-# one-kernel ncu capture in profiles/k_render_step_room_4views_full.md (4 views, tile 16x8, 64 faces
-# per stage), scaled by the views of the launch; reported only for that launch configuration
-STEP_TRAFFIC_PER_VIEW = (150.826240e6 + 76.013824e6) / 4
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per view of one k_render_step launch of
+# this workload, from a one-kernel, one-launch ncu capture of the same step cut to 4 views (tile
+# 16x8, 64 faces per stage), scaled by the views of the launch; reported only for that configuration
+STEP_TRAFFIC_PER_VIEW = (150.714112e6 + 77.189632e6) / 4
 W, H, F, N_FACES, N_VIEWS = 1200, 680, 600.0, 300_000, 20
 WORKLOAD = "room 1200x680 f=600, 300k faces, 20 poses, fwd+bwd (L1 colour+depth), batched"
 

@@ -76,10 +76,13 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t* __restri
   if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the block sums in place (one block); writes the grand total.
+// Exclusive scan of the block sums in place (one block); writes the grand total, and zeroes
+// *zero_out (the sort's count of long lists) for the launches that follow.
 __global__ void __launch_bounds__(SCAN_T) k_scan_bsums(uint32_t* bsums, Len len, unsigned long long* total_out,
-                                                       unsigned int* err, long long cap) {
+                                                       unsigned int* err, long long cap, unsigned int* zero_out) {
   __shared__ uint32_t sm[33];
+  __shared__ unsigned long long wsum[SCAN_T / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long n = len.get();
   const long long nb = (n + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS;
   const long long per = (nb + SCAN_T - 1) / SCAN_T;
@@ -88,20 +91,26 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_bsums(uint32_t* bsums, Len len,
   for (long long i = b0; i < b0 + per && i < nb; ++i) s += bsums[i];
   uint32_t tot;
   uint32_t run = block_excl_scan((uint32_t)s, sm, &tot);
-  // the 64-bit total guards against overflow of the 32-bit running offsets
-  __shared__ unsigned long long tot64;
-  if (threadIdx.x == 0) tot64 = 0;
-  __syncthreads();
-  atomicAdd(&tot64, s);
-  __syncthreads();
+  // the 64-bit total guards against overflow of the 32-bit running offsets: a warp reduction,
+  // then the warps' sums in order
+  unsigned long long ws = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+  if (lane == 0) wsum[warp] = ws;
   for (long long i = b0; i < b0 + per && i < nb; ++i) {
     const uint32_t v = bsums[i];
     bsums[i] = run;
     run += v;
   }
-  if (threadIdx.x == 0 && total_out) {
-    *total_out = tot64;
-    if ((long long)tot64 > cap) atomicOr(err, TS_ERRBIT_CAPACITY);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot64 = 0;
+    for (int w = 0; w < SCAN_T / 32; ++w) tot64 += wsum[w];
+    if (total_out) {
+      *total_out = tot64;
+      if ((long long)tot64 > cap) atomicOr(err, TS_ERRBIT_CAPACITY);
+    }
+    if (zero_out) *zero_out = 0u;
   }
 }
 
@@ -478,10 +487,13 @@ __global__ void __launch_bounds__(LARGE_T) k_tile_sort_large(SortOut o, unsigned
 
 cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
   const long long VM = (long long)p->V * p->M;
-  cudaError_t e = cudaMemsetAsync(w.ranges, 0, (size_t)p->n_tiles * sizeof(uint2), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->n_large, 0, sizeof(unsigned int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->n_pairs, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess || VM == 0) return e;
+  cudaError_t e = cudaSuccess;
+  if (VM == 0) {  // no records: empty ranges and no pairs (otherwise the kernels below write them)
+    e = cudaMemsetAsync(w.ranges, 0, (size_t)p->n_tiles * sizeof(uint2), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->n_large, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->n_pairs, 0, sizeof(unsigned long long), s);
+    return e;
+  }
   if (p->bin_blocks > 0) {
     // 1-3 with shared-memory counts: counts, their scan (the total is the pair count; above the
     // capacity latches its bit), places, ranges
@@ -496,7 +508,7 @@ cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
     Len lm{p->n_tiles * p->bin_blocks};
     const unsigned nb = (unsigned)((lm.n + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
     k_scan_reduce<<<nb, SCAN_T, 0, s>>>(w.tmat, lm, w.bsums);
-    k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.bsums, lm, &w.hdr->n_pairs, &w.hdr->error_bits, p->cap);
+    k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.bsums, lm, &w.hdr->n_pairs, &w.hdr->error_bits, p->cap, &w.hdr->n_large);
     k_scan_apply<<<nb, SCAN_T, 0, s>>>(w.tmat, lm, w.bsums);
     k_bin_place<<<grid, BIN_T, smem, s>>>(ma);
     k_bin_ranges<<<(unsigned)((p->n_tiles + 255) / 256), 256, 0, s>>>(ma);
@@ -511,7 +523,7 @@ cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
     Len lt{p->n_tiles};
     const unsigned nb = (unsigned)((p->n_tiles + TS_SCAN_ITEMS - 1) / TS_SCAN_ITEMS);
     k_scan_reduce<<<nb, SCAN_T, 0, s>>>(w.tcnt, lt, w.bsums);
-    k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.bsums, lt, &w.hdr->n_pairs, &w.hdr->error_bits, p->cap);
+    k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.bsums, lt, &w.hdr->n_pairs, &w.hdr->error_bits, p->cap, &w.hdr->n_large);
     k_tile_starts<<<nb, SCAN_T, 0, s>>>(ta, w.bsums);
     k_tile_scatter<<<nf, 256, 0, s>>>(ta);
   }
