@@ -762,10 +762,11 @@ def main():
         else:
             roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": None}
-        # setup + project, binning (tile counts, scan (3), places, ranges, warp and CTA segment
-        # sorts), then either forward, loss (2) and raster backward, or the fused step and its loss
-        # reduction; the chain-rule pass, pose reduction
-        launches = 2 + 8 + (1 + 2 + 1 if args.separate else 2) + 1 + 1
+        # setup + project, binning (tile counts, scan (3), places, warp and CTA segment sorts, the
+        # warp sort also writing the ranges), then either forward, loss (2) and raster backward, or
+        # the fused step and its loss reduction; the chain-rule pass (one kernel from 8 views on,
+        # two below), pose reduction
+        launches = 2 + 7 + (1 + 2 + 1 if args.separate else 2) + (1 if sc.n_views >= 8 else 2) + 1
         line = {
             "metric": "Mpix/s fwd+bwd raster", "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,

@@ -303,16 +303,6 @@ __global__ void __launch_bounds__(BIN_T) k_bin_place(MatArgs a) {
   }
 }
 
-// [start, end) of each tile from the scanned matrix: its first block's place and the next tile's.
-__global__ void __launch_bounds__(256) k_bin_ranges(MatArgs a) {
-  const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
-  if (t >= a.n_tiles) return;
-  const uint32_t start = a.mat[t * a.B];
-  const uint32_t end = t + 1 < a.n_tiles ? a.mat[(t + 1) * a.B]
-                                         : (uint32_t)min(*a.n_pairs, (unsigned long long)0xffffffffu);
-  a.ranges[t] = make_uint2(start, end);
-}
-
 // Step 4.  Bitonic networks in the form whose every compare-exchange moves the smaller key to the
 // lower index (each merge starts by comparing mirrored positions), so that the positions past a
 // segment's end can stand for +infinity without being stored: a pair with one of them never moves.
@@ -324,6 +314,9 @@ struct SortOut {
   long long n_tiles, cap;
   uint32_t* large;         // tiles left to the CTA-wide sort
   unsigned int* n_large;
+  const uint32_t* mat;     // the scanned [tile][face block] count matrix, or null: ranges from the scatter
+  long long B;             // face blocks per tile row of the matrix
+  const unsigned long long* n_pairs;
 };
 
 __device__ __forceinline__ void put_pair(const SortOut& o, long long t, long long pos, unsigned long long k) {
@@ -341,12 +334,20 @@ __global__ void __launch_bounds__(32 * SORT_WARPS_PER_BLOCK) k_tile_sort(SortOut
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long t = (long long)blockIdx.x * SORT_WARPS_PER_BLOCK + warp;
   if (t >= o.n_tiles) return;
-  const uint2 rg = o.ranges[t];
+  // the segment: from the scanned matrix (its first block's place, the next tile's, the pair total
+  // after the last tile), else as the scatter left it in ranges
+  uint2 rg;
+  if (o.mat) {
+    rg.x = o.mat[t * o.B];
+    rg.y = t + 1 < o.n_tiles ? o.mat[(t + 1) * o.B] : (uint32_t)min(*o.n_pairs, 0xffffffffull);
+  } else {
+    rg = o.ranges[t];
+  }
   const long long start = min((long long)rg.x, o.cap);
   const long long end = min((long long)rg.y, o.cap);
-  // past the capacity (its bit is latched) the lists are cut, and the ranges with them, so that
-  // no later pass reads outside the pair list
-  if (lane == 0 && (long long)rg.y > o.cap) o.ranges[t] = make_uint2((uint32_t)start, (uint32_t)end);
+  // the tile's range for the passes that follow; past the capacity (its bit is latched) the lists
+  // are cut, and the ranges with them, so that no later pass reads outside the pair list
+  if (lane == 0 && (o.mat || (long long)rg.y > o.cap)) o.ranges[t] = make_uint2((uint32_t)start, (uint32_t)end);
   const int n = (int)max(0LL, end - start);
   if (n == 0) return;
   if (n <= 32) {
@@ -511,7 +512,6 @@ cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
     k_scan_bsums<<<1, SCAN_T, 0, s>>>(w.bsums, lm, &w.hdr->n_pairs, &w.hdr->error_bits, p->cap, &w.hdr->n_large);
     k_scan_apply<<<nb, SCAN_T, 0, s>>>(w.tmat, lm, w.bsums);
     k_bin_place<<<grid, BIN_T, smem, s>>>(ma);
-    k_bin_ranges<<<(unsigned)((p->n_tiles + 255) / 256), 256, 0, s>>>(ma);
   } else {
     // 1-3 with global counts: counts, their scan, starts, places
     e = cudaMemsetAsync(w.tcnt, 0, (size_t)p->n_tiles * sizeof(uint32_t), s);
@@ -528,7 +528,9 @@ cudaError_t ts_launch_bin(const TsPlanImpl* p, const TsWs& w, cudaStream_t s) {
     k_tile_scatter<<<nf, 256, 0, s>>>(ta);
   }
   // 4: the segments' sorts
-  SortOut so{w.keys[1], w.keys[0], w.vals[0], w.ranges, p->n_tiles, p->cap, w.tlarge, &w.hdr->n_large};
+  // (with the matrix, the sort also writes each tile's range)
+  SortOut so{w.keys[1], w.keys[0], w.vals[0], w.ranges, p->n_tiles, p->cap, w.tlarge, &w.hdr->n_large,
+             p->bin_blocks > 0 ? w.tmat : nullptr, p->bin_blocks, &w.hdr->n_pairs};
   k_tile_sort<<<(unsigned)((p->n_tiles + SORT_WARPS_PER_BLOCK - 1) / SORT_WARPS_PER_BLOCK), 32 * SORT_WARPS_PER_BLOCK,
                 0, s>>>(so);
   e = ts_smem_limit((const void*)k_tile_sort_large, (int)(LARGE_SMEM_ITEMS * sizeof(unsigned long long)));
