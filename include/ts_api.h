@@ -48,7 +48,7 @@ typedef enum {
   TS_ERR_CUDA = 2,        /* a CUDA launch or runtime call failed */
   TS_ERR_CAPACITY = 3,    /* more (tile, face) pairs than the plan's pair capacity */
   TS_ERR_TIMEOUT = 4,     /* a bounded device wait expired; outputs unspecified */
-  TS_ERR_UNSUPPORTED = 5  /* a parameter combination this build does not implement */
+  TS_ERR_UNSUPPORTED = 5  /* a parameter combination the library does not implement */
 } ts_status;
 
 #define TS_MAX_VIEWS 256

@@ -333,3 +333,30 @@ def test_counters_match_oracle(oracle, name):
     assert c["n_visible"] == int((pr["count"] > 0).sum())
     assert c["n_pairs"] == len(b["ids"])
     assert c["fwd_contrib"] == c["bwd_contrib"] == int(st["coverage"].sum()) > 0
+
+
+def test_chain_rule_forms_agree():
+    """The chain rule's one-pass form (8 views and more) and its two-pass form (fewer) on the same
+    work: the C1 view alone (two-pass), and the C1 view with seven more views that see nothing, the
+    camera 100 m behind the map (one-pass).  Both forms sum each face's views in view order and each
+    view's faces in face order, so they differ only by the order of the raster's atomic adds into
+    the slots."""
+    sc = random_triangles_scene(seed=1)
+    n = 8
+    poses = np.repeat(sc.poses[:1], n, axis=0).copy()
+    poses[1:, 11] -= 100.0
+    cams = np.repeat(sc.cams[:1], n, axis=0)
+    big = Scene(sc.pos, sc.col, sc.opa, sc.faces, cams, poses)
+    tc, td = noise_targets(44, cams)
+    big.tgt_color = [sc.tgt_color[0]] + list(tc[1:])
+    big.tgt_depth = [sc.tgt_depth[0]] + list(td[1:])
+    p, _ = params_pair()
+    one = gpu_run(sc, p)
+    many = gpu_run(big, p)
+    assert many["counters"]["n_visible"] == one["counters"]["n_visible"] > 0
+    assert many["counters"]["fwd_contrib"] == one["counters"]["fwd_contrib"]
+    for k in ("dpos", "dcol", "dopa"):
+        scale = np.abs(one[k]).max()
+        assert np.allclose(many[k], one[k], rtol=1e-5, atol=1e-7 * scale), k
+    assert np.allclose(many["dtau"][0], one["dtau"][0], rtol=1e-5, atol=1e-7 * np.abs(one["dtau"][0]).max())
+    assert not np.any(many["dtau"][1:])
