@@ -105,7 +105,7 @@ typedef struct {
 
 /* ts_raster_params.flags: a forward-only plan, for callers that render without differentiating
  * (the render requests of a serving loop).  Its workspace holds no gradient slots and no per-pair
- * lane masks, the projection clears no gradient slots and the forward records no lane masks.
+ * lane masks, and the forward records no lane masks.
  * ts_render_bwd, ts_render_bwd_n, ts_render_step_l1 and ts_pose_grad on such a plan return
  * TS_ERR_INVALID_ARG. */
 #define TS_FLAG_FORWARD_ONLY 32
@@ -169,7 +169,9 @@ size_t ts_workspace_size(const ts_plan* plan);
 
 /* Zero the workspace's persistent state (counters, error word, per-pixel backward state).  Call
  * once after allocating the workspace and again after any device-side error; a workspace may then
- * be reused by plans of any layout that fits it.  Asynchronous. */
+ * be reused by plans of any layout that fits it, as long as each plan's calls on it begin with
+ * ts_project (the per-face gradient slots are cleared by the backward that reads them, and the
+ * projection clears them again when another plan used the workspace in between).  Asynchronous. */
 ts_status ts_workspace_init(const ts_plan* plan, void* ws, size_t ws_bytes, ts_stream stream);
 
 /* Eq. 1-3 per (view, face): rigid transform, projection, culling, the face's screen-space
@@ -208,7 +210,9 @@ ts_status ts_render_fwd_n(const ts_plan* plan, void* ws, float* color, float* de
  * then the chain rule through the projection into the map gradients (added, see ts_map_grad)
  * and the per-view pose gradient partials consumed by ts_pose_grad.
  *   dC [3][H][W], dD, dA [H][W] packed per view (device); dD or dA may be NULL (zero).
- *   grad may be NULL or have NULL members to skip map gradients. */
+ *   grad may be NULL or have NULL members to skip map gradients.
+ * The per-face sums start from zero and are cleared again as the chain rule reads them, so
+ * several backward calls after one forward are independent of each other. */
 ts_status ts_render_bwd(const ts_plan* plan, void* ws, const float* dC, const float* dD,
                         const float* dA, const ts_map_grad* grad, ts_stream stream);
 

@@ -360,3 +360,74 @@ def test_chain_rule_forms_agree():
         assert np.allclose(many[k], one[k], rtol=1e-5, atol=1e-7 * scale), k
     assert np.allclose(many["dtau"][0], one["dtau"][0], rtol=1e-5, atol=1e-7 * np.abs(one["dtau"][0]).max())
     assert not np.any(many["dtau"][1:])
+
+
+@pytest.mark.parametrize("name", ["c1", "room_10v"])
+def test_backward_calls_are_independent(name):
+    """The backward adds into per-face slots that its chain-rule pass clears as it reads them (both
+    forms: one view, ten views), so two backward calls after one forward give the same gradients,
+    the raster's atomic order aside."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    from harness import pack_targets
+    sc = SCENES[name]()
+    p, _ = params_pair()
+    rast = ts.Rasterizer(sc.cams, sc.n_faces, p)
+    m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa, sc.faces)
+    rast.forward(m, ts.poses_tensor(sc.poses))
+    tc, td = pack_targets(sc)
+    dev = lambda a: torch.as_tensor(np.asarray(a, np.float32), device="cuda")  # noqa: E731
+    _, gC, gD = rast.l1_loss(dev(tc), dev(td), 0.05)
+    outs = []
+    for _ in range(2):
+        g = m.zeros_like()
+        rast.backward(gC, gD, None, g)
+        dtau = rast.pose_grad().clone()
+        torch.cuda.synchronize()
+        outs.append((g.pos.cpu().numpy().astype(np.float64), dtau.cpu().numpy().astype(np.float64)))
+    assert rast.counters()["error_bits"] == 0
+    for a, b in zip(outs[0], outs[1]):
+        scale = np.abs(a).max()
+        assert scale > 0 and np.allclose(b, a, rtol=1e-5, atol=1e-7 * scale)
+
+
+def test_plans_sharing_a_workspace():
+    """Two plans of different layouts (one view; ten views) take turns on one workspace, each call
+    sequence starting with the projection, and give what each gives on a workspace of its own: the
+    gradient slots, cleared by the backward that reads them, are cleared again by the projection
+    when the other plan used the workspace in between."""
+    import torch
+    import paper_2605_31419_gb300 as ts
+    from harness import pack_targets
+    p, _ = params_pair()
+    scenes = [random_triangles_scene(seed=1), _room_10v()]
+
+    def make(sc):
+        r = ts.Rasterizer(sc.cams, sc.n_faces, p)
+        m = ts.Map.from_numpy(sc.pos, sc.col, sc.opa, sc.faces)
+        tc, td = pack_targets(sc)
+        return r, m, ts.poses_tensor(sc.poses), torch.as_tensor(tc, device="cuda"), torch.as_tensor(td, device="cuda")
+
+    def step(r, m, poses, tc, td):
+        g = m.zeros_like()
+        r.project(m, poses)
+        r.bin()
+        r.step_l1(tc, td, 0.05, g)
+        dtau = r.pose_grad().clone()
+        torch.cuda.synchronize()
+        assert r.counters()["error_bits"] == 0
+        return g.pos.cpu().numpy().astype(np.float64), dtau.cpu().numpy().astype(np.float64)
+
+    alone = [step(*make(sc)) for sc in scenes]
+    shared = [make(sc) for sc in scenes]
+    big = max(s[0].ws_bytes for s in shared)
+    ws = torch.empty(big, dtype=torch.uint8, device="cuda")
+    for s in shared:
+        s[0].ws, s[0].ws_bytes = ws, big
+    ts.ts_workspace_init(shared[1][0].plan, ws)
+    for turn in range(4):
+        k = turn % 2
+        got = step(*shared[k])
+        for a, b in zip(alone[k], got):
+            scale = np.abs(a).max()
+            assert scale > 0 and np.allclose(b, a, rtol=1e-5, atol=1e-7 * scale), (turn, k)
