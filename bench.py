@@ -504,14 +504,15 @@ def bench_serving(ts, torch, dev, rates=(200, 500, 1000, 2000), seconds=10.0, n_
     return out
 
 
-def bench_e2e(ts, torch, dev, rast, m, poses, tgt_c, tgt_d, grad, flush, stream, pixels, args):
+def bench_e2e(ts, torch, dev, rast, m, poses, tgt_c, tgt_d, grad, stream, pixels, args):
     """The step end to end through the public API, as a training loop with a double-buffered input
     pipeline runs it: every step copies its inputs (map, poses, targets) from pinned host memory
     and reads its results (map gradients, pose gradients, per-view loss) back into pinned host
     memory.  Step k+1's inputs cross on a copy stream while step k computes, and step k's results
     cross on another while step k+1 computes; each buffer is reused only after the step that read
     it has finished.  The timed region spans all K steps: the first step's input copy and the last
-    step's result copy are inside it, and the L2 flush before every step is part of each step."""
+    step's result copy are inside it.  L2 is not flushed: every step's inputs (286 MB at the
+    default workload) are fresh copies, more than the 129 MB L2 holds, as a training loop has them."""
     h_in = [t.cpu().pin_memory() for t in (m.pos, m.col, m.opa, poses, tgt_c, tgt_d)]
     h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (grad.pos, grad.col, grad.opa)]
     h_out += [torch.empty(rast.V, 6).pin_memory(), torch.empty(rast.V).pin_memory()]
@@ -545,7 +546,6 @@ def bench_e2e(ts, torch, dev, rast, m, poses, tgt_c, tgt_d, grad, flush, stream,
                 stream.wait_event(out_read[b])  # step k-2's results have left buffer b
             pos, col, opa, ps, tc, td = d_in[b]
             dm, g = ts.Map(pos, col, opa), d_grad[b]
-            flush.fill_(1.0)
             g.pos.zero_(); g.col.zero_(); g.opa.zero_()
             if separate:
                 rast.forward(dm, ps)
@@ -580,7 +580,8 @@ def bench_e2e(ts, torch, dev, rast, m, poses, tgt_c, tgt_d, grad, flush, stream,
     return {"value": vals[best], "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "path": best, "by_path": vals, "steps": K,
             "pipeline": "inputs of step k+1 cross while step k computes; results of step k cross while step k+1 "
-                        "computes; first input copy and last result copy inside the timed region"}
+                        "computes; first input copy and last result copy inside the timed region",
+            "l2": f"not flushed: each step's inputs ({h2d / 1e6:.0f} MB) are fresh host copies larger than L2"}
 
 
 def run_reference(args):
@@ -730,7 +731,7 @@ def main():
     # -- end to end: pinned host inputs in, results out, through the same API ---------------------
     e2e = None
     if rank == 0:
-        e2e = bench_e2e(ts, torch, dev, rast, m, poses, tgt_c, tgt_d, grad, flush, stream, pixels, args)
+        e2e = bench_e2e(ts, torch, dev, rast, m, poses, tgt_c, tgt_d, grad, stream, pixels, args)
 
     if rank == 0:
         peaks, peak_src = measured_peaks()
