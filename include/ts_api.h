@@ -105,7 +105,7 @@ typedef struct {
 
 /* ts_raster_params.flags: a forward-only plan, for callers that render without differentiating
  * (the render requests of a serving loop).  Its workspace holds no gradient slots and no per-pair
- * lane masks, and the forward records no lane masks.
+ * lane masks, the projection clears no gradient slots and the forward records no lane masks.
  * ts_render_bwd, ts_render_bwd_n, ts_render_step_l1 and ts_pose_grad on such a plan return
  * TS_ERR_INVALID_ARG. */
 #define TS_FLAG_FORWARD_ONLY 32
@@ -169,9 +169,7 @@ size_t ts_workspace_size(const ts_plan* plan);
 
 /* Zero the workspace's persistent state (counters, error word, per-pixel backward state).  Call
  * once after allocating the workspace and again after any device-side error; a workspace may then
- * be reused by plans of any layout that fits it, as long as each plan's calls on it begin with
- * ts_project (the per-face gradient slots are cleared by the backward that reads them, and the
- * projection clears them again when another plan used the workspace in between).  Asynchronous. */
+ * be reused by plans of any layout that fits it.  Asynchronous. */
 ts_status ts_workspace_init(const ts_plan* plan, void* ws, size_t ws_bytes, ts_stream stream);
 
 /* Eq. 1-3 per (view, face): rigid transform, projection, culling, the face's screen-space
@@ -211,8 +209,9 @@ ts_status ts_render_fwd_n(const ts_plan* plan, void* ws, float* color, float* de
  * and the per-view pose gradient partials consumed by ts_pose_grad.
  *   dC [3][H][W], dD, dA [H][W] packed per view (device); dD or dA may be NULL (zero).
  *   grad may be NULL or have NULL members to skip map gradients.
- * The per-face sums start from zero and are cleared again as the chain rule reads them, so
- * several backward calls after one forward are independent of each other. */
+ * The per-face sums it accumulates start from the slots ts_project cleared, so each backward (this
+ * call, ts_render_bwd_n or ts_render_step_l1) needs a ts_project of its own: a second backward
+ * after one projection adds into the first one's sums. */
 ts_status ts_render_bwd(const ts_plan* plan, void* ws, const float* dC, const float* dD,
                         const float* dA, const ts_map_grad* grad, ts_stream stream);
 
@@ -263,7 +262,8 @@ ts_status ts_normal_loss(const ts_plan* plan, void* ws, const float* normal, con
  *   grad: as in ts_render_bwd (map gradients added; pose partials for ts_pose_grad).
  * Calls on the workspace: ts_project -> ts_bin -> ts_render_step_l1 [-> ts_pose_grad].  The fused
  * step does not record the per-pixel T_final and last-contribution position (its backward keeps
- * them on the chip), so ts_render_bwd cannot follow it without a new ts_render_fwd.  A plan with
+ * them on the chip), so ts_render_bwd cannot follow it without a new ts_render_fwd; as for every
+ * backward, a second one needs a new ts_project.  A plan with
  * TS_FLAG_NORMALS or TS_FLAG_FACE_SIGMA, a NULL required pointer, or a negative or non-finite
  * lambda_dep returns TS_ERR_INVALID_ARG. */
 ts_status ts_render_step_l1(const ts_plan* plan, void* ws, const float* tgt_color, const float* tgt_depth,

@@ -29,6 +29,7 @@ class RenderFunction(torch.autograd.Function):
         C, D, A = rast.forward(m, poses)
         ctx.rast = rast
         ctx.generation = rast.generation
+        ctx.done = False
         ctx.map = m
         ctx.need_pose = tau is not None and tau.requires_grad
         return C.clone(), D.clone(), A.clone()
@@ -38,6 +39,9 @@ class RenderFunction(torch.autograd.Function):
         rast: Rasterizer = ctx.rast
         if rast.generation != ctx.generation:
             raise RuntimeError("the rasterizer was reused by another forward before this backward")
+        if ctx.done:  # the per-face sums of a projection serve one backward
+            raise RuntimeError("a second backward through one render; render again to differentiate again")
+        ctx.done = True
         m = ctx.map
         g = m.zeros_like()
         dA = gA.contiguous() if gA is not None else None

@@ -20,7 +20,7 @@ struct MapArgs {
 };
 
 __global__ void k_setup(TsViewTable tab, int V, MapArgs map, const ts_pose* __restrict__ poses, TsDevHeader* hdr,
-                        TsView* views, ts_pose* ws_poses, unsigned long long* ctr, unsigned long long plan_id) {
+                        TsView* views, ts_pose* ws_poses, unsigned long long* ctr) {
   const int t = threadIdx.x;
   for (int v = t; v < V; v += blockDim.x) {
     views[v] = tab.v[v];
@@ -28,10 +28,6 @@ __global__ void k_setup(TsViewTable tab, int V, MapArgs map, const ts_pose* __re
   }
   for (int i = t; i < TS_N_CTR * TS_CTR_SLOTS; i += blockDim.x) ctr[(size_t)i * TS_CTR_STRIDE] = 0ull;
   if (t == 0) {
-    // the gradient slots are clean only if this plan's chain-rule pass left them so; from here on
-    // this call sequence may write over another plan's slots, so no plan's tag stands
-    hdr->slot_dirty = hdr->slot_tag != plan_id ? 1u : 0u;
-    hdr->slot_tag = 0ull;
     hdr->n_pairs = 0;
     hdr->n_visible = 0;
     hdr->fwd_contrib = 0;
@@ -101,15 +97,10 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjArgs a, int views_per_bl
     }
   }
   const float sig_m = (face_ok && a.sigma) ? __ldg(a.sigma + m) : 0.f;
-  // the gradient slots of the faces found visible are cleared unless the last chain-rule pass on
-  // this workspace was this plan's and the face was visible then (null grad: a forward-only plan)
-  const bool clear_known = a.grad && !a.hdr->slot_dirty;
   for (int view = v0; view < v1; ++view) {
     const long long idx = (long long)view * a.M + m;
     bool vis = face_ok;
     if (m < a.M) {
-      // visible at this plan's last projection: then its last backward read the slot and cleared it
-      const bool was_visible = clear_known && a.count[idx] > 0;
       const TsView vw = a.views[view];
       const ts_pose P = a.poses[view];
       float u[3], v[3], z[3], xv[3], yv[3];
@@ -174,13 +165,14 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjArgs a, int views_per_bl
         rec[4] = make_float4(oF, col[0][0], col[0][1], col[0][2]);
         rec[5] = make_float4(col[1][0], col[1][1], col[1][2], col[2][0]);
         rec[6] = make_float4(col[2][1], col[2][2], z[0], z[1]);
-        // gradient slot of this (view, face), face-major so that a face's views are adjacent
+        // gradient slot of this (view, face), face-major so that a face's views are adjacent;
+        // cleared here for the raster backward's atomics
         const long long slot = m * a.V + view;
         rec[7] = make_float4(z[2], __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
                              __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)slot));
-        if (a.grad && !was_visible) {
+        if (a.grad) {  // null for a forward-only plan
           // the raster backward adds into words 0..22, and with the side array (normals, sigma_F)
-          // also into 23, 24, 30, 31
+          // also into 23, 24, 30, 31; words 25..29 are not used
           float4* gs = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
           const int nz = a.aux ? TS_GRAD_WORDS / 4 : 6;
           for (int i = 0; i < nz; ++i) gs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -231,7 +223,7 @@ cudaError_t ts_launch_setup(const TsPlanImpl* p, const TsWs& w, const ts_map* ma
   TsViewTable local;  // passed by value: capture-safe, no host-to-device copy
   for (int v = 0; v < p->V; ++v) local.v[v] = p->views[v];
   MapArgs m{map->px, map->py, map->pz, map->cr, map->cg, map->cb, map->op, map->faces, map->n_vertices};
-  k_setup<<<1, 256, 0, s>>>(local, p->V, m, poses, w.hdr, w.views, w.poses, w.ctr, (unsigned long long)p->id);
+  k_setup<<<1, 256, 0, s>>>(local, p->V, m, poses, w.hdr, w.views, w.poses, w.ctr);
   return cudaGetLastError();
 }
 

@@ -12,8 +12,8 @@
 //   * the pinhole (Eq. 1) to camera space, R^T to world space, and the left-perturbation pose
 //     Jacobian [I, -[v_C]x] (Eq. 7): dL/dtau += [g_C ; v_C x g_C].
 //
-// Gradient slots are face-major (slot = face * V + view).  They are zero when the raster backward
-// adds into them (workspace initialisation, then this pass clears every slot it has read).  Persistent warps take 4 faces at a time; one ballot per face and 32 views
+// Gradient slots are face-major (slot = face * V + view) and cleared by the projection pass for
+// the visible ones.  Persistent warps take 4 faces at a time; one ballot per face and 32 views
 // gives the face's visible views.  Lanes 0..20 each own one output word (3 positions x 3 vertices,
 // 3 colours x 3 vertices, the opacity; lane 21 sigma_F), sum it over the face's visible views in
 // view order and add it to the map gradient.  Each view's pose terms are added to the warp's
@@ -45,8 +45,7 @@ struct PBArgs {
   const float4* aux;  // per (view, face) normal and sigma_F (TS_FLAG_NORMALS / TS_FLAG_FACE_SIGMA)
   bool normals, face_sigma;
   float* dst_sigma;  // dL/dsigma_F per face (TS_FLAG_FACE_SIGMA), may be null
-  TsDevHeader* hdr;
-  unsigned long long plan_id;  // tags the slots as cleared by this plan
+  const TsDevHeader* hdr;
   float* dst[7];  // gpx, gpy, gpz, gcr, gcg, gcb, gop
   bool min_opacity;  // o_F = min of the vertex opacities: dL/do_F to the first minimal vertex
   float* part;
@@ -336,18 +335,6 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
           for (int u = 0; u < 8; ++u) s[f] += vals[u];
         }
       }
-      // the faces' visible slots are read; clear them for the next backward (lane L word L)
-      __syncwarp();
-#pragma unroll
-      for (int f = 0; f < PG_F; ++f) {
-        unsigned bits = msk[f];
-        float* row = a.grad + (m0 + f) * a.V * TS_GRAD_WORDS + lane;
-        while (bits) {
-          const int v = r * 32 + __ffs(bits) - 1;
-          bits &= bits - 1;
-          row[(long long)v * TS_GRAD_WORDS] = 0.f;
-        }
-      }
     }
 #pragma unroll
     for (int f = 0; f < PG_F; ++f) {
@@ -373,8 +360,6 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_gather(PBArgs a) {
     for (int w = 0; w < PG_WARPS; ++w) sum += pv[((size_t)w * a.V + v) * 8 + i];
     a.part[((long long)v * a.nblocks + blockIdx.x) * 6 + i] = sum;
   }
-  // every slot this pass read is clear when the kernel ends (a later call reads the tag)
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->slot_tag = a.plan_id;
 }
 
 // One-pass form.
@@ -472,11 +457,6 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_face(PBArgs a) {
         }
         v = r * 32 + pb;
         chain_terms(a, v, m0 + fe, t);
-        {  // the slot is read; clear it for the next backward
-          float4* gz = reinterpret_cast<float4*>(a.grad + ((m0 + fe) * a.V + v) * TS_GRAD_WORDS);
-          const int nz = a.aux ? TS_GRAD_WORDS / 4 : 6;
-          for (int i = 0; i < nz; ++i) gz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
         float* row = rows + lane * PG_RS;
 #pragma unroll
         for (int i = 0; i < 9; ++i) row[i] = t.out[i];
@@ -528,8 +508,6 @@ __global__ void __launch_bounds__(PG_T) k_pbwd_face(PBArgs a) {
     for (int w = 0; w < PG_WARPS; ++w) sum += pv[((size_t)w * a.V + v) * 8 + i];
     a.part[((long long)v * a.nblocks + blockIdx.x) * 6 + i] = sum;
   }
-  // every slot this pass read is clear when the kernel ends (a later call reads the tag)
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->slot_tag = a.plan_id;
 }
 
 __global__ void __launch_bounds__(256) k_pose_reduce(const float* __restrict__ part, int nblocks, float* dtau) {
@@ -581,7 +559,6 @@ cudaError_t ts_launch_project_bwd(const TsPlanImpl* p, const TsWs& w, const ts_m
   a.face_sigma = p->face_sigma;
   a.dst_sigma = p->face_sigma ? g->gsigma : nullptr;
   a.hdr = w.hdr;
-  a.plan_id = (unsigned long long)p->id;
   a.dst[0] = g->gpx; a.dst[1] = g->gpy; a.dst[2] = g->gpz;
   a.dst[3] = g->gcr; a.dst[4] = g->gcg; a.dst[5] = g->gcb;
   a.dst[6] = g->gop;

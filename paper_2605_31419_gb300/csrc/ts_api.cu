@@ -2,7 +2,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -191,8 +190,6 @@ ts_status ts_plan_init(ts_plan* plan, const ts_camera* cams, int32_t n_views, in
   p->o_cov = take(p->stats ? (size_t)VM * 4 : 0);
   p->o_ctr = take((size_t)TS_N_CTR * TS_CTR_SLOTS * TS_CTR_STRIDE * 8);
   p->total = o;
-  static std::atomic<uint64_t> next_id{1};
-  p->id = next_id.fetch_add(1);
   p->magic = TS_PLAN_MAGIC;
   return TS_OK;
 }
@@ -234,9 +231,9 @@ ts_status ts_workspace_init(const ts_plan* plan, void* ws, size_t ws_bytes, ts_s
   const TsPlanImpl* p = impl(plan);
   if (!p || !ws_ok(p, ws, ws_bytes)) return TS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  // the header (counters, error word, no slot tag: the next projection clears the gradient slots
-  // of the faces it finds visible) and the per-pixel state the backward reads; every other region
-  // is written before it is read within a call sequence
+  // the header (counters, error word) and the per-pixel state the backward reads; every other
+  // region is written before it is read within a call sequence (the projection clears the
+  // gradient slots of the visible faces)
   cudaError_t e = cudaMemsetAsync((char*)ws + p->o_hdr, 0, sizeof(TsDevHeader), s);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)ws + p->o_tfin, 0, p->o_grad - p->o_tfin, s);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)ws + p->o_ctr, 0, (size_t)TS_N_CTR * TS_CTR_SLOTS * TS_CTR_STRIDE * 8, s);

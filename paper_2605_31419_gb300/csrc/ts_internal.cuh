@@ -80,18 +80,12 @@ struct TsDevHeader {
   long long n_vertices;
   unsigned int tile_counter;  // work counter of the persistent raster launches
   unsigned int n_large;       // tiles listed for the CTA-wide pair sort
-  // The gradient slots are zero between calls when the chain-rule pass of the plan with this id
-  // cleared them last; a projection reads the tag into slot_dirty and then drops it, since what
-  // it writes may lie where another plan keeps its slots (0: no plan)
-  unsigned long long slot_tag;
-  unsigned int slot_dirty;    // this projection clears the slots of the faces it finds visible
-  unsigned int pad[9];
+  unsigned int pad[12];
 };
 
 struct TsPlanImpl {
   uint32_t magic;
   int32_t V;
-  uint64_t id;  // unique within the process: tags the gradient slots this plan left cleared
   int64_t M;
   int64_t cap;
   ts_raster_params prm;
