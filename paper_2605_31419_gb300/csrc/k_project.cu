@@ -41,6 +41,14 @@ __global__ void k_setup(TsViewTable tab, int V, MapArgs map, const ts_pose* __re
   }
 }
 
+// One 32-byte store (eight floats) to a 32-byte aligned global address.
+__device__ __forceinline__ void st_v8(float* p, float a0, float a1, float a2, float a3, float a4, float a5, float a6,
+                                      float a7) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a0), "f"(a1), "f"(a2),
+               "f"(a3), "f"(a4), "f"(a5), "f"(a6), "f"(a7)
+               : "memory");
+}
+
 struct ProjArgs {
   MapArgs map;
   const TsView* views;
@@ -157,25 +165,21 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjArgs a, int views_per_bl
         const float e2x = u[0] - u[2], e2y = v[0] - v[2];
         const float invD = 1.0f / area2;
         const float k0 = (per / len[0]) * invD, k1 = (per / len[1]) * invD, k2 = (per / len[2]) * invD;
-        float4* rec = a.frec + idx * (TS_REC_WORDS / 4);
-        rec[0] = make_float4(u[0], u[1], u[2], v[0]);
-        rec[1] = make_float4(v[1], v[2], e0x, e0y);
-        rec[2] = make_float4(e1x, e1y, e2x, e2y);
-        rec[3] = make_float4(k0, k1, k2, invD);
-        rec[4] = make_float4(oF, col[0][0], col[0][1], col[0][2]);
-        rec[5] = make_float4(col[1][0], col[1][1], col[1][2], col[2][0]);
-        rec[6] = make_float4(col[2][1], col[2][2], z[0], z[1]);
+        float* rec = reinterpret_cast<float*>(a.frec + idx * (TS_REC_WORDS / 4));
+        st_v8(rec, u[0], u[1], u[2], v[0], v[1], v[2], e0x, e0y);
+        st_v8(rec + 8, e1x, e1y, e2x, e2y, k0, k1, k2, invD);
+        st_v8(rec + 16, oF, col[0][0], col[0][1], col[0][2], col[1][0], col[1][1], col[1][2], col[2][0]);
         // gradient slot of this (view, face), face-major so that a face's views are adjacent;
         // cleared here for the raster backward's atomics
         const long long slot = m * a.V + view;
-        rec[7] = make_float4(z[2], __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
-                             __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)slot));
+        st_v8(rec + 24, col[2][1], col[2][2], z[0], z[1], z[2], __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
+              __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)), __uint_as_float((uint32_t)slot));
         if (a.grad) {  // null for a forward-only plan
           // the raster backward adds into words 0..22, and with the side array (normals, sigma_F)
           // also into 23, 24, 30, 31; words 25..29 are not used
-          float4* gs = reinterpret_cast<float4*>(a.grad + slot * TS_GRAD_WORDS);
-          const int nz = a.aux ? TS_GRAD_WORDS / 4 : 6;
-          for (int i = 0; i < nz; ++i) gs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          float* gs = a.grad + slot * TS_GRAD_WORDS;
+          const int nz = a.aux ? TS_GRAD_WORDS / 8 : 3;
+          for (int i = 0; i < nz; ++i) st_v8(gs + 8 * i, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
         }
         const int tx0 = x0 / a.tile_w, tx1 = x1 / a.tile_w, ty0 = y0 / a.tile_h, ty1 = y1 / a.tile_h;
         a.rect[idx] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);

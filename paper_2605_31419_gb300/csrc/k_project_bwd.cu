@@ -57,6 +57,14 @@ __device__ __forceinline__ long long face_vertex(const TsDevHeader* h, long long
   return (j >= 0 && j < h->n_vertices) ? j : 0;
 }
 
+// One 32-byte load (eight floats) from a 32-byte aligned global address.
+__device__ __forceinline__ void ld_v8(const float* p, float* o) {
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+               : "l"(p)
+               : "memory");
+}
+
 // What the chain rule of one visible (view, face) gives: the world-space vertex-position
 // gradients, the pose terms, and the slot's colour, opacity and sigma_F sums passed through.
 struct SlotTerms {
@@ -71,14 +79,12 @@ struct SlotTerms {
 __device__ __forceinline__ void chain_terms(const PBArgs& a, int v, long long m, SlotTerms& t) {
   const TsDevHeader* h = a.hdr;
   const long long slot = m * a.V + v;
-  const float4* gp = reinterpret_cast<const float4*>(a.grad + slot * TS_GRAD_WORDS);
+  const float* gw = a.grad + slot * TS_GRAD_WORDS;
   float G[24];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const float4 q = gp[i];
-    G[4 * i] = q.x; G[4 * i + 1] = q.y; G[4 * i + 2] = q.z; G[4 * i + 3] = q.w;
-  }
-  const float gsig = a.face_sigma ? gp[6].x : 0.f;  // word 24
+  ld_v8(gw, G);
+  ld_v8(gw + 8, G + 8);
+  ld_v8(gw + 16, G + 16);
+  const float gsig = a.face_sigma ? gw[24] : 0.f;  // word 24
   const TsView vw = a.views[v];
   const ts_pose P = a.poses[v];
   // The projection, edge vectors, lengths and area are recomputed in the forward record's fixed
