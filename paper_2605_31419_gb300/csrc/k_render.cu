@@ -806,12 +806,12 @@ __global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_
   __shared__ RenderSmem sm;
   __shared__ FwdMasks fm;
   int seq = 0;
-  if (!PERSIST) {
+  if constexpr (!PERSIST) {
     fwd_tile<TW, TH, AUX>(a, blockIdx.x, smrec, sm, fm, seq);
-    return;
+  } else {
+    for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
+      fwd_tile<TW, TH, AUX>(a, t, smrec, sm, fm, seq);
   }
-  for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    fwd_tile<TW, TH, AUX>(a, t, smrec, sm, fm, seq);
 }
 
 template <int TW, int TH, bool PERSIST, bool AUX>
@@ -819,12 +819,12 @@ __global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_
   extern __shared__ __align__(128) float4 smrec[];
   __shared__ RenderSmem sm;
   int seq = 0;
-  if (!PERSIST) {
+  if constexpr (!PERSIST) {
     bwd_tile<TW, TH, AUX>(a, blockIdx.x, smrec, sm, seq);
-    return;
+  } else {
+    for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
+      bwd_tile<TW, TH, AUX>(a, t, smrec, sm, seq);
   }
-  for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm))
-    bwd_tile<TW, TH, AUX>(a, t, smrec, sm, seq);
 }
 
 // The fused step kernel.  Its forward's coverage counts (TS_FLAG_STATS) live in the space of the
@@ -836,11 +836,11 @@ __global__ void __launch_bounds__(TW * TH, raster_min_blocks(TW * TH)) k_render_
   static_assert(sizeof(FwdMasks) <= (TW * TH / 32) * Ring<false>::BYTES_PER_WARP, "coverage counts fit the rings");
   FwdMasks& fm = *reinterpret_cast<FwdMasks*>(smrec + (size_t)2 * a.S * 8);
   int seq = 0;
-  if (!PERSIST) {
+  if constexpr (!PERSIST) {
     step_tile<TW, TH>(a, blockIdx.x, smrec, sm, fm, seq);
-    return;
+  } else {
+    for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm)) step_tile<TW, TH>(a, t, smrec, sm, fm, seq);
   }
-  for (long long t = next_tile(a, sm); t >= 0; t = next_tile(a, sm)) step_tile<TW, TH>(a, t, smrec, sm, fm, seq);
 }
 
 // Per view, the sum of its tiles' loss partials in a fixed order.
